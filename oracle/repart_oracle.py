@@ -1,0 +1,454 @@
+"""CPU oracle of the repartitioning hot path.
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import, call or
+execute this module: only the tests, the smoke check of ``__graft_entry__``
+and the CPU-baseline / reference leg of ``bench.py`` use it. It shares no
+code with the CUDA path; it reads its inputs (rank descriptors, staging
+buffers, right-hand sides) as plain arrays.
+
+Everything is plain NumPy in FP64 (FP32 only where the mixed form says so),
+written for a reader to check against the paper by eye:
+
+* blockwise ownership of CPU ranks by GPU parts, ``n_GPU = n_CPU / alpha``
+  (Sec. 3);
+* the local / non-local split of coefficients and the localisation of
+  interface entries whose column lies in the part's own rows, the criterion
+  ``j in I_GPU(r) = union_l I_CPU(alpha*r + l)`` (Sec. 3, steps 1-3);
+* the three outputs of the repartitioning: sparsity pattern, update pattern
+  (per-rank offsets into one continuous buffer) and the permutation from LDU
+  order to row-major order (Sec. 3);
+* the value update: the continuous buffer reordered by that permutation
+  (Sec. 3, update procedure);
+* Jacobi-preconditioned CG for the merged pressure system (the paper solves
+  it with CG, Sec. 4; the preconditioner is Jacobi here);
+* FP32-inner / FP64-outer iterative refinement, the adjoint solve and the
+  gradients with respect to the stored entries (plain definitions).
+
+Library primitives used as single steps: ``numpy.lexsort`` (sorting) and
+``scipy.sparse.csr_matrix @ x`` (a sparse matrix-vector product).
+
+Pins: every function is checked in ``tests/test_oracle_pins.py`` against
+hand-enumerated maps, ``scipy.sparse`` COO->CSR conversion, dense solves,
+the closed-form eigenpairs of the 7-point operator, a face-loop LDU product
+written independently below, decomposition invariance and central finite
+differences.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+
+# --------------------------------------------------------------------------
+# Ownership and layout (Sec. 3, blockwise distribution)
+# --------------------------------------------------------------------------
+
+
+def rank_offsets(ranks) -> np.ndarray:
+    """off[r] = first merged row of CPU rank r; off[k] = total rows.
+
+    Under blockwise ownership the merged numbering of a part is the
+    concatenation of its ranks' local numberings (Sec. 3)."""
+    off = np.zeros(len(ranks) + 1, np.int64)
+    for r, d in enumerate(ranks):
+        off[r + 1] = off[r] + int(d.n_cells)
+    return off
+
+
+def slot_offsets(ranks, symmetric: bool) -> np.ndarray:
+    """Start of each rank's block in the continuous coefficient buffer.
+
+    Each rank contributes ``[diag n | upper F | lower F | iface E]`` (no
+    ``lower`` when the matrix is symmetric): the buffer is ordered by rank,
+    then by LDU order (Sec. 3, update procedure)."""
+    off = np.zeros(len(ranks) + 1, np.int64)
+    for r, d in enumerate(ranks):
+        f = len(d.lower_addr)
+        off[r + 1] = off[r] + int(d.n_cells) + (1 if symmetric else 2) * f + len(d.iface_row)
+    return off
+
+
+def part_of_rank(k: int, n_parts: int) -> np.ndarray:
+    """GPU part of every CPU rank: part p owns ranks alpha*p .. alpha*p+alpha-1
+    with alpha = k / n_parts (Sec. 3)."""
+    if n_parts < 1 or k % n_parts:
+        raise ValueError("n_parts must divide the number of CPU ranks")
+    alpha = k // n_parts
+    return np.arange(k, dtype=np.int64) // alpha
+
+
+def coo_entries(ranks, symmetric: bool):
+    """Every stored coefficient as (global row, global col, buffer slot).
+
+    Step 1 of Sec. 3: the sparsity pattern of each LDU matrix including its
+    coupling to non-local entries. Entry conventions: diag (i, i); upper[f]
+    at (l_f, u_f); lower[f] at (u_f, l_f); interface entry e at
+    (row_e, col_e of rank q_e). In symmetric mode the lower triangle reads
+    the upper slot."""
+    off = rank_offsets(ranks)
+    soff = slot_offsets(ranks, symmetric)
+    rows, cols, slots = [], [], []
+    for r, d in enumerate(ranks):
+        n = int(d.n_cells)
+        lo = np.asarray(d.lower_addr, np.int64)
+        up = np.asarray(d.upper_addr, np.int64)
+        f = lo.shape[0]
+        ir = np.asarray(d.iface_row, np.int64)
+        iq = np.asarray(d.iface_nbr_rank, np.int64)
+        ic = np.asarray(d.iface_nbr_col, np.int64)
+        s0 = soff[r]
+        i = np.arange(n, dtype=np.int64)
+        rows += [off[r] + i, off[r] + lo, off[r] + up]
+        cols += [off[r] + i, off[r] + up, off[r] + lo]
+        upper_slot = s0 + n + np.arange(f, dtype=np.int64)
+        lower_slot = upper_slot if symmetric else s0 + n + f + np.arange(f, dtype=np.int64)
+        iface_slot = s0 + n + (1 if symmetric else 2) * f + np.arange(ir.shape[0], dtype=np.int64)
+        slots += [s0 + i, upper_slot, lower_slot]
+        rows.append(off[r] + ir)
+        cols.append(off[iq] + ic)
+        slots.append(iface_slot)
+    return np.concatenate(rows), np.concatenate(cols), np.concatenate(slots)
+
+
+def _csr(rows, cols, slots, n_rows):
+    """Row-major ordering with ascending columns inside a row."""
+    order = np.lexsort((cols, rows))
+    r, c, s = rows[order], cols[order], slots[order]
+    if r.shape[0] > 1:
+        dup = (r[1:] == r[:-1]) & (c[1:] == c[:-1])
+        if dup.any():
+            raise ValueError("duplicate (row, col) entry")
+    row_ptr = np.zeros(n_rows + 1, np.int64)
+    np.cumsum(np.bincount(r, minlength=n_rows), out=row_ptr[1:])
+    return row_ptr, c, s
+
+
+@dataclasses.dataclass
+class PartMap:
+    """The repartitioned matrix of one GPU part (Sec. 3, three outputs)."""
+
+    row_off: int            # first merged row of the part
+    n_rows: int
+    buf_off: int            # start of the part's slice of the continuous buffer
+    buf_len: int
+    row_ptr: np.ndarray     # local CSR
+    col_idx: np.ndarray     # part-local columns
+    src_of: np.ndarray      # permutation: buffer slot feeding CSR position p
+    diag_pos: np.ndarray
+    tpos: np.ndarray        # CSR position of the transposed entry
+    nl_row_ptr: np.ndarray  # non-local CSR (rows of the part)
+    nl_col_idx: np.ndarray  # compressed non-local column
+    nl_src_of: np.ndarray
+    nl_cols: np.ndarray     # global column of each compressed non-local column
+
+
+def repartition_map(ranks, n_parts: int = 1, symmetric: bool = False):
+    """Fuse the sparsity patterns of the CPU ranks into one pattern per GPU part.
+
+    Sec. 3, step 3: a part fuses the local patterns of its alpha ranks; an
+    interface entry joins the local pattern when its column lies in the
+    part's rows, otherwise the non-local pattern, whose columns are the
+    ascending list of distinct remote global columns. Returns one PartMap
+    per part; ``src_of`` indexes the part's own slice of the buffer."""
+    k = len(ranks)
+    part = part_of_rank(k, n_parts)
+    off = rank_offsets(ranks)
+    soff = slot_offsets(ranks, symmetric)
+    rows, cols, slots = coo_entries(ranks, symmetric)
+    alpha = k // n_parts
+    out = []
+    for p in range(n_parts):
+        r0, r1 = off[p * alpha], off[(p + 1) * alpha]
+        b0, b1 = soff[p * alpha], soff[(p + 1) * alpha]
+        mine = (rows >= r0) & (rows < r1)
+        local = mine & (cols >= r0) & (cols < r1)       # j in I_GPU(p)
+        remote = mine & ~local
+        n_rows = int(r1 - r0)
+        row_ptr, col_idx, src_of = _csr(rows[local] - r0, cols[local] - r0, slots[local] - b0, n_rows)
+        # diagonal position and transposed position of each entry
+        row_of = np.repeat(np.arange(n_rows, dtype=np.int64), np.diff(row_ptr))
+        diag_pos = np.full(n_rows, -1, np.int64)
+        is_d = row_of == col_idx
+        diag_pos[row_of[is_d]] = np.nonzero(is_d)[0]
+        key = row_of * n_rows + col_idx                    # sorted ascending
+        tkey = col_idx * n_rows + row_of
+        tpos = np.searchsorted(key, tkey)
+        tpos_ok = (tpos < key.shape[0]) & (key[np.minimum(tpos, key.shape[0] - 1)] == tkey)
+        tpos = np.where(tpos_ok, tpos, -1)
+        nl_cols = np.unique(cols[remote])
+        nl_row_ptr, nl_col_idx, nl_src_of = _csr(
+            rows[remote] - r0, np.searchsorted(nl_cols, cols[remote]), slots[remote] - b0, n_rows)
+        out.append(PartMap(int(r0), n_rows, int(b0), int(b1 - b0), row_ptr, col_idx, src_of,
+                           diag_pos, tpos, nl_row_ptr, nl_col_idx, nl_src_of, nl_cols))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Value update (Sec. 3, update procedure)
+# --------------------------------------------------------------------------
+
+
+def pack_buffer(rank_arrays, symmetric: bool) -> np.ndarray:
+    """The continuous buffer: per rank diag, upper, (lower,) iface, in rank order."""
+    parts = []
+    for diag, upper, lower, iface in rank_arrays:
+        parts += [np.asarray(diag, np.float64), np.asarray(upper, np.float64)]
+        if not symmetric:
+            parts.append(np.asarray(lower, np.float64))
+        parts.append(np.asarray(iface, np.float64))
+    return np.concatenate(parts) if parts else np.zeros(0)
+
+
+def update_values(src_of: np.ndarray, buffer: np.ndarray) -> np.ndarray:
+    """vals[p] = buffer[src_of[p]]: the buffer reordered by the permutation."""
+    return buffer[src_of]
+
+
+def to_fp32(vals: np.ndarray) -> np.ndarray:
+    """FP32 copy of the values, round to nearest even."""
+    return vals.astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# Matrix-vector products
+# --------------------------------------------------------------------------
+
+
+def csr_matrix(row_ptr, col_idx, vals, n_cols=None):
+    n = row_ptr.shape[0] - 1
+    return sp.csr_matrix((vals, col_idx, row_ptr), shape=(n, n if n_cols is None else n_cols))
+
+
+def spmv(row_ptr, col_idx, vals, x):
+    """y_i = sum over stored (i, j) of a_ij x_j."""
+    return csr_matrix(row_ptr, col_idx, vals, x.shape[0]) @ x
+
+
+def ldu_matvec(ranks, buffer, x, symmetric: bool = False):
+    """Sum over CPU ranks of the LDU product plus interface coupling.
+
+    Written face by face, the way an LDU matrix is applied (rank r, face f:
+    y[l] += upper[f] x[u], y[u] += lower[f] x[l]), with no repartitioning at
+    all; its result must equal the merged CSR product."""
+    off = rank_offsets(ranks)
+    soff = slot_offsets(ranks, symmetric)
+    y = np.zeros(int(off[-1]), np.float64)
+    for r, d in enumerate(ranks):
+        n = int(d.n_cells)
+        lo = np.asarray(d.lower_addr, np.int64) + off[r]
+        up = np.asarray(d.upper_addr, np.int64) + off[r]
+        f = lo.shape[0]
+        s = int(soff[r])
+        diag = buffer[s:s + n]
+        upper = buffer[s + n:s + n + f]
+        lower = upper if symmetric else buffer[s + n + f:s + n + 2 * f]
+        iface = buffer[s + n + (1 if symmetric else 2) * f:int(soff[r + 1])]
+        rows = slice(int(off[r]), int(off[r + 1]))
+        y[rows] += diag * x[rows]
+        np.add.at(y, lo, upper * x[up])
+        np.add.at(y, up, lower * x[lo])
+        gcol = off[np.asarray(d.iface_nbr_rank, np.int64)] + np.asarray(d.iface_nbr_col, np.int64)
+        np.add.at(y, off[r] + np.asarray(d.iface_row, np.int64), iface * x[gcol])
+    return y
+
+
+# --------------------------------------------------------------------------
+# Jacobi-preconditioned CG (textbook PCG)
+# --------------------------------------------------------------------------
+
+OK, NOT_CONVERGED, BREAKDOWN = 0, 7, 8
+
+
+@dataclasses.dataclass
+class SolveResult:
+    x: np.ndarray
+    iterations: int
+    status: int
+    rel_residual: float       # recursive residual at exit
+    true_rel_residual: float  # ||b - A x|| / ||b|| recomputed at exit
+    outer_iterations: int = 0
+
+
+def jacobi_inverse(row_ptr, col_idx, vals, diag_pos=None):
+    """1 / a_ii (FP64, correctly rounded division)."""
+    if diag_pos is None:
+        n = row_ptr.shape[0] - 1
+        row_of = np.repeat(np.arange(n), np.diff(row_ptr))
+        diag = np.zeros(n, vals.dtype)
+        m = row_of == col_idx
+        diag[row_of[m]] = vals[m]
+    else:
+        diag = vals[diag_pos]
+    one = np.array(1.0, diag.dtype)
+    return one / diag
+
+
+def pcg(A, dinv, b, tol=1e-9, max_iter=10000, x0=None) -> SolveResult:
+    """Preconditioned CG with z = D^-1 r.
+
+    x0 = 0 unless given; r = b - A x; z = D^-1 r; p = z; per iteration
+    alpha = (r.z)/(p.Ap), x += alpha p, r -= alpha Ap; stop when
+    ||r|| <= tol ||b||, after confirming with the true residual b - A x (if
+    that fails, r is replaced by it and the iteration restarts from p = z);
+    otherwise z = D^-1 r, beta = (r.z)_new/(r.z)_old, p = z + beta p."""
+    b = np.asarray(b, np.float64)
+    bb = float(b @ b)
+    if bb == 0.0:
+        return SolveResult(np.zeros_like(b), 0, OK, 0.0, 0.0)
+    thresh = tol * tol * bb
+    x = np.zeros_like(b) if x0 is None else np.array(x0, np.float64)
+    r = b - A @ x if x0 is not None else b.copy()
+    it = 0
+    status = NOT_CONVERGED
+    rr = float(r @ r)
+    restart = True
+    while True:
+        if restart:
+            z = dinv * r
+            p = z.copy()
+            rz = float(r @ z)
+            restart = False
+            if rr <= thresh:
+                tr = b - A @ x
+                if float(tr @ tr) <= thresh:
+                    status = OK
+                    break
+        if it >= max_iter:
+            break
+        q = A @ p
+        pq = float(p @ q)
+        if not pq > 0.0:
+            status = BREAKDOWN
+            break
+        alpha = rz / pq
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        rr = float(r @ r)
+        if rr <= thresh:
+            tr = b - A @ x
+            trr = float(tr @ tr)
+            if trr <= thresh:
+                status = OK
+                break
+            r = tr
+            rr = trr
+            restart = True
+            continue
+        z = dinv * r
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        p = z + beta * p
+        rz = rz_new
+    tr = b - A @ x
+    return SolveResult(x, it, status, float(np.sqrt(rr / bb)), float(np.sqrt((tr @ tr) / bb)))
+
+
+def pcg_fp32(A32, dinv32, rhs32, rel_tol=1e-5, max_iter=10000):
+    """Inner FP32 PCG of the mixed form, x0 = 0.
+
+    Vectors, values and products are FP32; the dot products are accumulated
+    in FP64 and alpha / beta are rounded to FP32 before use. Stops on the
+    recursive residual ||r|| <= rel_tol ||rhs||. Returns (d, iterations,
+    status)."""
+    f32 = np.float32
+    x = np.zeros_like(rhs32)
+    r = rhs32.copy()
+    r64 = r.astype(np.float64)
+    thresh = rel_tol * rel_tol * float(r64 @ r64)
+    if thresh == 0.0:
+        return x, 0, OK
+    z = dinv32 * r
+    p = z.copy()
+    rz = float(r64 @ z.astype(np.float64))
+    it = 0
+    while it < max_iter:
+        q = A32 @ p
+        pq = float(p.astype(np.float64) @ q.astype(np.float64))
+        if not pq > 0.0:
+            return x, it, BREAKDOWN
+        alpha = f32(rz / pq)
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        r64 = r.astype(np.float64)
+        if float(r64 @ r64) <= thresh:
+            return x, it, OK
+        z = dinv32 * r
+        rz_new = float(r64 @ z.astype(np.float64))
+        beta = f32(rz_new / rz)
+        p = z + beta * p
+        rz = rz_new
+    return x, it, NOT_CONVERGED
+
+
+def mixed_ir(A64, A32, dinv32, b, tol=1e-9, inner_tol=1e-5, max_outer=50, max_inner=10000) -> SolveResult:
+    """FP32-inner / FP64-outer iterative refinement.
+
+    x = 0; repeat: r = b - A x with FP64 values; stop when ||r|| <= tol ||b||;
+    solve A32 d = fl32(r) by FP32 PCG to inner_tol relative; x += d in FP64."""
+    b = np.asarray(b, np.float64)
+    bb = float(b @ b)
+    x = np.zeros_like(b)
+    if bb == 0.0:
+        return SolveResult(x, 0, OK, 0.0, 0.0, 0)
+    inner_total = 0
+    status = NOT_CONVERGED
+    outer = 0
+    while True:
+        r = b - A64 @ x
+        rr = float(r @ r)
+        if rr <= tol * tol * bb:
+            status = OK
+            break
+        if outer >= max_outer:
+            break
+        d, it, st = pcg_fp32(A32, dinv32, r.astype(np.float32), inner_tol, max_inner)
+        inner_total += it
+        outer += 1
+        if st == BREAKDOWN:
+            status = BREAKDOWN
+            break
+        x += d.astype(np.float64)
+    rel = float(np.sqrt(rr / bb))
+    return SolveResult(x, inner_total, status, rel, rel, outer)
+
+
+# --------------------------------------------------------------------------
+# Adjoint and gradients
+# --------------------------------------------------------------------------
+
+
+def transpose_values(vals, tpos):
+    """Values of A^T in A's pattern: valsT[p] = vals[tpos[p]]."""
+    return vals[tpos]
+
+
+def entry_grad(row_ptr, col_idx, lam, x):
+    """dL/da_ij = -lambda_i x_j for every stored entry (from A x = b and
+    A^T lambda = dL/dx)."""
+    n = row_ptr.shape[0] - 1
+    row_of = np.repeat(np.arange(n), np.diff(row_ptr))
+    return -lam[row_of] * x[col_idx]
+
+
+def slot_grad(src_of, g_entry, n_slots):
+    """Gradient per buffer slot: the sum over CSR positions fed by the slot."""
+    return np.bincount(src_of, weights=g_entry, minlength=n_slots)
+
+
+def face_grad_ldu(ranks, lam, x):
+    """Gradient w.r.t. a face coefficient a_f entering as +a_f on both
+    diagonals and -a_f on both off-diagonals: -(lam_l - lam_u)(x_l - x_u).
+    Returns per rank [internal faces | interface entries], rank after rank."""
+    off = rank_offsets(ranks)
+    out = []
+    for r, d in enumerate(ranks):
+        lo = np.asarray(d.lower_addr, np.int64) + off[r]
+        up = np.asarray(d.upper_addr, np.int64) + off[r]
+        out.append(-(lam[lo] - lam[up]) * (x[lo] - x[up]))
+        i = off[r] + np.asarray(d.iface_row, np.int64)
+        j = off[np.asarray(d.iface_nbr_rank, np.int64)] + np.asarray(d.iface_nbr_col, np.int64)
+        out.append(-(lam[i] - lam[j]) * (x[i] - x[j]))
+    return np.concatenate(out) if out else np.zeros(0)

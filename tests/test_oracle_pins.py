@@ -1,0 +1,357 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each test ties one oracle function to something independent: a
+hand-enumerated map, a different library construction, a dense solve, a
+closed form, an invariant written another way, or finite differences.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import repart_oracle as O
+from paper_2510_08536_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- maps
+
+
+@pytest.mark.parametrize("case", ["two_cells_k2", "four_cells_k2"])
+def test_hand_enumerated_alpha2(case):
+    g = _golden("alpha2_maps.json")[case]
+    mesh = synth.box_mesh(*g["mesh"], *g["ranks"])
+    (m,) = O.repartition_map(mesh.ranks, 1)
+    e = g["n_parts_1"]
+    for key in ("row_ptr", "col_idx", "src_of", "diag_pos", "tpos"):
+        np.testing.assert_array_equal(getattr(m, key), e[key], err_msg=key)
+    assert m.nl_col_idx.size == 0
+    if "n_parts_2" in g:
+        parts = O.repartition_map(mesh.ranks, 2)
+        for m, e in zip(parts, g["n_parts_2"]):
+            for key, v in e.items():
+                np.testing.assert_array_equal(getattr(m, key), v, err_msg=key)
+
+
+def _scipy_csr(mesh, symmetric):
+    """Independent construction: scipy COO -> CSR of (row, col, slot+1)."""
+    off = np.cumsum([0] + [r.n_cells for r in mesh.ranks])
+    rows, cols, slots = [], [], []
+    s = 0
+    for ri, r in enumerate(mesh.ranks):
+        n, f, e = r.n_cells, r.n_faces, r.n_iface
+        rows += list(off[ri] + np.arange(n)); cols += list(off[ri] + np.arange(n)); slots += list(s + np.arange(n))
+        rows += list(off[ri] + r.lower_addr); cols += list(off[ri] + r.upper_addr); slots += list(s + n + np.arange(f))
+        lslot = s + n + np.arange(f) if symmetric else s + n + f + np.arange(f)
+        rows += list(off[ri] + r.upper_addr); cols += list(off[ri] + r.lower_addr); slots += list(lslot)
+        base = s + n + (1 if symmetric else 2) * f
+        rows += list(off[ri] + r.iface_row); cols += list(off[r.iface_nbr_rank] + r.iface_nbr_col)
+        slots += list(base + np.arange(e))
+        s = base + e
+    n = off[-1]
+    m = sp.coo_matrix((np.array(slots, np.float64) + 1, (rows, cols)), shape=(n, n)).tocsr()
+    m.sort_indices()
+    return m
+
+
+@pytest.mark.parametrize("dims,parts,symmetric", [
+    ((6, 5, 4), (2, 1, 2), False),
+    ((7, 3, 5), (3, 1, 1), True),
+    ((5, 6, 7), (1, 3, 2), False),
+    ((9, 4, 3), (2, 2, 1), True),
+])
+def test_map_equals_scipy_coo_to_csr(dims, parts, symmetric):
+    mesh = synth.box_mesh(*dims, *parts)
+    (m,) = O.repartition_map(mesh.ranks, 1, symmetric)
+    ref = _scipy_csr(mesh, symmetric)
+    np.testing.assert_array_equal(m.row_ptr, ref.indptr)
+    np.testing.assert_array_equal(m.col_idx, ref.indices)
+    np.testing.assert_array_equal(m.src_of, ref.data.astype(np.int64) - 1)
+    # the transposed position really holds the transposed entry
+    n = m.n_rows
+    row_of = np.repeat(np.arange(n), np.diff(m.row_ptr))
+    assert (m.tpos >= 0).all()
+    np.testing.assert_array_equal(row_of[m.tpos], m.col_idx)
+    np.testing.assert_array_equal(m.col_idx[m.tpos], row_of)
+    np.testing.assert_array_equal(m.col_idx[m.diag_pos], np.arange(n))
+
+
+def test_nonlocal_split_partitions_every_entry():
+    """With n_parts > 1 every entry lands in exactly one of the local or
+    non-local matrices of its owning part, with the right global column."""
+    mesh = synth.box_mesh(8, 6, 4, 4, 2, 1)
+    ref = _scipy_csr(mesh, False).tocoo()
+    want = set(zip(ref.row.tolist(), ref.col.tolist(), (ref.data.astype(int) - 1).tolist()))
+    got = set()
+    for pm in O.repartition_map(mesh.ranks, 4):
+        row_of = np.repeat(np.arange(pm.n_rows), np.diff(pm.row_ptr))
+        got |= set(zip((row_of + pm.row_off).tolist(), (pm.col_idx + pm.row_off).tolist(),
+                       (pm.src_of + pm.buf_off).tolist()))
+        nrow = np.repeat(np.arange(pm.n_rows), np.diff(pm.nl_row_ptr))
+        gcol = pm.nl_cols[pm.nl_col_idx]
+        assert ((gcol < pm.row_off) | (gcol >= pm.row_off + pm.n_rows)).all()
+        assert (np.diff(pm.nl_cols) > 0).all()
+        got |= set(zip((nrow + pm.row_off).tolist(), gcol.tolist(), (pm.nl_src_of + pm.buf_off).tolist()))
+    assert got == want
+
+
+def test_fewer_parts_fewer_nonlocal_entries():
+    """Sec. 3: repartitioning into fewer parts leaves fewer non-local coefficients."""
+    mesh = synth.box_mesh(8, 8, 8, 2, 2, 2)
+    counts = [sum(pm.nl_col_idx.size for pm in O.repartition_map(mesh.ranks, p)) for p in (8, 4, 2, 1)]
+    assert counts[0] > counts[1] > counts[2] > counts[3] == 0
+
+
+def test_duplicate_entry_rejected():
+    mesh = synth.box_mesh(3, 2, 2)
+    r = mesh.ranks[0]
+    r.lower_addr = np.concatenate([r.lower_addr, r.lower_addr[:1]])
+    r.upper_addr = np.concatenate([r.upper_addr, r.upper_addr[:1]])
+    with pytest.raises(ValueError):
+        O.repartition_map(mesh.ranks, 1)
+
+
+# ---------------------------------------------------------------- values
+
+
+def _dense_physical(mesh, a, shift=synth.DIAG_SHIFT):
+    """The physical matrix in GLOBAL cell order, straight from the faces."""
+    nx, ny, nz = mesh.nx, mesh.ny, mesh.nz
+    n = mesh.n_cells
+    A = np.zeros((n, n))
+    gid = lambda i, j, k: i + nx * (j + ny * k)
+    f = 0
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx - 1):
+                c1, c2 = gid(i, j, k), gid(i + 1, j, k)
+                A[c1, c2] -= a[f]; A[c2, c1] -= a[f]; A[c1, c1] += a[f]; A[c2, c2] += a[f]; f += 1
+    for k in range(nz):
+        for j in range(ny - 1):
+            for i in range(nx):
+                c1, c2 = gid(i, j, k), gid(i, j + 1, k)
+                A[c1, c2] -= a[f]; A[c2, c1] -= a[f]; A[c1, c1] += a[f]; A[c2, c2] += a[f]; f += 1
+    for k in range(nz - 1):
+        for j in range(ny):
+            for i in range(nx):
+                c1, c2 = gid(i, j, k), gid(i, j, k + 1)
+                A[c1, c2] -= a[f]; A[c2, c1] -= a[f]; A[c1, c1] += a[f]; A[c2, c2] += a[f]; f += 1
+    for k in range(nz):
+        for j in range(ny):
+            c = gid(0, j, k)
+            A[c, c] += 2 * a[f]; f += 1
+    A += shift * np.eye(n)
+    return A
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_updated_values_form_the_physical_matrix(symmetric):
+    mesh = synth.box_mesh(5, 4, 3, 2, 2, 1)
+    a = synth.face_coeffs(mesh, 0.5, 7)
+    stg = synth.Assembler(mesh, symmetric).staging(a)
+    (m,) = O.repartition_map(mesh.ranks, 1, symmetric)
+    vals = O.update_values(m.src_of, stg)
+    merged = O.csr_matrix(m.row_ptr, m.col_idx, vals).toarray()
+    gid = mesh.merged_gid()
+    A = _dense_physical(mesh, a)
+    np.testing.assert_allclose(merged, A[np.ix_(gid, gid)], rtol=1e-14, atol=1e-14)
+    v32 = O.to_fp32(vals)
+    assert v32.dtype == np.float32 and np.array_equal(v32, vals.astype(np.float32))
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_spmv_equals_sum_of_ldu_products(symmetric):
+    mesh = synth.box_mesh(9, 7, 6, 3, 1, 2)
+    a = synth.face_coeffs(mesh, 1.0, 3)
+    stg = synth.Assembler(mesh, symmetric).staging(a)
+    (m,) = O.repartition_map(mesh.ranks, 1, symmetric)
+    x = np.random.default_rng(5).standard_normal(mesh.n_cells)
+    y_csr = O.spmv(m.row_ptr, m.col_idx, O.update_values(m.src_of, stg), x)
+    y_ldu = O.ldu_matvec(mesh.ranks, stg, x, symmetric)
+    np.testing.assert_allclose(y_csr, y_ldu, rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- solves
+
+
+def _system(mesh, sigma, seed=100, symmetric=False):
+    a = synth.face_coeffs(mesh, sigma, seed)
+    stg = synth.Assembler(mesh, symmetric).staging(a)
+    (m,) = O.repartition_map(mesh.ranks, 1, symmetric)
+    vals = O.update_values(m.src_of, stg)
+    A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
+    dinv = O.jacobi_inverse(m.row_ptr, m.col_idx, vals, m.diag_pos)
+    return m, vals, A, dinv, a, stg
+
+
+def test_pcg_matches_dense_solve():
+    mesh = synth.box_mesh(10, 10, 10, 2, 2, 1)
+    m, vals, A, dinv, _, _ = _system(mesh, 1.0)
+    b = synth.uniform_vector(mesh, 0)
+    res = O.pcg(A, dinv, b, tol=1e-12)
+    assert res.status == O.OK and res.true_rel_residual <= 1e-12
+    x = np.linalg.solve(A.toarray(), b)
+    assert np.linalg.norm(res.x - x) / np.linalg.norm(x) < 1e-9
+
+
+def _eig(mesh, m_, p_, q_):
+    nx, ny, nz = mesh.nx, mesh.ny, mesh.nz
+    lam = (4 * np.sin((2 * m_ + 1) * np.pi / (4 * nx)) ** 2 + 4 * np.sin(p_ * np.pi / (2 * ny)) ** 2
+           + 4 * np.sin(q_ * np.pi / (2 * nz)) ** 2 + synth.DIAG_SHIFT)
+    i = np.arange(nx) + 0.5
+    j = np.arange(ny) + 0.5
+    k = np.arange(nz) + 0.5
+    v = (np.sin((2 * m_ + 1) * np.pi * i / (2 * nx))[None, None, :]
+         * np.cos(p_ * np.pi * j / ny)[None, :, None] * np.cos(q_ * np.pi * k / nz)[:, None, None])
+    return lam, v.ravel()
+
+
+@pytest.mark.parametrize("mpq", [(0, 0, 0), (2, 1, 3), (5, 4, 0)])
+def test_closed_form_eigenpairs(mpq):
+    """Uniform 7-point operator, Dirichlet at x=0 (ghost cell), Neumann
+    elsewhere: A v = lambda v, and PCG on b = v returns v / lambda."""
+    mesh = synth.box_mesh(12, 10, 8, 2, 2, 2)
+    m, vals, A, dinv, _, _ = _system(mesh, None)
+    lam, vg = _eig(mesh, *mpq)
+    v = vg[mesh.merged_gid()]
+    np.testing.assert_allclose(A @ v, lam * v, rtol=0, atol=1e-13)
+    res = O.pcg(A, dinv, v, tol=1e-13)
+    assert res.status == O.OK
+    np.testing.assert_allclose(res.x, v / lam, rtol=0, atol=1e-9 * np.abs(v / lam).max())
+
+
+def test_manufactured_solution():
+    mesh = synth.box_mesh(16, 12, 10, 2, 3, 2)
+    m, vals, A, dinv, a, stg = _system(mesh, 0.5, seed=11)
+    gid = mesh.merged_gid()
+    gi, gj, gk = gid % mesh.nx, (gid // mesh.nx) % mesh.ny, gid // (mesh.nx * mesh.ny)
+    xs = np.sin(0.3 * gi) * np.cos(0.2 * gj) + 0.1 * np.random.default_rng(2).standard_normal(gid.size) + gk * 0.01
+    b = O.ldu_matvec(mesh.ranks, stg, xs)  # not through the CSR path
+    res = O.pcg(A, dinv, b, tol=1e-13)
+    assert res.status == O.OK
+    assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) < 1e-9
+
+
+def test_decomposition_invariance():
+    sols = []
+    for p in [(1, 1, 1), (2, 2, 2), (4, 4, 4)]:
+        mesh = synth.box_mesh(16, 16, 16, *p)
+        m, vals, A, dinv, _, _ = _system(mesh, 0.5)
+        b = synth.uniform_vector(mesh, 0)
+        res = O.pcg(A, dinv, b, tol=1e-12)
+        xg = np.empty_like(res.x)
+        xg[mesh.merged_gid()] = res.x
+        sols.append((xg, res.iterations))
+    for xg, it in sols[1:]:
+        assert np.linalg.norm(xg - sols[0][0]) / np.linalg.norm(sols[0][0]) < 1e-10
+        # same physical matrix, permuted: the CG recurrence is the same up to rounding
+        assert abs(it - sols[0][1]) <= 2
+
+
+def test_pcg_edge_cases():
+    mesh = synth.box_mesh(4, 4, 4, 2, 1, 1)
+    m, vals, A, dinv, _, _ = _system(mesh, 0.5)
+    z = O.pcg(A, dinv, np.zeros(mesh.n_cells))
+    assert z.status == O.OK and z.iterations == 0 and not z.x.any()
+    b = synth.uniform_vector(mesh, 0)
+    exact = np.linalg.solve(A.toarray(), b)
+    warm = O.pcg(A, dinv, b, tol=1e-9, x0=exact)
+    assert warm.status == O.OK and warm.iterations == 0
+    lim = O.pcg(A, dinv, b, tol=1e-14, max_iter=3)
+    assert lim.status == O.NOT_CONVERGED and lim.iterations == 3
+    # an indefinite matrix breaks down (p.Ap <= 0)
+    neg = O.pcg(-A, -dinv, b, tol=1e-9)
+    assert neg.status == O.BREAKDOWN
+
+
+def test_jacobi_inverse_is_reciprocal_diagonal():
+    mesh = synth.box_mesh(5, 5, 5, 1, 1, 1)
+    m, vals, A, dinv, _, _ = _system(mesh, 1.0)
+    np.testing.assert_array_equal(dinv, 1.0 / A.diagonal())
+    np.testing.assert_array_equal(O.jacobi_inverse(m.row_ptr, m.col_idx, vals), dinv)
+
+
+def test_mixed_refinement_reaches_fp64_residual():
+    mesh = synth.box_mesh(16, 16, 16, 2, 2, 2)
+    m, vals, A, dinv, _, _ = _system(mesh, 1.0)
+    v32 = O.to_fp32(vals)
+    A32 = O.csr_matrix(m.row_ptr, m.col_idx, v32)
+    dinv32 = np.float32(1.0) / v32[m.diag_pos]
+    b = synth.uniform_vector(mesh, 0)
+    res = O.mixed_ir(A, A32, dinv32, b, tol=1e-9, inner_tol=1e-5)
+    assert res.status == O.OK and res.outer_iterations >= 2
+    tr = np.linalg.norm(b - A @ res.x) / np.linalg.norm(b)
+    assert tr <= 1e-9
+    x = np.linalg.solve(A.toarray(), b)
+    assert np.linalg.norm(res.x - x) / np.linalg.norm(x) < 1e-6
+    # FP32 values alone cannot reach 1e-9: the FP64 outer residual is what gets there
+    d, _, _ = O.pcg_fp32(A32, dinv32, b.astype(np.float32), 1e-7, 5000)
+    assert np.linalg.norm(b - A @ d.astype(np.float64)) / np.linalg.norm(b) > 1e-9
+
+
+# ---------------------------------------------------------------- adjoint
+
+
+def test_transpose_values_give_dense_transpose():
+    mesh = synth.box_mesh(4, 3, 3, 2, 1, 1)
+    (m,) = O.repartition_map(mesh.ranks, 1)
+    rng = np.random.default_rng(3)
+    vals = rng.standard_normal(m.src_of.size)  # a general (non-symmetric) matrix
+    A = O.csr_matrix(m.row_ptr, m.col_idx, vals).toarray()
+    AT = O.csr_matrix(m.row_ptr, m.col_idx, O.transpose_values(vals, m.tpos)).toarray()
+    np.testing.assert_array_equal(AT, A.T)
+
+
+def test_gradients_by_central_differences():
+    """L = 0.5 ||x - x_t||^2 with A x = b: dL/db = lambda and the face
+    gradient -(lam_l - lam_u)(x_l - x_u) agree with central differences."""
+    mesh = synth.box_mesh(6, 5, 4, 2, 1, 2)
+    a = synth.face_coeffs(mesh, 0.5, 100)
+    asm = synth.Assembler(mesh)
+    b = synth.uniform_vector(mesh, 0)
+    xt = synth.uniform_vector(mesh, 1)
+    (m,) = O.repartition_map(mesh.ranks, 1)
+
+    def solve(a_, b_):
+        vals = O.update_values(m.src_of, asm.staging(a_))
+        A = O.csr_matrix(m.row_ptr, m.col_idx, vals).toarray()
+        return A, np.linalg.solve(A, b_)
+
+    def loss(a_, b_):
+        return 0.5 * float(np.sum((solve(a_, b_)[1] - xt) ** 2))
+
+    A, x = solve(a, b)
+    vals = O.update_values(m.src_of, asm.staging(a))
+    AT = O.csr_matrix(m.row_ptr, m.col_idx, O.transpose_values(vals, m.tpos))
+    lam = np.linalg.solve(AT.toarray(), x - xt)
+    np.testing.assert_allclose(lam, np.linalg.solve(A, x - xt), rtol=1e-12, atol=1e-12)  # symmetric A
+    h = 1e-6
+    for i in [0, 7, 33, mesh.n_cells - 1]:
+        e = np.zeros_like(b); e[i] = h
+        fd = (loss(a, b + e) - loss(a, b - e)) / (2 * h)
+        assert abs(fd - lam[i]) <= 1e-6 * max(1.0, abs(lam[i]))
+    # face gradient through global face ids, interface faces included
+    fg = O.face_grad_ldu(mesh.ranks, lam, x)
+    fid = np.concatenate([np.concatenate([r.face_gid, r.iface_face_gid]) for r in mesh.ranks])
+    for t in [0, 5, len(fid) // 2, len(fid) - 1]:
+        f = fid[t]
+        e = np.zeros_like(a); e[f] = h
+        fd = (loss(a + e, b) - loss(a - e, b)) / (2 * h)
+        assert abs(fd - fg[t]) <= 1e-6 * max(1.0, abs(fg[t]))
+    # the entry gradient, summed per slot, reproduces the face gradient by the chain rule
+    ge = O.entry_grad(m.row_ptr, m.col_idx, lam, x)
+    gs = O.slot_grad(m.src_of, ge, asm.index.size)
+    r0 = mesh.ranks[0]
+    n0, f0 = r0.n_cells, r0.n_faces
+    for f in range(f0):
+        l, u = r0.lower_addr[f], r0.upper_addr[f]
+        chain = gs[l] + gs[u] - gs[n0 + f] - gs[n0 + f0 + f]
+        assert abs(chain - fg[f]) <= 1e-12 * max(1.0, abs(fg[f]))
