@@ -1,0 +1,214 @@
+/*
+ * repart.h -- C ABI of the GB300 repartitioning library (librepart.so).
+ *
+ * Method: matrix repartitioning of Olenik, Koch and Anzt, "Investigating
+ * Matrix Repartitioning to Address the Over- and Undersubscription Challenge
+ * for a GPU-based CFD Solver" (arXiv 2510.08536). Many CPU ranks each hold an
+ * OpenFOAM LDU matrix (diagonal, upper and lower face coefficients over
+ * owner/neighbour addressing, plus processor-interface coefficients). The
+ * library fuses their sparsity into one device matrix per GPU part once
+ * (Sec. 3, steps 1-3), updates the values in place every time step through a
+ * permutation of one continuous buffer (Sec. 3, update procedure), and solves
+ * the merged pressure system with Jacobi-preconditioned CG (the paper's
+ * pressure solve is CG, Sec. 4).
+ *
+ * Conventions for every call:
+ *   - Every call returns rp_status; no exception crosses the ABI. On failure
+ *     rp_last_error() gives a message for the calling thread.
+ *   - Host-side validation runs before any device work.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). All device work is ordered on that stream; a call only blocks
+ *     the host where its comment says so.
+ *   - A handle owns all of its device memory and frees it in rp_destroy. The
+ *     caller owns every pointer it passes; the library keeps none of them
+ *     after the call returns.
+ *   - A handle must not be used by two host threads, or on two streams whose
+ *     work overlaps, at the same time.
+ *   - Merged row order: the rows of a part are its CPU ranks' local rows,
+ *     rank after rank (blockwise ownership, Sec. 3). Vectors b, x, lambda, g
+ *     use this order.
+ */
+#ifndef REPART_H
+#define REPART_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rp_status {
+  RP_OK = 0,
+  RP_EINVAL = 1,         /* malformed argument or descriptor                  */
+  RP_EDUP = 2,           /* two stored coefficients share one (row, col)      */
+  RP_ERANGE = 3,         /* an index is out of its range                      */
+  RP_EOVERFLOW = 4,      /* a size does not fit the 32-bit index types        */
+  RP_ENOMEM = 5,         /* device or host allocation failed                  */
+  RP_ECUDA = 6,          /* a CUDA call failed                                */
+  RP_NOT_CONVERGED = 7,  /* iteration limit reached before the tolerance      */
+  RP_BREAKDOWN = 8,      /* p.Ap <= 0 (matrix not SPD) or a NaN appeared      */
+  RP_DEVICE_TIMEOUT = 9, /* a bounded device wait ran out                     */
+  RP_EUNSUPPORTED = 10   /* valid request this build does not serve           */
+} rp_status;
+
+enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1 };   /* where a buffer lives       */
+enum { RP_FP64 = 0, RP_MIXED = 1 };            /* solve precision            */
+
+typedef struct rp_handle rp_handle;
+
+/* One CPU rank's LDU sparsity (Sec. 3, step 1: the pattern including the
+ * coupling to non-local entries). Host pointers, caller-owned, read only
+ * during rp_build_repartition.
+ *   lower_addr[f] < upper_addr[f] < n_cells: face f couples owner l and
+ *     neighbour u; upper[f] is entry (l, u), lower[f] is entry (u, l).
+ *   Interface entry e: entry (iface_row[e], iface_nbr_col[e] of rank
+ *     iface_nbr_rank[e]), with iface_nbr_rank[e] != this rank. Interfaces
+ *     must be paired: rank q holds the transposed entry.                   */
+typedef struct rp_ldu_desc {
+  int32_t n_cells;
+  int32_t n_faces;
+  const int32_t* lower_addr;
+  const int32_t* upper_addr;
+  int32_t n_iface;
+  const int32_t* iface_row;
+  const int32_t* iface_nbr_rank;
+  const int32_t* iface_nbr_col;
+} rp_ldu_desc;
+
+typedef struct rp_options {
+  int32_t n_parts;        /* GPU parts n_GPU = k / alpha; must divide k (Sec. 3) */
+  int32_t symmetric;      /* 1: ranks pass no lower[]; (u,l) reads upper[f]       */
+  int32_t want_fp32;      /* keep an FP32 copy of the values (mixed solves)       */
+  int32_t want_transpose; /* build tpos[] (transpose permutation, adjoint)        */
+  int32_t max_iter;       /* PCG iteration cap (FP64; inner cap when mixed)       */
+  int32_t max_outer;      /* refinement steps cap of the mixed solve              */
+  int32_t max_restarts;   /* residual-replacement restarts allowed per solve      */
+  int32_t device;         /* CUDA device ordinal (-1: current device)             */
+  double inner_tol;       /* relative tolerance of the FP32 inner solve           */
+  int64_t spin_limit;     /* iteration limit of every device-side wait            */
+} rp_options;
+
+/* Defaults: n_parts 1, general (non-symmetric) storage, FP32 copy on,
+ * transpose off, max_iter 20000, max_outer 30, max_restarts 8, current
+ * device, inner_tol 1e-5, spin_limit 1<<26. */
+void rp_default_options(rp_options* opts);
+
+/* Sec. 3 steps 1-3 and the three outputs (sparsity pattern, update pattern,
+ * permutation P): validates the k descriptors on the host, uploads them,
+ * and builds on the device, per part, the CSR pattern (columns ascending in
+ * each row), src_of[p] (the buffer slot feeding CSR position p, i.e. P),
+ * diag_pos, tpos (optional) and the non-local pattern for n_parts > 1.
+ * Errors: RP_EINVAL (bad counts, null arrays, owner >= neighbour, self or
+ * unpaired interface, n_parts not dividing k), RP_ERANGE (index outside its
+ * rank), RP_EOVERFLOW (rows, entries or slots >= 2^31), RP_EDUP (repeated
+ * (row, col)), RP_ENOMEM, RP_ECUDA. Blocks the host until done. */
+rp_status rp_build_repartition(const rp_ldu_desc* ranks, int32_t k, const rp_options* opts,
+                               rp_handle** out);
+
+/* Device views of part `part`'s map, owned by the handle.
+ * row_ptr[n_rows+1] counts from 0; col_idx is part-local; src_of indexes the
+ * part's slice [buf_off, buf_off+buf_len) of the continuous buffer;
+ * nl_cols[n_nl_cols] holds the global column of each compressed non-local
+ * column. tpos is NULL unless want_transpose. */
+typedef struct rp_map_view {
+  int64_t n_rows, nnz, nl_nnz, n_nl_cols, row_off, buf_off, buf_len;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const int32_t* src_of;
+  const int32_t* diag_pos;
+  const int32_t* tpos;
+  const int32_t* nl_row_ptr;
+  const int32_t* nl_col_idx;
+  const int32_t* nl_src_of;
+  const int32_t* nl_cols;
+} rp_map_view;
+rp_status rp_get_part_map(const rp_handle* h, int32_t part, rp_map_view* out);
+
+/* Total merged rows, stored local entries, buffer slots and parts. */
+rp_status rp_get_sizes(const rp_handle* h, int64_t* n_rows, int64_t* nnz, int64_t* n_slots,
+                       int32_t* n_parts);
+
+/* Sec. 3, update procedure. `buffer` is the continuous coefficient buffer:
+ * rank after rank, [diag n_r | upper F_r | lower F_r | iface E_r] (no lower
+ * block in symmetric mode), n_slots doubles. where = RP_MEM_HOST copies it
+ * into the handle's device staging buffer first (pinned memory makes that
+ * copy asynchronous); RP_MEM_DEVICE reads it in place. Then one permutation
+ * pass writes vals[p] = buffer[src_of[p]] (and the FP32 copy, round to
+ * nearest even) and the Jacobi diagonal 1/a_ii. Asynchronous. */
+rp_status rp_update_values_packed(rp_handle* h, const double* buffer, int32_t where, void* stream);
+
+/* Same, from per-rank arrays (k pointers each; lower may be NULL in
+ * symmetric mode). The arrays are copied into the staging buffer at their
+ * rank's offsets, then permuted. */
+rp_status rp_update_values(rp_handle* h, const double* const* diag, const double* const* upper,
+                           const double* const* lower, const double* const* iface, int32_t where,
+                           void* stream);
+
+/* Device views of the current values (vals32 NULL without want_fp32). */
+rp_status rp_get_values(const rp_handle* h, const double** vals, const float** vals32,
+                        const double** dinv);
+
+/* y = A x with the merged FP64 matrix (n_parts == 1); if xy is not NULL the
+ * device double *xy receives x.y. x, y, xy are device pointers. Uses the
+ * handle's reduction scratch. Asynchronous. */
+rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* xy, void* stream);
+
+typedef struct rp_solve_info {
+  int32_t status;           /* RP_OK, RP_NOT_CONVERGED or RP_BREAKDOWN       */
+  int32_t iterations;       /* PCG iterations (FP32 inner ones when mixed)   */
+  int32_t outer_iterations; /* refinement steps (mixed)                      */
+  int32_t restarts;         /* residual replacements                         */
+  double rel_residual;      /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
+} rp_solve_info;
+
+/* Solve A x = b for the merged matrix (n_parts == 1) to
+ * ||b - A x||_2 <= tol ||b||_2 (true residual, FP64).
+ * precision RP_FP64: Jacobi-PCG in FP64. RP_MIXED: iterative refinement with
+ * the residual, the update x += d and the convergence test in FP64 and the
+ * inner Jacobi-PCG on the FP32 values to inner_tol (needs want_fp32).
+ * x_is_guess: start from x (else x = 0). where: b and x are host or device.
+ * The whole iteration runs on the device (CUDA graph with conditional
+ * nodes), with no host synchronisation. If info is not NULL the call waits
+ * for the stream and fills it; the return value is then info->status. */
+rp_status rp_solve(rp_handle* h, const double* b, double* x, double tol, int32_t precision,
+                   int32_t x_is_guess, int32_t where, rp_solve_info* info, void* stream);
+
+/* Kernel timing: starts a CG run from x = 0 on right-hand side b (device)
+ * with the current values and launches `iters` iterations of the three
+ * iteration kernels of `precision` on the stream (outside any graph, with no
+ * stopping test), each bracketed by CUDA events. ms_out[0..2] receives the
+ * average duration of the SpMV kernel, the residual-update kernel and the
+ * x/p-update kernel. The kernels are the ones rp_solve's graph runs. Uses the
+ * handle's work vectors; blocks the host. */
+rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t precision, int32_t iters,
+                               float* ms_out, void* stream);
+
+/* Adjoint solve A^T lambda = g (FP64 Jacobi-PCG on the transposed values,
+ * built through tpos; needs want_transpose unless symmetric storage).
+ * Device pointers; info as in rp_solve. */
+rp_status rp_solve_adjoint(rp_handle* h, const double* g, double* lambda, double tol,
+                           rp_solve_info* info, void* stream);
+
+/* Gradients of a loss L(x) with A x = b and A^T lambda = dL/dx:
+ * dL/da_ij = -lambda_i x_j for every stored entry, summed per buffer slot
+ * into g_buffer[n_slots] (the layout of rp_update_values_packed).
+ * Device pointers. Asynchronous. */
+rp_status rp_entry_grad(rp_handle* h, const double* lambda, const double* x, double* g_buffer,
+                        void* stream);
+
+/* Gradient w.r.t. face coefficients a_f that enter as +a_f on both
+ * diagonals and -a_f on both off-diagonals: -(lambda_l - lambda_u)(x_l - x_u),
+ * written rank after rank as [faces F_r | interface entries E_r].
+ * Device pointers. Asynchronous. */
+rp_status rp_face_grad(rp_handle* h, const double* lambda, const double* x, double* g_face,
+                       void* stream);
+
+void rp_destroy(rp_handle* h);
+const char* rp_status_str(rp_status s);
+const char* rp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REPART_H */

@@ -111,6 +111,32 @@ def coo_entries(ranks, symmetric: bool):
     return np.concatenate(rows), np.concatenate(cols), np.concatenate(slots)
 
 
+def row_entries(ranks, row: int, symmetric: bool = False):
+    """The stored entries of one merged row, straight from the definitions:
+    sorted (global col, buffer slot) pairs. Slow; for sampling large maps."""
+    off = rank_offsets(ranks)
+    soff = slot_offsets(ranks, symmetric)
+    r = int(np.searchsorted(off, row, side="right") - 1)
+    d = ranks[r]
+    i = row - int(off[r])
+    n = int(d.n_cells)
+    lo = np.asarray(d.lower_addr, np.int64)
+    up = np.asarray(d.upper_addr, np.int64)
+    f = lo.shape[0]
+    s0 = int(soff[r])
+    out = [(row, s0 + i)]
+    for fi in np.nonzero(lo == i)[0]:
+        out.append((int(off[r] + up[fi]), s0 + n + int(fi)))
+    for fi in np.nonzero(up == i)[0]:
+        out.append((int(off[r] + lo[fi]), s0 + n + int(fi) + (0 if symmetric else f)))
+    base = s0 + n + (1 if symmetric else 2) * f
+    ir = np.asarray(d.iface_row, np.int64)
+    for e in np.nonzero(ir == i)[0]:
+        q = int(d.iface_nbr_rank[e])
+        out.append((int(off[q] + d.iface_nbr_col[e]), base + int(e)))
+    return sorted(out)
+
+
 def _csr(rows, cols, slots, n_rows):
     """Row-major ordering with ascending columns inside a row."""
     order = np.lexsort((cols, rows))

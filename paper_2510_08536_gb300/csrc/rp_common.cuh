@@ -1,0 +1,235 @@
+// Internal declarations shared by the translation units of librepart.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/repart.h"
+
+namespace rp {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const char* fmt, ...);
+rp_status fail(rp_status s, const char* fmt, ...);
+
+#define RP_TRY_CUDA(call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return ::rp::fail(RP_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                               \
+  } while (0)
+
+#define RP_TRY(call)                 \
+  do {                               \
+    rp_status s_ = (call);           \
+    if (s_ != RP_OK) return s_;      \
+  } while (0)
+
+// ---------------------------------------------------------------- constants
+
+constexpr int kThreads = 256;        // block size of the streaming kernels
+constexpr int kBlocksPerSm = 8;      // 8 x 256 threads = full residency on sm_103
+constexpr int kMaxPartials = 8;      // doubles reduced per block at most
+
+// ---------------------------------------------------------------- solver control
+
+// Device-resident scalars of one PCG / refinement run. All values are
+// written by the last block of a kernel and read by later kernels: no host
+// round trip inside the iteration.
+struct Ctl {
+  double bb;            // ||b||^2
+  double thresh;        // tol^2 ||b||^2
+  double rz;            // (r, z) of the current iterate
+  double rr;            // (r, r): recursive in the loop, true after a residual pass
+  double pq;            // (p, A p)
+  double alpha, beta;
+  double inner_thresh;  // mixed: inner_tol^2 ||fl32(r)||^2
+  double tol, inner_tol;
+  int32_t iter;         // iterations of the current inner run
+  int32_t iter_total;   // all inner iterations of the solve
+  int32_t max_iter;     // cap: total (FP64) or per inner run (mixed)
+  int32_t stop;         // inner loop exit requested
+  int32_t skip_x;       // this iteration broke down before its x update
+  int32_t status;       // -1 running, then RP_OK / RP_NOT_CONVERGED / RP_BREAKDOWN
+  int32_t pass;         // residual passes done
+  int32_t restarts;
+  int32_t max_restarts;
+  int32_t outer;        // refinement steps started (mixed)
+  int32_t max_outer;
+  int32_t x_zero;       // first pass starts from x = 0
+  int32_t skip_correct; // mixed: no correction to add this pass
+  unsigned int ticket;  // last-block election counter (reset by the last block)
+};
+
+// Pointers that change between calls (user buffers); the captured graphs
+// read them from device memory so they never need re-instantiation.
+struct SolveIO {
+  const double* b;
+  double* x;
+};
+
+struct Graphs {
+  cudaGraphExec_t fp64 = nullptr;
+  cudaGraphExec_t mixed = nullptr;
+  cudaGraphExec_t adjoint = nullptr;
+};
+
+}  // namespace rp
+
+// ---------------------------------------------------------------- handle
+
+struct rp_handle {
+  int device = 0;
+  int num_sms = 0;
+  int32_t k = 0, n_parts = 0;
+  int64_t n = 0;        // merged rows (all parts)
+  int64_t nnz = 0;      // stored local entries (all parts)
+  int64_t nl_nnz = 0;   // stored non-local entries (all parts)
+  int64_t n_slots = 0;  // continuous buffer length
+  int64_t n_face_out = 0;  // sum over ranks of F_r + E_r
+  bool symmetric = false, want_fp32 = false, want_transpose = false;
+  rp_options opts{};
+
+  // per rank (host)
+  std::vector<int64_t> row_off, slot_off, face_off, iface_off;
+  std::vector<int32_t> n_cells, n_faces, n_iface;
+  // per part (host)
+  std::vector<int64_t> part_row_off, part_nnz_off, part_nl_off, part_buf_off, part_nlcol_off;
+
+  // device map (per part segments, see rp_map_view)
+  int32_t* row_ptr = nullptr;     // n + n_parts
+  int32_t* col_idx = nullptr;     // nnz
+  int32_t* src_of = nullptr;      // nnz
+  int32_t* diag_pos = nullptr;    // n
+  int32_t* tpos = nullptr;        // nnz (optional)
+  int32_t* nl_row_ptr = nullptr;  // n + n_parts
+  int32_t* nl_col_idx = nullptr;
+  int32_t* nl_src_of = nullptr;
+  int32_t* nl_cols = nullptr;
+  // rank tables on the device (k + 1 entries)
+  int64_t* d_row_off = nullptr;
+  int64_t* d_slot_off = nullptr;
+  int64_t* d_face_off = nullptr;
+  int64_t* d_iface_off = nullptr;
+  int32_t* d_lower = nullptr;  // concatenated addressing, kept for face gradients
+  int32_t* d_upper = nullptr;
+  int32_t* d_iface_row = nullptr;
+  int32_t* d_iface_gcol = nullptr;  // global column of each interface entry
+  int64_t* d_out_off = nullptr;     // per-rank offsets of the face-gradient output
+
+  // values
+  double* staging = nullptr;  // n_slots
+  double* vals = nullptr;     // nnz (+pad)
+  float* vals32 = nullptr;    // nnz (+pad)
+  double* nl_vals = nullptr;
+  double* valsT = nullptr;    // transposed values (adjoint, on demand)
+  double* dinv = nullptr;     // n
+  float* dinv32 = nullptr;    // n
+  double* dinvT = nullptr;
+
+  // solver work space
+  double *r = nullptr, *p = nullptr, *q = nullptr;
+  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
+  double* b_host_stage = nullptr;  // device copies for host-side callers
+  double* x_host_stage = nullptr;
+  double* partials = nullptr;      // grid * kMaxPartials
+  rp::Ctl* ctl = nullptr;          // device
+  rp::SolveIO* io = nullptr;       // device
+  unsigned int* ticket = nullptr;  // spare ticket for rp_spmv
+  int grid = 0;                    // blocks of every streaming kernel
+  rp::Graphs graphs;
+  cudaStream_t capture_stream = nullptr;
+};
+
+namespace rp {
+
+// streaming-grid size for n rows
+inline int grid_for(const rp_handle* h, int64_t n) {
+  int64_t want = (n + kThreads - 1) / kThreads;
+  int64_t cap = (int64_t)h->num_sms * kBlocksPerSm;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
+rp_status ensure_solver_buffers(rp_handle* h);
+rp_status build_graphs(rp_handle* h);
+void free_solver(rp_handle* h);
+
+}  // namespace rp
+
+// ---------------------------------------------------------------- device helpers
+
+namespace rp {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide partial sums of NV values, written to partials[blockIdx.x*NV+i];
+// returns true in every thread of the one block that arrives last, with the
+// grid totals in tot[] (summed in block order: deterministic for a fixed
+// grid). The ticket is reset by that block.
+template <int NV>
+__device__ __forceinline__ bool reduce_last_block(double (&v)[NV], double* partials,
+                                                  unsigned int* ticket, double (&tot)[NV]) {
+  __shared__ double sm[NV][32];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = warp_sum(v[i]);
+    if (lane == 0) sm[i][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = lane < nw ? sm[i][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) partials[(size_t)blockIdx.x * NV + i] = s;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+      s += __ldcg(partials + (size_t)b * NV + i);
+    s = warp_sum(s);
+    __syncthreads();
+    if (lane == 0) sm[i][wid] = s;
+    __syncthreads();
+    double t = lane < nw ? sm[i][lane] : 0.0;
+    tot[i] = warp_sum(t);  // every warp computes the same total
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// index of the rank owning position t in an offset table off[0..k]
+__device__ __forceinline__ int find_rank(const int64_t* __restrict__ off, int k, int64_t t) {
+  int lo = 0, hi = k;  // off[lo] <= t < off[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace rp

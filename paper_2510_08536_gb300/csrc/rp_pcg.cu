@@ -1,0 +1,606 @@
+// Jacobi-preconditioned CG on the merged device matrix, FP64 and
+// FP32-inner / FP64-outer iterative refinement.
+//
+// One iteration is three HBM-streaming kernels with the two reductions of
+// CG fused into them; every scalar stays on the device:
+//   K1  q = A p,                    partial (p, q)   -> alpha = (r,z)/(p,q)
+//   K2  r -= alpha q, z = D^-1 r,   partial (r,z), (r,r) -> beta, stop test
+//   K3  x += alpha p, p = z + beta p
+// Bytes per row and iteration (FP64, 7 entries per row): K1 12*nnz/n + 4
+// (+8 p gather, +8 q write), K2 32, K3 48.
+//
+// Control: the solve is one CUDA graph. An outer while-node runs a residual
+// pass (r = b - A x, the true residual, and the start of a CG run) and then
+// an inner while-node over K1-K3; the inner condition is cleared by K2 when
+// the recursive residual passes or the iteration cap is hit, the outer one
+// by the residual pass when the true residual passes (or a cap is hit).
+// Every loop is bounded by device-side counters.
+#include "rp_common.cuh"
+
+namespace rp {
+
+template <typename T>
+struct IterArgs {
+  int64_t n;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const T* vals;
+  const T* dinv;
+  T* r;
+  T* p;
+  T* q;
+  T* xd;  // iterate updated by K3: the correction d (mixed); nullptr = io->x
+  Ctl* ctl;
+  SolveIO* io;
+  double* partials;
+  cudaGraphConditionalHandle inner;
+  int in_graph;  // 0: launched on a stream (kernel timing), no condition to set
+};
+
+struct ResArgs {
+  int64_t n;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* vals;
+  const double* dinv;  // FP64 path
+  double* r;
+  double* p;
+  const float* dinv32;  // mixed path
+  float* r32;
+  float* p32;
+  float* d32;
+  Ctl* ctl;
+  SolveIO* io;
+  double* partials;
+  cudaGraphConditionalHandle inner;
+  cudaGraphConditionalHandle outer;
+  int in_graph;
+};
+
+template <typename T>
+__device__ __forceinline__ T row_dot(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                     const T* __restrict__ vals, const T* __restrict__ x, int64_t i) {
+  const int s = __ldg(row_ptr + i), e = __ldg(row_ptr + i + 1);
+  T sum = T(0);
+  for (int j = s; j < e; ++j) sum = fma(__ldg(vals + j), __ldg(x + __ldg(col + j)), sum);
+  return sum;
+}
+
+// K1: q = A p and (p, q); the last block forms alpha.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_it_spmv(IterArgs<T> a) {
+  Ctl* c = a.ctl;
+  if (c->stop) return;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    T s = row_dot<T>(a.row_ptr, a.col, a.vals, a.p, i);
+    a.q[i] = s;
+    acc += (double)a.p[i] * (double)s;
+  }
+  double v[1] = {acc}, tot[1];
+  if (reduce_last_block<1>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    c->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      c->status = RP_BREAKDOWN;
+      c->stop = 1;
+      c->skip_x = 1;
+    } else {
+      c->alpha = c->rz / pq;
+    }
+  }
+}
+
+// K2: r -= alpha q; z = D^-1 r; (r, z), (r, r); stop test; beta.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
+  Ctl* c = a.ctl;
+  if (c->stop) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.in_graph) cudaGraphSetConditional(a.inner, 0);
+    return;
+  }
+  const T alpha = (T)c->alpha;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    T ri = fma(-alpha, a.q[i], a.r[i]);
+    a.r[i] = ri;
+    T zi = a.dinv[i] * ri;
+    rz += (double)ri * (double)zi;
+    rr += (double)ri * (double)ri;
+  }
+  double v[2] = {rz, rr}, tot[2];
+  if (reduce_last_block<2>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
+    c->iter += 1;
+    c->iter_total += 1;
+    c->rr = tot[1];
+    const double thresh = a.xd ? c->inner_thresh : c->thresh;
+    if (tot[1] <= thresh) {
+      c->stop = 1;
+    } else if (c->iter >= c->max_iter) {
+      c->stop = 1;
+    } else if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+      c->stop = 1;
+      c->status = RP_BREAKDOWN;
+    } else {
+      c->beta = tot[0] / c->rz;
+      c->rz = tot[0];
+    }
+    if (a.in_graph) cudaGraphSetConditional(a.inner, c->stop ? 0u : 1u);
+  }
+}
+
+// K3: x += alpha p; p = z + beta p (the latter only while iterating).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_it_xp(IterArgs<T> a) {
+  Ctl* c = a.ctl;
+  if (c->skip_x) return;
+  const T alpha = (T)c->alpha, beta = (T)c->beta;
+  const bool upd_p = !c->stop;
+  T* x = a.xd;
+  if (x == nullptr) x = reinterpret_cast<T*>(a.io->x);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    T pi = a.p[i];
+    x[i] = fma(alpha, pi, x[i]);
+    if (upd_p) a.p[i] = fma(beta, pi, a.dinv[i] * a.r[i]);
+  }
+}
+
+// Residual pass of the FP64 solve: r = b - A x (or r = b, x = 0 on a cold
+// start), p = z = D^-1 r, (r, z), (r, r) [, (b, b)]; decides the next step.
+__global__ void __launch_bounds__(kThreads) k_res64(ResArgs a) {
+  Ctl* c = a.ctl;
+  const bool cold = c->pass == 0 && c->x_zero;
+  const bool first = c->pass == 0;
+  const double* __restrict__ b = a.io->b;
+  double* __restrict__ x = a.io->x;
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    double ri;
+    if (cold) {
+      ri = bi;
+      x[i] = 0.0;
+    } else {
+      ri = bi - row_dot<double>(a.row_ptr, a.col, a.vals, x, i);
+    }
+    a.r[i] = ri;
+    const double zi = a.dinv[i] * ri;
+    a.p[i] = zi;
+    rz += ri * zi;
+    rr += ri * ri;
+    bb += bi * bi;
+  }
+  double v[3] = {rz, rr, bb}, tot[3];
+  if (reduce_last_block<3>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
+    if (first) {
+      c->bb = tot[2];
+      c->thresh = c->tol * c->tol * tot[2];
+    }
+    c->rr = tot[1];
+    c->rz = tot[0];
+    c->pass += 1;
+    bool go = false;
+    if (tot[1] <= c->thresh) {
+      c->status = RP_OK;
+    } else if (c->status == RP_BREAKDOWN) {
+    } else if (!isfinite(tot[1])) {
+      c->status = RP_BREAKDOWN;
+    } else if (c->iter_total >= c->max_iter || (!first && c->restarts >= c->max_restarts)) {
+      c->status = RP_NOT_CONVERGED;
+    } else {
+      if (!first) c->restarts += 1;
+      go = true;
+    }
+    c->stop = go ? 0 : 1;
+    c->skip_x = 0;
+    if (a.in_graph) {
+      cudaGraphSetConditional(a.inner, go ? 1u : 0u);
+      cudaGraphSetConditional(a.outer, go ? 1u : 0u);
+    }
+  }
+}
+
+// Residual pass of the mixed solve: r = b - A x in FP64 with FP64 values,
+// its FP32 copy as the inner right-hand side, d = 0, p = z = D32^-1 r32.
+__global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
+  Ctl* c = a.ctl;
+  const bool cold = c->pass == 0 && c->x_zero;
+  const bool first = c->pass == 0;
+  const double* __restrict__ b = a.io->b;
+  double* __restrict__ x = a.io->x;
+  double rz = 0.0, rr = 0.0, bb = 0.0, rr32 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    double ri;
+    if (cold) {
+      ri = bi;
+      x[i] = 0.0;
+    } else {
+      ri = bi - row_dot<double>(a.row_ptr, a.col, a.vals, x, i);
+    }
+    const float r32 = (float)ri;
+    a.r32[i] = r32;
+    a.d32[i] = 0.0f;
+    const float z32 = a.dinv32[i] * r32;
+    a.p32[i] = z32;
+    rz += (double)r32 * (double)z32;
+    rr32 += (double)r32 * (double)r32;
+    rr += ri * ri;
+    bb += bi * bi;
+  }
+  double v[4] = {rz, rr, bb, rr32}, tot[4];
+  if (reduce_last_block<4>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
+    if (first) {
+      c->bb = tot[2];
+      c->thresh = c->tol * c->tol * tot[2];
+    }
+    c->rr = tot[1];
+    c->pass += 1;
+    bool go = false;
+    if (tot[1] <= c->thresh) {
+      c->status = RP_OK;
+    } else if (c->status == RP_BREAKDOWN) {
+    } else if (!isfinite(tot[1])) {
+      c->status = RP_BREAKDOWN;
+    } else if (c->outer >= c->max_outer) {
+      c->status = RP_NOT_CONVERGED;
+    } else {
+      go = true;
+      c->outer += 1;
+      c->rz = tot[0];
+      c->inner_thresh = c->inner_tol * c->inner_tol * tot[3];
+      c->iter = 0;
+    }
+    c->stop = go ? 0 : 1;
+    c->skip_x = 0;
+    c->skip_correct = go ? 0 : 1;
+    if (a.in_graph) {
+      cudaGraphSetConditional(a.inner, go ? 1u : 0u);
+      cudaGraphSetConditional(a.outer, go ? 1u : 0u);
+    }
+  }
+}
+
+struct CorrectArgs {
+  int64_t n;
+  const float* d;
+  Ctl* c;
+  SolveIO* io;
+};
+
+// x += d (FP64) after an inner FP32 solve.
+__global__ void __launch_bounds__(kThreads) k_correct(CorrectArgs a) {
+  if (a.c->skip_correct || a.c->status == RP_BREAKDOWN) return;
+  double* __restrict__ x = a.io->x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)a.d[i];
+}
+
+__global__ void k_setup(Ctl* c, SolveIO* io, const double* b, double* x, double tol, double inner_tol, int x_zero,
+                        int max_iter, int max_restarts, int max_outer) {
+  io->b = b;
+  io->x = x;
+  c->tol = tol;
+  c->inner_tol = inner_tol;
+  c->x_zero = x_zero;
+  c->max_iter = max_iter;
+  c->max_restarts = max_restarts;
+  c->max_outer = max_outer;
+  c->iter = 0;
+  c->iter_total = 0;
+  c->pass = 0;
+  c->restarts = 0;
+  c->outer = 0;
+  c->status = -1;
+  c->stop = 0;
+  c->skip_x = 0;
+  c->skip_correct = 1;
+  c->alpha = c->beta = 0.0;
+  c->ticket = 0u;
+}
+
+// y = A x and, optionally, x.y
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_plain(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                 const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y,
+                 double* xy, double* partials, unsigned int* ticket) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = row_dot<double>(row_ptr, col, vals, x, i);
+    y[i] = s;
+    acc += x[i] * s;
+  }
+  if (xy == nullptr) return;
+  double v[1] = {acc}, tot[1];
+  if (reduce_last_block<1>(v, partials, ticket, tot) && threadIdx.x == 0) *xy = tot[0];
+}
+
+// ------------------------------------------------------------------ graphs
+
+namespace {
+
+rp_status add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* dep, void* fn, int grid,
+                     void* argp) {
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeKernel;
+  np.kernel.func = fn;
+  np.kernel.gridDim = dim3((unsigned)grid);
+  np.kernel.blockDim = dim3(kThreads);
+  np.kernel.sharedMemBytes = 0;
+  void* args[1] = {argp};
+  np.kernel.kernelParams = args;
+  RP_TRY_CUDA(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &np));
+  return RP_OK;
+}
+
+rp_status add_while(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* dep,
+                    cudaGraphConditionalHandle hnd, cudaGraph_t* body) {
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = hnd;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  RP_TRY_CUDA(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &np));
+  *body = np.conditional.phGraph_out[0];
+  return RP_OK;
+}
+
+struct GraphGuard {
+  cudaGraph_t g = nullptr;
+  ~GraphGuard() {
+    if (g) cudaGraphDestroy(g);
+  }
+};
+
+// while (outer) { residual pass; while (inner) { K1; K2; K3 }; [x += d] }
+rp_status build_solve_graph(rp_handle* h, bool mixed, const double* vals, const double* dinv,
+                            cudaGraphExec_t* exec) {
+  GraphGuard top;
+  RP_TRY_CUDA(cudaGraphCreate(&top.g, 0));
+  cudaGraphConditionalHandle hout, hin;
+  RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hout, top.g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNode_t wout, nres, win, n1, n2, n3, ncor;
+  cudaGraph_t obody, ibody;
+  RP_TRY(add_while(top.g, &wout, nullptr, hout, &obody));
+  RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hin, obody, 0, 0));
+
+  ResArgs ra{};
+  ra.n = h->n;
+  ra.row_ptr = h->row_ptr;
+  ra.col = h->col_idx;
+  ra.vals = vals;
+  ra.dinv = dinv;
+  ra.r = h->r;
+  ra.p = h->p;
+  ra.dinv32 = h->dinv32;
+  ra.r32 = h->r32;
+  ra.p32 = h->p32;
+  ra.d32 = h->d32;
+  ra.ctl = h->ctl;
+  ra.io = h->io;
+  ra.partials = h->partials;
+  ra.inner = hin;
+  ra.outer = hout;
+  ra.in_graph = 1;
+  RP_TRY(add_kernel(obody, &nres, nullptr, mixed ? (void*)k_res_mixed : (void*)k_res64, h->grid, &ra));
+  RP_TRY(add_while(obody, &win, &nres, hin, &ibody));
+  if (mixed) {
+    IterArgs<float> ia{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
+                       h->ctl, h->io, h->partials, hin, 1};
+    RP_TRY(add_kernel(ibody, &n1, nullptr, (void*)k_it_spmv<float>, h->grid, &ia));
+    RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<float>, h->grid, &ia));
+    RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<float>, h->grid, &ia));
+    CorrectArgs ca{h->n, h->d32, h->ctl, h->io};
+    RP_TRY(add_kernel(obody, &ncor, &win, (void*)k_correct, h->grid, &ca));
+  } else {
+    IterArgs<double> ia{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
+                        h->ctl, h->io, h->partials, hin, 1};
+    RP_TRY(add_kernel(ibody, &n1, nullptr, (void*)k_it_spmv<double>, h->grid, &ia));
+    RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<double>, h->grid, &ia));
+    RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<double>, h->grid, &ia));
+  }
+  RP_TRY_CUDA(cudaGraphInstantiate(exec, top.g, 0));
+  return RP_OK;
+}
+
+template <typename T>
+rp_status dalloc(T** p, int64_t count) {
+  if (*p) return RP_OK;
+  if (count <= 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, (size_t)count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(RP_ENOMEM, "cudaMalloc of %lld bytes failed", (long long)(count * sizeof(T)));
+  }
+  return RP_OK;
+}
+
+}  // namespace
+
+rp_status ensure_solver_buffers(rp_handle* h) {
+  const int64_t n = h->n + 64;
+  RP_TRY(dalloc(&h->r, n));
+  RP_TRY(dalloc(&h->p, n));
+  RP_TRY(dalloc(&h->q, n));
+  if (h->want_fp32) {
+    RP_TRY(dalloc(&h->r32, n));
+    RP_TRY(dalloc(&h->p32, n));
+    RP_TRY(dalloc(&h->q32, n));
+    RP_TRY(dalloc(&h->d32, n));
+  }
+  RP_TRY(dalloc(&h->partials, (int64_t)h->num_sms * kBlocksPerSm * kMaxPartials));
+  RP_TRY(dalloc(&h->ctl, 1));
+  RP_TRY(dalloc(&h->io, 1));
+  RP_TRY(dalloc(&h->ticket, 4));
+  RP_TRY_CUDA(cudaMemset(h->ctl, 0, sizeof(Ctl)));
+  RP_TRY_CUDA(cudaMemset(h->ticket, 0, 4 * sizeof(unsigned int)));
+  return RP_OK;
+}
+
+void free_solver(rp_handle* h) {
+  void* ptrs[] = {h->r, h->p, h->q, h->r32, h->p32, h->q32, h->d32, h->b_host_stage, h->x_host_stage,
+                  h->partials, h->ctl, h->io, h->ticket};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h->r = h->p = h->q = nullptr;
+  h->r32 = h->p32 = h->q32 = h->d32 = nullptr;
+  h->b_host_stage = h->x_host_stage = nullptr;
+  h->partials = nullptr;
+  h->ctl = nullptr;
+  h->io = nullptr;
+  h->ticket = nullptr;
+  if (h->graphs.fp64) cudaGraphExecDestroy(h->graphs.fp64);
+  if (h->graphs.mixed) cudaGraphExecDestroy(h->graphs.mixed);
+  if (h->graphs.adjoint) cudaGraphExecDestroy(h->graphs.adjoint);
+  h->graphs = Graphs{};
+}
+
+rp_status launch_solve(rp_handle* h, cudaGraphExec_t exec, const double* b, double* x, double tol, bool x_zero,
+                       int max_iter, rp_solve_info* info, cudaStream_t s) {
+  k_setup<<<1, 1, 0, s>>>(h->ctl, h->io, b, x, tol, h->opts.inner_tol, x_zero ? 1 : 0, max_iter,
+                          h->opts.max_restarts, h->opts.max_outer);
+  RP_TRY_CUDA(cudaGetLastError());
+  RP_TRY_CUDA(cudaGraphLaunch(exec, s));
+  (void)info;
+  return RP_OK;
+}
+
+rp_status read_info(rp_handle* h, rp_solve_info* info, cudaStream_t s) {
+  Ctl c;
+  RP_TRY_CUDA(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  RP_TRY_CUDA(cudaStreamSynchronize(s));
+  info->status = c.status < 0 ? RP_NOT_CONVERGED : c.status;
+  info->iterations = c.iter_total;
+  info->outer_iterations = c.outer;
+  info->restarts = c.restarts;
+  info->rel_residual = c.bb > 0.0 ? sqrt(c.rr / c.bb) : 0.0;
+  return RP_OK;
+}
+
+rp_status solve_common(rp_handle* h, bool mixed, const double* vals, const double* dinv, cudaGraphExec_t* slot,
+                       const double* b, double* x, double tol, int32_t x_is_guess, int32_t where,
+                       rp_solve_info* info, cudaStream_t s) {
+  if (!*slot) RP_TRY(build_solve_graph(h, mixed, vals, dinv, slot));
+  const double* bd = b;
+  double* xd = x;
+  if (where == RP_MEM_HOST) {
+    RP_TRY(dalloc(&h->b_host_stage, h->n + 64));
+    RP_TRY(dalloc(&h->x_host_stage, h->n + 64));
+    RP_TRY_CUDA(cudaMemcpyAsync(h->b_host_stage, b, 8 * h->n, cudaMemcpyHostToDevice, s));
+    if (x_is_guess) RP_TRY_CUDA(cudaMemcpyAsync(h->x_host_stage, x, 8 * h->n, cudaMemcpyHostToDevice, s));
+    bd = h->b_host_stage;
+    xd = h->x_host_stage;
+  }
+  RP_TRY(launch_solve(h, *slot, bd, xd, tol, !x_is_guess, h->opts.max_iter, info, s));
+  if (where == RP_MEM_HOST) RP_TRY_CUDA(cudaMemcpyAsync(x, h->x_host_stage, 8 * h->n, cudaMemcpyDeviceToHost, s));
+  if (info) {
+    RP_TRY(read_info(h, info, s));
+    return (rp_status)info->status;
+  }
+  return RP_OK;
+}
+
+}  // namespace rp
+
+using namespace rp;
+
+extern "C" rp_status rp_solve(rp_handle* h, const double* b, double* x, double tol, int32_t precision,
+                              int32_t x_is_guess, int32_t where, rp_solve_info* info, void* stream) {
+  if (!h || (!b && h->n) || (!x && h->n)) return fail(RP_EINVAL, "null argument");
+  if (!(tol >= 0.0)) return fail(RP_EINVAL, "tol must be >= 0");
+  if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
+  if (h->n_parts != 1) return fail(RP_EUNSUPPORTED, "solve needs n_parts == 1 (one merged matrix per GPU)");
+  if (precision != RP_FP64 && precision != RP_MIXED) return fail(RP_EINVAL, "precision must be RP_FP64 or RP_MIXED");
+  if (precision == RP_MIXED && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
+  if (h->n == 0) {
+    if (info) *info = rp_solve_info{RP_OK, 0, 0, 0, 0.0};
+    return RP_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == RP_MIXED)
+    return solve_common(h, true, h->vals, h->dinv, &h->graphs.mixed, b, x, tol, x_is_guess, where, info, s);
+  return solve_common(h, false, h->vals, h->dinv, &h->graphs.fp64, b, x, tol, x_is_guess, where, info, s);
+}
+
+extern "C" rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* xy, void* stream) {
+  if (!h || (!x && h->n) || (!y && h->n)) return fail(RP_EINVAL, "null argument");
+  if (h->n_parts != 1) return fail(RP_EUNSUPPORTED, "rp_spmv needs n_parts == 1");
+  if (h->n == 0) return RP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_spmv_plain<<<h->grid, kThreads, 0, s>>>(h->n, h->row_ptr, h->col_idx, h->vals, x, y, xy, h->partials, h->ticket);
+  RP_TRY_CUDA(cudaGetLastError());
+  return RP_OK;
+}
+
+extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t precision, int32_t iters,
+                                          float* ms_out, void* stream) {
+  if (!h || !b || !ms_out || iters < 1) return fail(RP_EINVAL, "invalid argument");
+  if (h->n_parts != 1) return fail(RP_EUNSUPPORTED, "needs n_parts == 1");
+  if (precision != RP_FP64 && precision != RP_MIXED) return fail(RP_EINVAL, "precision must be RP_FP64 or RP_MIXED");
+  if (precision == RP_MIXED && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
+  if (h->n == 0) return fail(RP_EINVAL, "empty system");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool mixed = precision == RP_MIXED;
+  RP_TRY(dalloc(&h->x_host_stage, h->n + 64));
+  // a fresh CG run from x = 0 that never meets its tolerance (tol = 0)
+  k_setup<<<1, 1, 0, s>>>(h->ctl, h->io, b, h->x_host_stage, 0.0, 0.0, 1, iters + 2, 0, 1);
+  ResArgs ra{};
+  ra.n = h->n;
+  ra.row_ptr = h->row_ptr;
+  ra.col = h->col_idx;
+  ra.vals = h->vals;
+  ra.dinv = h->dinv;
+  ra.r = h->r;
+  ra.p = h->p;
+  ra.dinv32 = h->dinv32;
+  ra.r32 = h->r32;
+  ra.p32 = h->p32;
+  ra.d32 = h->d32;
+  ra.ctl = h->ctl;
+  ra.io = h->io;
+  ra.partials = h->partials;
+  ra.in_graph = 0;
+  if (mixed) k_res_mixed<<<h->grid, kThreads, 0, s>>>(ra);
+  else k_res64<<<h->grid, kThreads, 0, s>>>(ra);
+  RP_TRY_CUDA(cudaGetLastError());
+  std::vector<cudaEvent_t> ev(3 * iters + 1, nullptr);
+  struct EvFree {
+    std::vector<cudaEvent_t>& v;
+    ~EvFree() {
+      for (auto e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } evfree{ev};
+  for (auto& e : ev) RP_TRY_CUDA(cudaEventCreate(&e));
+  IterArgs<double> a64{h->n, h->row_ptr, h->col_idx, h->vals, h->dinv, h->r, h->p, h->q, nullptr,
+                       h->ctl, h->io, h->partials, 0, 0};
+  IterArgs<float> a32{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
+                      h->ctl, h->io, h->partials, 0, 0};
+  RP_TRY_CUDA(cudaEventRecord(ev[0], s));
+  for (int it = 0; it < iters; ++it) {
+    if (mixed) k_it_spmv<float><<<h->grid, kThreads, 0, s>>>(a32);
+    else k_it_spmv<double><<<h->grid, kThreads, 0, s>>>(a64);
+    RP_TRY_CUDA(cudaEventRecord(ev[3 * it + 1], s));
+    if (mixed) k_it_resid<float><<<h->grid, kThreads, 0, s>>>(a32);
+    else k_it_resid<double><<<h->grid, kThreads, 0, s>>>(a64);
+    RP_TRY_CUDA(cudaEventRecord(ev[3 * it + 2], s));
+    if (mixed) k_it_xp<float><<<h->grid, kThreads, 0, s>>>(a32);
+    else k_it_xp<double><<<h->grid, kThreads, 0, s>>>(a64);
+    RP_TRY_CUDA(cudaEventRecord(ev[3 * it + 3], s));
+  }
+  RP_TRY_CUDA(cudaGetLastError());
+  RP_TRY_CUDA(cudaStreamSynchronize(s));
+  double acc[3] = {0, 0, 0};
+  for (int it = 0; it < iters; ++it)
+    for (int kk = 0; kk < 3; ++kk) {
+      float ms = 0.f;
+      RP_TRY_CUDA(cudaEventElapsedTime(&ms, ev[3 * it + kk], ev[3 * it + kk + 1]));
+      acc[kk] += ms;
+    }
+  for (int kk = 0; kk < 3; ++kk) ms_out[kk] = (float)(acc[kk] / iters);
+  Ctl c;
+  RP_TRY_CUDA(cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  if (c.status == RP_BREAKDOWN) return fail(RP_BREAKDOWN, "iteration broke down while being timed");
+  return RP_OK;
+}

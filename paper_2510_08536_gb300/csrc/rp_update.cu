@@ -1,0 +1,134 @@
+// Value update (Sec. 3, update procedure): the continuous buffer, ordered by
+// rank and LDU order, is reordered into the row-major device matrix by the
+// permutation P (src_of). The sparsity is never rebuilt.
+//
+// Roofline: HBM bound. Per stored entry one 4-byte index read, one 8-byte
+// gathered read and one 8-byte write (+4 bytes for the FP32 copy); the
+// gather is nearly sequential (a handful of monotone streams per rank), so
+// it moves close to the algorithmic bytes.
+#include "rp_common.cuh"
+
+namespace rp {
+
+template <bool FP32>
+__global__ void __launch_bounds__(kThreads)
+    k_permute(const double* __restrict__ buf, const int32_t* __restrict__ src_of, double* __restrict__ vals,
+              float* __restrict__ vals32, int64_t nnz) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(src_of) | reinterpret_cast<uintptr_t>(vals)) & 15) == 0 &&
+                   (!FP32 || (reinterpret_cast<uintptr_t>(vals32) & 15) == 0);
+  int64_t done = 0;
+  if (vec) {
+    const int64_t nv = nnz >> 2;
+    const int4* s4 = reinterpret_cast<const int4*>(src_of);
+    double2* v2 = reinterpret_cast<double2*>(vals);
+    float4* f4 = reinterpret_cast<float4*>(vals32);
+    for (int64_t i = tid; i < nv; i += stride) {
+      int4 s = __ldcs(s4 + i);
+      double a = __ldg(buf + s.x), b = __ldg(buf + s.y), c = __ldg(buf + s.z), d = __ldg(buf + s.w);
+      __stcs(v2 + 2 * i, make_double2(a, b));
+      __stcs(v2 + 2 * i + 1, make_double2(c, d));
+      if (FP32) __stcs(f4 + i, make_float4((float)a, (float)b, (float)c, (float)d));
+    }
+    done = nv << 2;
+  }
+  for (int64_t i = done + tid; i < nnz; i += stride) {
+    double a = __ldg(buf + src_of[i]);
+    vals[i] = a;
+    if (FP32) vals32[i] = (float)a;
+  }
+}
+
+// Jacobi diagonal straight from the diagonal block of each rank (contiguous
+// in the buffer): dinv[i] = 1 / a_ii, and 1/(float)a_ii for the FP32 copy.
+template <bool FP32>
+__global__ void __launch_bounds__(kThreads)
+    k_dinv(const double* __restrict__ buf, const int64_t* __restrict__ row_off,
+           const int64_t* __restrict__ slot_off, int k, int64_t n, double* __restrict__ dinv,
+           float* __restrict__ dinv32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int r = find_rank(row_off, k, i);
+    double d = __ldg(buf + slot_off[r] + (i - row_off[r]));
+    dinv[i] = 1.0 / d;
+    if (FP32) dinv32[i] = 1.0f / (float)d;
+  }
+}
+
+static rp_status permute_all(rp_handle* h, const double* buf, cudaStream_t s) {
+  for (int p = 0; p < h->n_parts; ++p) {
+    const double* base = buf + h->part_buf_off[p];
+    int64_t o = h->part_nnz_off[p], cnt = h->part_nnz_off[p + 1] - o;
+    int g = grid_for(h, (cnt + 3) / 4);
+    if (cnt > 0) {
+      if (h->want_fp32)
+        k_permute<true><<<g, kThreads, 0, s>>>(base, h->src_of + o, h->vals + o, h->vals32 + o, cnt);
+      else
+        k_permute<false><<<g, kThreads, 0, s>>>(base, h->src_of + o, h->vals + o, nullptr, cnt);
+    }
+    int64_t no = h->part_nl_off[p], ncnt = h->part_nl_off[p + 1] - no;
+    if (ncnt > 0)
+      k_permute<false><<<grid_for(h, (ncnt + 3) / 4), kThreads, 0, s>>>(base, h->nl_src_of + no, h->nl_vals + no,
+                                                                        nullptr, ncnt);
+  }
+  if (h->n > 0) {
+    if (h->want_fp32)
+      k_dinv<true><<<grid_for(h, h->n), kThreads, 0, s>>>(buf, h->d_row_off, h->d_slot_off, h->k, h->n, h->dinv,
+                                                          h->dinv32);
+    else
+      k_dinv<false><<<grid_for(h, h->n), kThreads, 0, s>>>(buf, h->d_row_off, h->d_slot_off, h->k, h->n, h->dinv,
+                                                           nullptr);
+  }
+  RP_TRY_CUDA(cudaGetLastError());
+  return RP_OK;
+}
+
+}  // namespace rp
+
+using namespace rp;
+
+extern "C" rp_status rp_update_values_packed(rp_handle* h, const double* buffer, int32_t where, void* stream) {
+  if (!h || (!buffer && h->n_slots > 0)) return fail(RP_EINVAL, "null argument");
+  if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* src = buffer;
+  if (where == RP_MEM_HOST) {
+    if (h->n_slots > 0)
+      RP_TRY_CUDA(cudaMemcpyAsync(h->staging, buffer, sizeof(double) * h->n_slots, cudaMemcpyHostToDevice, s));
+    src = h->staging;
+  }
+  return permute_all(h, src, s);
+}
+
+extern "C" rp_status rp_update_values(rp_handle* h, const double* const* diag, const double* const* upper,
+                                      const double* const* lower, const double* const* iface, int32_t where,
+                                      void* stream) {
+  if (!h || !diag || !upper || !iface || (!h->symmetric && !lower)) return fail(RP_EINVAL, "null argument");
+  if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaMemcpyKind kind = where == RP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  for (int r = 0; r < h->k; ++r) {
+    const int64_t n = h->n_cells[r], F = h->n_faces[r], E = h->n_iface[r];
+    double* dst = h->staging + h->slot_off[r];
+    if ((n && !diag[r]) || (F && !upper[r]) || (F && !h->symmetric && !lower[r]) || (E && !iface[r]))
+      return fail(RP_EINVAL, "rank %d: null coefficient array", r);
+    if (n) RP_TRY_CUDA(cudaMemcpyAsync(dst, diag[r], 8 * n, kind, s));
+    if (F) RP_TRY_CUDA(cudaMemcpyAsync(dst + n, upper[r], 8 * F, kind, s));
+    int64_t at = n + F;
+    if (!h->symmetric) {
+      if (F) RP_TRY_CUDA(cudaMemcpyAsync(dst + at, lower[r], 8 * F, kind, s));
+      at += F;
+    }
+    if (E) RP_TRY_CUDA(cudaMemcpyAsync(dst + at, iface[r], 8 * E, kind, s));
+  }
+  return permute_all(h, h->staging, s);
+}
+
+extern "C" rp_status rp_get_values(const rp_handle* h, const double** vals, const float** vals32,
+                                   const double** dinv) {
+  if (!h) return fail(RP_EINVAL, "null handle");
+  if (vals) *vals = h->vals;
+  if (vals32) *vals32 = h->vals32;
+  if (dinv) *dinv = h->dinv;
+  return RP_OK;
+}

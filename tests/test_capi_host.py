@@ -1,0 +1,101 @@
+"""The C ABI loads, exports what include/repart.h declares, and rejects
+malformed descriptors on the host before any device work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2510_08536_gb300 import build, repart, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return repart.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "repart.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rp_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_symbols_exported(lib):
+    names = _declared()
+    assert "rp_build_repartition" in names and "rp_solve" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(repart.Exports().names)
+
+
+def test_status_strings(lib):
+    assert lib.rp_status_str(0) == b"RP_OK"
+    assert lib.rp_status_str(repart.RP_EDUP) == b"RP_EDUP"
+    assert lib.rp_status_str(repart.RP_BREAKDOWN) == b"RP_BREAKDOWN"
+
+
+def test_default_options(lib):
+    o = repart.default_options()
+    assert o.n_parts == 1 and o.want_fp32 == 1 and o.max_iter > 0 and o.inner_tol == 1e-5
+
+
+class _R:
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def _ranks():
+    m = synth.box_mesh(4, 3, 2, 2, 1, 1)
+    return [_R(n_cells=r.n_cells, lower_addr=r.lower_addr.copy(), upper_addr=r.upper_addr.copy(),
+               iface_row=r.iface_row.copy(), iface_nbr_rank=r.iface_nbr_rank.copy(),
+               iface_nbr_col=r.iface_nbr_col.copy()) for r in m.ranks]
+
+
+def _status(ranks, **kw):
+    with pytest.raises(repart.RepartError) as e:
+        repart.build_repartition(ranks, **kw)
+    return e.value.status
+
+
+def test_rejects_bad_descriptors(lib):
+    r = _ranks()
+    r[0].lower_addr[0] = r[0].upper_addr[0]
+    assert _status(r) == repart.RP_EINVAL          # owner must be below neighbour
+    r = _ranks()
+    r[1].upper_addr[0] = r[1].n_cells
+    assert _status(r) == repart.RP_ERANGE          # address outside the rank
+    r = _ranks()
+    r[0].iface_nbr_rank[0] = 0
+    assert _status(r) == repart.RP_EINVAL          # interface to itself
+    r = _ranks()
+    r[0].iface_nbr_rank[0] = 5
+    assert _status(r) == repart.RP_ERANGE          # unknown neighbour rank
+    r = _ranks()
+    r[0].iface_nbr_col[0] = (r[0].iface_nbr_col[0] + 1) % r[1].n_cells
+    assert _status(r) == repart.RP_EINVAL          # interfaces not paired
+    r = _ranks()
+    r[1].iface_nbr_col[0] = r[0].n_cells + 3
+    assert _status(r) == repart.RP_ERANGE
+    assert _status(_ranks(), n_parts=3) == repart.RP_EINVAL  # n_parts must divide k
+    r = _ranks()
+    r[0].n_cells = -1
+    assert _status(r) == repart.RP_EINVAL
+
+
+def test_rejects_index_overflow(lib):
+    big = _R(n_cells=2**31 - 100, lower_addr=np.zeros(0, np.int32), upper_addr=np.zeros(0, np.int32),
+             iface_row=np.zeros(0, np.int32), iface_nbr_rank=np.zeros(0, np.int32),
+             iface_nbr_col=np.zeros(0, np.int32))
+    assert _status([big]) == repart.RP_EOVERFLOW
+
+
+def test_null_arguments(lib):
+    assert lib.rp_build_repartition(None, 0, None, None) == repart.RP_EINVAL
+    assert lib.rp_solve(None, None, None, 1e-9, 0, 0, 0, None, None) == repart.RP_EINVAL
+    assert lib.rp_update_values_packed(None, None, 0, None) == repart.RP_EINVAL
+    assert b"null" in lib.rp_last_error()
+    lib.rp_destroy(None)  # no-op

@@ -110,6 +110,16 @@ def test_fewer_parts_fewer_nonlocal_entries():
     assert counts[0] > counts[1] > counts[2] > counts[3] == 0
 
 
+def test_row_entries_match_full_map():
+    mesh = synth.box_mesh(7, 6, 5, 2, 3, 1)
+    for symmetric in (False, True):
+        (m,) = O.repartition_map(mesh.ranks, 1, symmetric)
+        for row in [0, 1, 17, 41, mesh.n_cells - 1]:
+            s, e = m.row_ptr[row], m.row_ptr[row + 1]
+            want = list(zip(m.col_idx[s:e].tolist(), m.src_of[s:e].tolist()))
+            assert O.row_entries(mesh.ranks, row, symmetric) == want
+
+
 def test_duplicate_entry_rejected():
     mesh = synth.box_mesh(3, 2, 2)
     r = mesh.ranks[0]
