@@ -1,0 +1,438 @@
+#!/usr/bin/env python3
+"""Time-step benchmark of the repartitioning hot path on GB300.
+
+One step = one simulated time step of the paper's pressure solve (Sec. 3-4):
+a new coefficient draw is pushed through ``rp_update_values_packed`` (the
+permutation update of the continuous buffer) and the merged system is solved
+with ``rp_solve`` to relative residual 1e-9 from x = 0. The default workload
+is 256^3 cells decomposed into k = 128 CPU ranks (8x4x4) merged into one CSR
+matrix, lognormal(0, 1) face coefficients, rhs U[-1, 1] seed 0.
+
+Both precisions are timed (FP64 Jacobi-PCG and FP32-inner / FP64-outer
+refinement); ``--precision`` picks the headline ``value``. Inputs are
+resident in HBM when the timed region starts and are larger than L2
+(0.94 GB coefficient buffer, 1.4 GB matrix), so no L2 flush is needed.
+
+``--impl reference`` times the CPU oracle instead (a bounded sample per
+step, scaled to a per-time-step figure with the oracle's own iteration
+counts): the paper ships no code, so the oracle is the reference arm.
+
+Multi-GPU (torchrun): the path does not shard; every rank runs an
+independent replica of the workload and ``value`` aggregates them.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "update+PCG ms/time-step at 256^3 cells, FP64 vs mixed; SpMV HBM GB/s vs peak"
+WORKLOAD_TEXT = {
+    "mixed_256": "256^3 cells (16,777,216), k=128 CPU ranks (8x4x4) merged into 1 CSR, lognormal(0,1.0) face "
+                 "coefficients redrawn every step, rhs U[-1,1] seed 0, rel. residual 1e-9 from x=0, inner tol 1e-5",
+    "update_128": "128^3 cells (2,097,152), k=64 CPU ranks (4x4x4) merged into 1 CSR, lognormal(0,0.5) face "
+                  "coefficients redrawn every step, rhs U[-1,1] seed 0, rel. residual 1e-9 from x=0",
+    "plain_fp64_32": "32^3 cells, k=8 ranks (2x2x2), uniform a_f=1, rhs U[-1,1] seed 0, rel. residual 1e-9",
+    "adjoint_128": "128^3 cells, k=64 ranks (4x4x4), lognormal(0,0.5) faces, rhs U[-1,1] seed 0, rel. residual 1e-9",
+    "profile_192": "192^3 cells, k=27 ranks (3x3x3), lognormal(0,1.0) faces (profiling size, larger than L2)",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixed_256", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--draws", type=int, default=4, help="distinct coefficient draws, cycled over the steps")
+    ap.add_argument("--only", default=None, choices=["mixed", "fp64"],
+                    help="time one precision only (profiling runs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the solve kernels from the host (for profilers; not a timing mode)")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(gpu_id), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(workload, draws, symmetric=False):
+    import numpy as np
+
+    from paper_2510_08536_gb300 import synth
+    w = synth.WORKLOADS[workload]
+    mesh = synth.workload_mesh(workload)
+    asm = synth.Assembler(mesh, symmetric)
+    stg = [asm.staging(synth.face_coeffs(mesh, w["sigma"], 100 + t)) for t in range(draws)]
+    b = synth.uniform_vector(mesh, 0)
+    return mesh, asm, stg, np.ascontiguousarray(b)
+
+
+# ---------------------------------------------------------------- oracle leg
+
+
+def oracle_sample(workload, seeds, iters, counts):
+    """Time the CPU oracle: per step one value update plus a bounded FP64 PCG.
+
+    t_fixed = pcg with 0 iterations (initial z, p and the final true
+    residual); t_iter = (pcg(iters) - t_fixed) / iters. Estimated ms per time
+    step = t_update + t_fixed + I * t_iter, with I the FP64 iteration count of
+    that step's system. Returns per-step estimates in ms."""
+    import numpy as np
+
+    from oracle import repart_oracle as O
+    from paper_2510_08536_gb300 import synth
+    w = synth.WORKLOADS[workload]
+    mesh = synth.workload_mesh(workload)
+    asm = synth.Assembler(mesh)
+    (m,) = O.repartition_map(mesh.ranks, 1)
+    b = synth.uniform_vector(mesh, 0)
+    out = []
+    for seed, count in zip(seeds, counts):
+        stg = asm.staging(synth.face_coeffs(mesh, w["sigma"], seed))
+        t0 = time.perf_counter()
+        vals = O.update_values(m.src_of, stg)
+        dinv = O.jacobi_inverse(m.row_ptr, m.col_idx, vals, m.diag_pos)
+        A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
+        t1 = time.perf_counter()
+        O.pcg(A, dinv, b, tol=0.0, max_iter=0)
+        t2 = time.perf_counter()
+        O.pcg(A, dinv, b, tol=0.0, max_iter=iters)
+        t3 = time.perf_counter()
+        t_upd, t_fix = t1 - t0, t2 - t1
+        t_it = max(0.0, (t3 - t2) - t_fix) / iters
+        out.append({"ms": 1e3 * (t_upd + t_fix + count * t_it), "update_ms": 1e3 * t_upd,
+                    "fixed_ms": 1e3 * t_fix, "iter_ms": 1e3 * t_it, "iterations": count,
+                    "sample_s": t3 - t0})
+        del stg, vals, A, dinv
+    return out
+
+
+def run_oracle_subprocess(workload, seeds, iters, counts, timeout=1800):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    arg = json.dumps({"workload": workload, "seeds": seeds, "iters": iters, "counts": counts})
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", arg], env=env,
+                       capture_output=True, text=True, timeout=timeout)
+    if p.returncode:
+        raise RuntimeError("oracle sample failed: " + p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def oracle_counts(workload, seeds):
+    p = os.path.join(ROOT, "tests", "golden", "iteration_counts.json")
+    d = json.load(open(p)).get(workload, {}) if os.path.exists(p) else {}
+    got = [d.get(str(s), {}).get("iterations") for s in seeds]
+    if any(c is None for c in got):
+        known = [v["iterations"] for v in d.values()]
+        fill = int(round(statistics.mean(known))) if known else None
+        got = [fill if c is None else c for c in got]
+    return got
+
+
+# ---------------------------------------------------------------- ours
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2510_08536_gb300 import repart
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    repart.load()
+    hbm_peak, peak_kind = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+
+    t0 = time.time()
+    draws = max(1, min(args.draws, args.steps + args.warmup))
+    mesh, asm, stg_host, b_np = make_inputs(args.workload, draws)
+    setup_s = time.time() - t0
+    n = mesh.n_cells
+    stg_dev = [torch.from_numpy(s).to(dev) for s in stg_host]
+    b = torch.from_numpy(b_np).to(dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    tb = time.perf_counter()
+    h = repart.build_repartition(mesh.ranks, host_loop=int(args.host_loop))
+    build_ms = 1e3 * (time.perf_counter() - tb)
+    nnz, n_slots = h.nnz, h.n_slots
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(t, prec, src, bb, xx):
+        repart.update_values_packed(h, src[t % draws])
+        return repart.solve(h, bb, xx, tol=1e-9, precision=prec)
+
+    def launches(prec, info):
+        per_iter = 3
+        solve = 1 + 3 * info["iterations"] + (2 if prec == "mixed" else 1) * info["passes"]
+        return 2 + solve  # permutation + Jacobi diagonal
+
+    results = {}
+    clocks = {}
+    precs = [args.only] if args.only else ["fp64", "mixed"]
+    head = args.only or args.precision
+    for prec in precs:
+        for t in range(args.warmup):
+            info = step(t, prec, stg_dev, b, x)
+            assert info["status"] == 0, info
+        barrier()
+        sampler = Clocks(gpu_id)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(stream)
+        for t in range(args.steps):
+            infos.append(step(args.warmup + t, prec, stg_dev, b, x))
+        e1.record(stream)
+        barrier()
+        clocks[prec] = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        bad = [i for i in infos if i["status"] != 0]
+        results[prec] = {
+            "ms_per_step": ms / (args.steps * world),
+            "ms_per_step_per_replica": ms / args.steps,
+            "iterations_mean": statistics.mean(i["iterations"] for i in infos),
+            "outer_mean": statistics.mean(i["outer_iterations"] for i in infos),
+            "max_rel_residual": max(i["rel_residual"] for i in infos),
+            "not_converged_steps": len(bad),
+            "gpu_launches": sum(launches(prec, i) for i in infos),
+        }
+
+    # kernel durations (CUDA events on the launching stream, same kernels as the graph runs)
+    kern = {}
+    for prec in precs:
+        kk = [repart.profile_iteration(h, b, prec, iters=20) for _ in range(2)]
+        kern[prec] = kk[-1]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    reps = 10
+    for t in range(reps):
+        repart.update_values_packed(h, stg_dev[t % draws])
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    upd_ms = ev[0].elapsed_time(ev[1]) / reps
+
+    def spmv_bytes(prec):
+        return (12 * nnz + 4 * (n + 1) + 16 * n) if prec == "fp64" else (8 * nnz + 4 * (n + 1) + 8 * n)
+
+    def gbs(bytes_, ms):
+        return bytes_ / (ms * 1e-3) / 1e9
+
+    upd_bytes = 20 * nnz + 4 * nnz + 20 * n  # idx + gather + FP64 write + FP32 write; diag read + 2 writes
+    roof = {"bound": "hbm", "kernel": f"k_it_spmv<{'double' if head == 'fp64' else 'float'}>",
+            "achieved": round(gbs(spmv_bytes(head), kern[head]["spmv"]), 1), "peak": hbm_peak, "unit": "GB/s",
+            "peak_kind": peak_kind}
+    roof["frac"] = round(roof["achieved"] / hbm_peak, 4)
+    roof["traffic"] = None
+    roof["algorithmic_bytes"] = spmv_bytes(head)
+    roof["ms_per_launch"] = kern[head]["spmv"]
+    other = [p for p in precs if p != head]
+    kernels = {}
+    for prec in precs:
+        w = 8 if prec == "fp64" else 4
+        kb = {"spmv": spmv_bytes(prec), "resid": 4 * w * n, "xp": 6 * w * n}
+        kernels[prec] = {k: {"ms": round(kern[prec][k], 5), "GB/s": round(gbs(kb[k], kern[prec][k]), 1),
+                             "frac": round(gbs(kb[k], kern[prec][k]) / hbm_peak, 4)} for k in kb}
+    kernels["update"] = {"ms": round(upd_ms, 4), "GB/s": round(gbs(upd_bytes, upd_ms), 1),
+                         "frac": round(gbs(upd_bytes, upd_ms) / hbm_peak, 4)}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        stg_pin = [torch.from_numpy(s).pin_memory() for s in stg_host]
+        b_pin = torch.from_numpy(b_np).pin_memory()
+        x_pin = torch.zeros(n, dtype=torch.float64).pin_memory()
+        for t in range(max(1, args.warmup)):
+            step(t, head, stg_pin, b_pin, x_pin)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(args.steps):
+            info = step(args.warmup + t, head, stg_pin, b_pin, x_pin)
+            assert info["status"] == 0, info
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([ems], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = {"value": round(ems / (args.steps * world), 3), "unit": "ms/time-step",
+               "h2d_bytes_per_step": 8 * n_slots + 8 * n, "d2h_bytes_per_step": 8 * n,
+               "path": "rp_update_values_packed + rp_solve with pinned host buffers"}
+        del stg_pin
+
+    # parity spot check of the last solve against the oracle SpMV is in the tests; here: residual report
+    h.close()
+    del stg_dev
+    torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and "fp64" in results:
+        seeds = [100 + ((args.warmup + args.steps - 1) % draws)]
+        cnt = [int(round(results["fp64"]["iterations_mean"]))]
+        try:
+            smp = run_oracle_subprocess(args.workload, seeds, 8, cnt)
+            s0 = smp[0]
+            cpu = {"value": round(s0["ms"], 1), "unit": "ms/time-step", "cores": 1, "kind": "oracle",
+                   "precision": "fp64",
+                   "sample": f"one value update + FP64 Jacobi-PCG with 0 and 8 iterations on the full workload "
+                             f"(single thread, {s0['sample_s']:.1f} s), per-iteration cost scaled to "
+                             f"{cnt[0]} iterations (the GPU FP64 mean on the same systems)",
+                   "update_ms": round(s0["update_ms"], 1), "iter_ms": round(s0["iter_ms"], 1)}
+        except Exception as exc:  # report, do not hide
+            cpu = {"value": None, "error": str(exc)[-300:]}
+
+    if rank != 0:
+        return None
+    headr = results[head]
+    line = {
+        "metric": METRIC, "value": round(headr["ms_per_step"], 3), "unit": "ms/time-step", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(headr["ms_per_step"], 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-in-f64" if head == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "headline": head,
+                   "n_rows": n, "nnz": nnz, "draws_cycled": draws, "l2": "inputs larger than L2, no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "fp64_ms_per_step": round(results["fp64"]["ms_per_step"], 3) if "fp64" in results else None,
+        "mixed_ms_per_step": round(results["mixed"]["ms_per_step"], 3) if "mixed" in results else None,
+        "per_precision": results, "kernels": kernels, "roofline": roof,
+        "roofline_other_spmv": {o: {"achieved": round(gbs(spmv_bytes(o), kern[o]["spmv"]), 1),
+                                    "frac": round(gbs(spmv_bytes(o), kern[o]["spmv"]) / hbm_peak, 4)} for o in other},
+        "map_build_ms": round(build_ms, 1), "input_setup_s": round(setup_s, 1),
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": results[head]["gpu_launches"],
+        "clocks": clocks[head], "clocks_other": {o: clocks[o] for o in other},
+    }
+    return line
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    draws = max(1, min(args.draws, args.steps + args.warmup))
+    seeds_all = [100 + (t % draws) for t in range(args.warmup + args.steps)]
+    counts = oracle_counts(args.workload, seeds_all)
+    if any(c is None for c in counts):
+        return {"impl": "reference", "unavailable": "no oracle iteration counts for this workload "
+                                                     "(tests/golden/make_iteration_counts.py)"}
+    t0 = time.time()
+    smp = run_oracle_subprocess(args.workload, seeds_all, 4, counts, timeout=3600)
+    timed = smp[args.warmup:]
+    ms = statistics.mean(s["ms"] for s in timed)
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms/time-step", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "headline": "fp64 oracle"},
+        "cpu_baseline": {"value": round(ms, 1), "unit": "ms/time-step", "cores": 1, "kind": "oracle",
+                         "sample": "per step: one value update + FP64 Jacobi-PCG with 0 and 4 iterations on the "
+                                   "full workload (single thread), per-iteration cost scaled to the oracle's own "
+                                   "iteration count for that draw (tests/golden/iteration_counts.json)"},
+        "e2e": {"value": round(ms, 1), "unit": "ms/time-step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(time.time() - t0, 1),
+    }
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        a = json.loads(args.oracle_sample)
+        print(json.dumps(oracle_sample(a["workload"], a["seeds"], a["iters"], a["counts"])))
+        return
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line))
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -87,6 +87,11 @@ typedef struct rp_options {
   int32_t device;         /* CUDA device ordinal (-1: current device)             */
   double inner_tol;       /* relative tolerance of the FP32 inner solve           */
   int64_t spin_limit;     /* iteration limit of every device-side wait            */
+  int32_t host_loop;      /* 1: rp_solve launches the same kernels from the host,
+                             reading the control block after every iteration
+                             (slow; for profilers that cannot look inside
+                             graphs with conditional nodes)                       */
+  int32_t reserved;
 } rp_options;
 
 /* Defaults: n_parts 1, general (non-symmetric) storage, FP32 copy on,
@@ -159,6 +164,7 @@ typedef struct rp_solve_info {
   int32_t iterations;       /* PCG iterations (FP32 inner ones when mixed)   */
   int32_t outer_iterations; /* refinement steps (mixed)                      */
   int32_t restarts;         /* residual replacements                         */
+  int32_t passes;           /* FP64 residual passes (b - A x) of the solve   */
   double rel_residual;      /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
 } rp_solve_info;
 

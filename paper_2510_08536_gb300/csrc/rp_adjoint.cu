@@ -70,7 +70,7 @@ extern "C" rp_status rp_solve_adjoint(rp_handle* h, const double* g, double* lam
   if (!(tol >= 0.0)) return fail(RP_EINVAL, "tol must be >= 0");
   if (h->n_parts != 1) return fail(RP_EUNSUPPORTED, "adjoint solve needs n_parts == 1");
   if (h->n == 0) {
-    if (info) *info = rp_solve_info{RP_OK, 0, 0, 0, 0.0};
+    if (info) *info = rp_solve_info{RP_OK, 0, 0, 0, 0, 0.0};
     return RP_OK;
   }
   cudaStream_t s = (cudaStream_t)stream;

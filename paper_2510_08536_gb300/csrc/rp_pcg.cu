@@ -15,6 +15,8 @@
 // the recursive residual passes or the iteration cap is hit, the outer one
 // by the residual pass when the true residual passes (or a cap is hit).
 // Every loop is bounded by device-side counters.
+#include <type_traits>
+
 #include "rp_common.cuh"
 
 namespace rp {
@@ -66,18 +68,53 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ row_ptr, const 
   return sum;
 }
 
+// 16-byte vectors of the streaming kernels
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int N = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int N = 2;
+};
+
+template <int E>
+__device__ __forceinline__ float& comp(float4& v) {
+  return E == 0 ? v.x : E == 1 ? v.y : E == 2 ? v.z : v.w;
+}
+template <int E>
+__device__ __forceinline__ double& comp(double2& v) {
+  return E == 0 ? v.x : v.y;
+}
+
+// apply f(element index e, element references...) to every component
+template <int W, typename F, int E = 0>
+__device__ __forceinline__ void for_each_comp(F&& f) {
+  if constexpr (E < W) {
+    f(std::integral_constant<int, E>{});
+    for_each_comp<W, F, E + 1>(static_cast<F&&>(f));
+  }
+}
+
 // K1: q = A p and (p, q); the last block forms alpha.
+// Per-thread partial sums are kept in T: the FP32 path does no per-element
+// FP64 work (GB300 runs FP64 and float<->double conversions ~70x slower
+// than FP32); one conversion per thread feeds the FP64 block reduction.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_it_spmv(IterArgs<T> a) {
   Ctl* c = a.ctl;
   if (c->stop) return;
-  double acc = 0.0;
+  T acc = T(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     T s = row_dot<T>(a.row_ptr, a.col, a.vals, a.p, i);
     a.q[i] = s;
-    acc += (double)a.p[i] * (double)s;
+    acc = fma(a.p[i], s, acc);
   }
-  double v[1] = {acc}, tot[1];
+  double v[1] = {(double)acc}, tot[1];
   if (reduce_last_block<1>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
     const double pq = tot[0];
     c->pq = pq;
@@ -100,15 +137,32 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
     return;
   }
   const T alpha = (T)c->alpha;
-  double rz = 0.0, rr = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  using V = typename Vec<T>::type;
+  constexpr int W = Vec<T>::N;
+  T rz = T(0), rr = T(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nv = a.n / W;
+  for (int64_t k = tid; k < nv; k += stride) {
+    V qv = reinterpret_cast<const V*>(a.q)[k];
+    V rv = reinterpret_cast<const V*>(a.r)[k];
+    V dv = reinterpret_cast<const V*>(a.dinv)[k];
+    for_each_comp<W>([&](auto e) {
+      constexpr int E = decltype(e)::value;
+      T ri = fma(-alpha, comp<E>(qv), comp<E>(rv));
+      comp<E>(rv) = ri;
+      rz = fma(ri, comp<E>(dv) * ri, rz);
+      rr = fma(ri, ri, rr);
+    });
+    reinterpret_cast<V*>(a.r)[k] = rv;
+  }
+  for (int64_t i = nv * W + tid; i < a.n; i += stride) {
     T ri = fma(-alpha, a.q[i], a.r[i]);
     a.r[i] = ri;
-    T zi = a.dinv[i] * ri;
-    rz += (double)ri * (double)zi;
-    rr += (double)ri * (double)ri;
+    rz = fma(ri, a.dinv[i] * ri, rz);
+    rr = fma(ri, ri, rr);
   }
-  double v[2] = {rz, rr}, tot[2];
+  double v[2] = {(double)rz, (double)rr}, tot[2];
   if (reduce_last_block<2>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
     c->iter += 1;
     c->iter_total += 1;
@@ -138,7 +192,31 @@ __global__ void __launch_bounds__(kThreads) k_it_xp(IterArgs<T> a) {
   const bool upd_p = !c->stop;
   T* x = a.xd;
   if (x == nullptr) x = reinterpret_cast<T*>(a.io->x);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  using V = typename Vec<T>::type;
+  constexpr int W = Vec<T>::N;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // the caller's x may not be 16-byte aligned: vectorise only when it is
+  const int64_t nv = (reinterpret_cast<uintptr_t>(x) & 15) ? 0 : a.n / W;
+  for (int64_t k = tid; k < nv; k += stride) {
+    V pv = reinterpret_cast<const V*>(a.p)[k];
+    V xv = reinterpret_cast<const V*>(x)[k];
+    for_each_comp<W>([&](auto e) {
+      constexpr int E = decltype(e)::value;
+      comp<E>(xv) = fma(alpha, comp<E>(pv), comp<E>(xv));
+    });
+    reinterpret_cast<V*>(x)[k] = xv;
+    if (upd_p) {
+      V rv = reinterpret_cast<const V*>(a.r)[k];
+      V dv = reinterpret_cast<const V*>(a.dinv)[k];
+      for_each_comp<W>([&](auto e) {
+        constexpr int E = decltype(e)::value;
+        comp<E>(pv) = fma(beta, comp<E>(pv), comp<E>(dv) * comp<E>(rv));
+      });
+      reinterpret_cast<V*>(a.p)[k] = pv;
+    }
+  }
+  for (int64_t i = nv * W + tid; i < a.n; i += stride) {
     T pi = a.p[i];
     x[i] = fma(alpha, pi, x[i]);
     if (upd_p) a.p[i] = fma(beta, pi, a.dinv[i] * a.r[i]);
@@ -474,14 +552,72 @@ rp_status read_info(rp_handle* h, rp_solve_info* info, cudaStream_t s) {
   info->iterations = c.iter_total;
   info->outer_iterations = c.outer;
   info->restarts = c.restarts;
+  info->passes = c.pass;
   info->rel_residual = c.bb > 0.0 ? sqrt(c.rr / c.bb) : 0.0;
+  return RP_OK;
+}
+
+// The kernel sequence of the solve graph, launched from the host: the
+// control block is read back after every residual pass and every iteration.
+rp_status host_loop_solve(rp_handle* h, bool mixed, const double* vals, const double* dinv, cudaStream_t s) {
+  ResArgs ra{};
+  ra.n = h->n;
+  ra.row_ptr = h->row_ptr;
+  ra.col = h->col_idx;
+  ra.vals = vals;
+  ra.dinv = dinv;
+  ra.r = h->r;
+  ra.p = h->p;
+  ra.dinv32 = h->dinv32;
+  ra.r32 = h->r32;
+  ra.p32 = h->p32;
+  ra.d32 = h->d32;
+  ra.ctl = h->ctl;
+  ra.io = h->io;
+  ra.partials = h->partials;
+  ra.in_graph = 0;
+  IterArgs<double> a64{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
+                       h->ctl, h->io, h->partials, 0, 0};
+  IterArgs<float> a32{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
+                      h->ctl, h->io, h->partials, 0, 0};
+  CorrectArgs ca{h->n, h->d32, h->ctl, h->io};
+  Ctl c;
+  auto read = [&]() -> rp_status {
+    RP_TRY_CUDA(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    RP_TRY_CUDA(cudaStreamSynchronize(s));
+    return RP_OK;
+  };
+  // same bounds as the graph: passes and iterations are capped on the device
+  for (;;) {
+    if (mixed) k_res_mixed<<<h->grid, kThreads, 0, s>>>(ra);
+    else k_res64<<<h->grid, kThreads, 0, s>>>(ra);
+    RP_TRY_CUDA(cudaGetLastError());
+    RP_TRY(read());
+    const bool go = !c.stop;
+    while (!c.stop) {
+      if (mixed) {
+        k_it_spmv<float><<<h->grid, kThreads, 0, s>>>(a32);
+        k_it_resid<float><<<h->grid, kThreads, 0, s>>>(a32);
+        k_it_xp<float><<<h->grid, kThreads, 0, s>>>(a32);
+      } else {
+        k_it_spmv<double><<<h->grid, kThreads, 0, s>>>(a64);
+        k_it_resid<double><<<h->grid, kThreads, 0, s>>>(a64);
+        k_it_xp<double><<<h->grid, kThreads, 0, s>>>(a64);
+      }
+      RP_TRY_CUDA(cudaGetLastError());
+      RP_TRY(read());
+    }
+    if (mixed) k_correct<<<h->grid, kThreads, 0, s>>>(ca);
+    if (!go) break;
+  }
+  RP_TRY_CUDA(cudaGetLastError());
   return RP_OK;
 }
 
 rp_status solve_common(rp_handle* h, bool mixed, const double* vals, const double* dinv, cudaGraphExec_t* slot,
                        const double* b, double* x, double tol, int32_t x_is_guess, int32_t where,
                        rp_solve_info* info, cudaStream_t s) {
-  if (!*slot) RP_TRY(build_solve_graph(h, mixed, vals, dinv, slot));
+  if (!*slot && !h->opts.host_loop) RP_TRY(build_solve_graph(h, mixed, vals, dinv, slot));
   const double* bd = b;
   double* xd = x;
   if (where == RP_MEM_HOST) {
@@ -492,7 +628,13 @@ rp_status solve_common(rp_handle* h, bool mixed, const double* vals, const doubl
     bd = h->b_host_stage;
     xd = h->x_host_stage;
   }
-  RP_TRY(launch_solve(h, *slot, bd, xd, tol, !x_is_guess, h->opts.max_iter, info, s));
+  if (h->opts.host_loop) {
+    k_setup<<<1, 1, 0, s>>>(h->ctl, h->io, bd, xd, tol, h->opts.inner_tol, x_is_guess ? 0 : 1, h->opts.max_iter,
+                            h->opts.max_restarts, h->opts.max_outer);
+    RP_TRY(host_loop_solve(h, mixed, vals, dinv, s));
+  } else {
+    RP_TRY(launch_solve(h, *slot, bd, xd, tol, !x_is_guess, h->opts.max_iter, info, s));
+  }
   if (where == RP_MEM_HOST) RP_TRY_CUDA(cudaMemcpyAsync(x, h->x_host_stage, 8 * h->n, cudaMemcpyDeviceToHost, s));
   if (info) {
     RP_TRY(read_info(h, info, s));
@@ -514,7 +656,7 @@ extern "C" rp_status rp_solve(rp_handle* h, const double* b, double* x, double t
   if (precision != RP_FP64 && precision != RP_MIXED) return fail(RP_EINVAL, "precision must be RP_FP64 or RP_MIXED");
   if (precision == RP_MIXED && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
   if (h->n == 0) {
-    if (info) *info = rp_solve_info{RP_OK, 0, 0, 0, 0.0};
+    if (info) *info = rp_solve_info{RP_OK, 0, 0, 0, 0, 0.0};
     return RP_OK;
   }
   cudaStream_t s = (cudaStream_t)stream;

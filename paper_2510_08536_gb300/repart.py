@@ -38,12 +38,13 @@ class Options(ctypes.Structure):
                 ("want_fp32", ctypes.c_int32), ("want_transpose", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("inner_tol", ctypes.c_double), ("spin_limit", ctypes.c_int64)]
+                ("inner_tol", ctypes.c_double), ("spin_limit", ctypes.c_int64),
+                ("host_loop", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
-                ("outer_iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("outer_iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double)]
 
     def as_dict(self):

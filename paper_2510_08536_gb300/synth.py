@@ -333,6 +333,8 @@ WORKLOADS = {
     "update_128": dict(n=(128, 128, 128), p=(4, 4, 4), sigma=0.5),
     "mixed_256": dict(n=(256, 256, 256), p=(8, 4, 4), sigma=1.0),
     "adjoint_128": dict(n=(128, 128, 128), p=(4, 4, 4), sigma=0.5),
+    # profiling size: every pass larger than L2, a few GB on the device
+    "profile_192": dict(n=(192, 192, 192), p=(3, 3, 3), sigma=1.0),
 }
 
 

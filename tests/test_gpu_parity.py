@@ -249,3 +249,20 @@ def test_adjoint_and_gradients(symmetric):
     np.testing.assert_allclose(gf.cpu().numpy(), O.face_grad_ldu(c.mesh.ranks, lam_np, x.cpu().numpy()),
                                rtol=1e-14, atol=0)
     h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_loop_matches_graph(precision):
+    """The profiler-friendly host-driven loop runs the graph's kernels in the same order."""
+    c = Case((20, 18, 16), (2, 2, 2), sigma=1.0, oracle_map=False)
+    outs = []
+    for host_loop in (0, 1):
+        h = repart.build_repartition(c.mesh.ranks, host_loop=host_loop)
+        repart.update_values_packed(h, _t(c.staging))
+        x = torch.zeros(c.mesh.n_cells, dtype=torch.float64, device=DEV)
+        info = repart.solve(h, _t(c.b), x, tol=1e-9, precision=precision)
+        assert info["status"] == 0
+        outs.append((x.cpu(), info))
+        h.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
