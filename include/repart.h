@@ -159,6 +159,25 @@ rp_status rp_get_values(const rp_handle* h, const double** vals, const float** v
  * handle's reduction scratch. Asynchronous. */
 rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* xy, void* stream);
 
+/* Allocation-free SpMV: y = A x and, if xy is not NULL, *xy = x.y, for a
+ * caller-owned CSR matrix (row_ptr[n+1] from 0, col_idx, vals, all device
+ * pointers, like the views of rp_get_part_map / rp_get_values). The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code whose device memory is owned by a host framework's
+ * pool, code running while a stream is being captured, and code that must
+ * not allocate after start-up -- and who therefore cannot create a handle.
+ * It allocates nothing (no cudaMalloc/cudaFree, no allocating library
+ * call): its reduction scratch is a static device array of 64 KiB + 256 B,
+ * which every GPU that loads the library holds until the process exits.
+ * Limit: n <= 16,777,216 rows (n above it returns RP_ERANGE, no device
+ * work). The first call on a device looks up the array's device address
+ * with that device current; make that first call before any stream
+ * capture. All calls on a device share the array: calls whose work overlaps
+ * on the GPU (different streams, no ordering) race and give wrong x.y. y is
+ * the same per row as rp_spmv's; x.y agrees to rounding. Asynchronous. */
+rp_status rp_spmv_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
+                          const double* x, double* y, double* xy, void* stream);
+
 typedef struct rp_solve_info {
   int32_t status;           /* RP_OK, RP_NOT_CONVERGED or RP_BREAKDOWN       */
   int32_t iterations;       /* PCG iterations (FP32 inner ones when mixed)   */

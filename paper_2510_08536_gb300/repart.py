@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rp_update_values": (i32, [vp, vp, vp, vp, vp, i32, vp]),
         "rp_get_values": (i32, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "rp_spmv": (i32, [vp, vp, vp, vp, vp]),
+        "rp_spmv_noalloc": (i32, [i64, vp, vp, vp, vp, vp, vp, vp]),
         "rp_solve": (i32, [vp, vp, vp, dbl, i32, i32, i32, ctypes.POINTER(SolveInfo), vp]),
         "rp_solve_adjoint": (i32, [vp, vp, vp, dbl, ctypes.POINTER(SolveInfo), vp]),
         "rp_profile_iteration": (i32, [vp, vp, i32, i32, ctypes.POINTER(ctypes.c_float), vp]),
@@ -243,6 +244,13 @@ def spmv(h: Handle, x, y, xy=None, stream=None):
     _check(load().rp_spmv(h.ptr, _ptr(x), _ptr(y), _ptr(xy), _stream(stream)), "rp_spmv")
 
 
+def spmv_noalloc(n: int, row_ptr, col_idx, vals, x, y, xy=None, stream=None):
+    """rp_spmv_noalloc: the same product for a caller-owned CSR matrix, with no
+    device allocation (for callers that cannot allocate device memory)."""
+    _check(load().rp_spmv_noalloc(int(n), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(x), _ptr(y), _ptr(xy),
+                                  _stream(stream)), "rp_spmv_noalloc")
+
+
 def solve(h: Handle, b, x, tol: float = 1e-9, precision: str = "fp64", x_is_guess: bool = False,
           stream=None, wait: bool = True, raise_on_status: bool = False):
     """rp_solve; returns the SolveInfo as a dict when ``wait`` (else None)."""
@@ -287,4 +295,4 @@ class Exports:
     names: tuple = ("rp_default_options", "rp_build_repartition", "rp_get_part_map", "rp_get_sizes",
                     "rp_update_values_packed", "rp_update_values", "rp_get_values", "rp_spmv", "rp_solve",
                     "rp_solve_adjoint", "rp_profile_iteration", "rp_entry_grad", "rp_face_grad", "rp_destroy", "rp_status_str",
-                    "rp_last_error")
+                    "rp_last_error", "rp_spmv_noalloc")
