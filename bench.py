@@ -62,6 +62,7 @@ def parse():
                     help="time one precision only (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solve kernels from the host (for profilers; not a timing mode)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -192,6 +193,80 @@ def oracle_counts(workload, seeds):
         fill = int(round(statistics.mean(known))) if known else None
         got = [fill if c is None else c for c in got]
     return got
+
+
+# ---------------------------------------------------------------- batched form
+
+
+def run_batch(args, dev, steps, warmup, loop_steps=1):
+    """256 uneven independent systems (8k-300k cells, aspect 1-4, lognormal(0, 0.5)):
+    update + solve of all of them in one persistent launch per step, FP64 and mixed,
+    launch shape autotuned; compared with a loop of single-system rp_solve calls."""
+    import torch
+
+    from paper_2510_08536_gb300 import repart, synth
+    t0 = time.time()
+    B = synth.Batch(256, 8000, 300000, seed=0)
+    draws = 2
+    stg = [torch.from_numpy(B.staging(0.5, 100 + t)).to(dev) for t in range(draws)]
+    b = torch.from_numpy(B.rhs(0)).to(dev)
+    x = torch.zeros(B.n_rows, dtype=torch.float64, device=dev)
+    setup_s = time.time() - t0
+    h = repart.batch_build(B.systems)
+    out = {"workload": "256 independent box systems, cells log-uniform in [8k, 300k], aspect ratios U[1,4], "
+                       "lognormal(0,0.5) faces, Dirichlet at x=0, rhs U[-1,1], rel. residual 1e-9 from x=0",
+           "systems": len(B.systems), "rows": B.n_rows, "nnz": h.nnz, "input_setup_s": round(setup_s, 1)}
+    c, t, ms = repart.batch_autotune(h, stg[0], b, x, tol=1e-9, precision="fp64")
+    out["autotuned"] = {"cluster": c, "threads": t, "tuning_ms": round(ms, 2)}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "mixed"):
+        for i in range(warmup):
+            repart.batch_update_solve(h, stg[i % draws], b, x, 1e-9, prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos_all = []
+        e0.record(stream)
+        for i in range(steps):
+            infos_all.append(repart.batch_update_solve(h, stg[(warmup + i) % draws], b, x, 1e-9, prec))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        bad = sum(1 for infos in infos_all for i in infos if i["status"] != 0)
+        iters = [sum(i["iterations"] for i in infos) for infos in infos_all]
+        out[prec] = {"ms_per_step": round(ms, 3), "not_converged_systems": bad,
+                     "iterations_sum_mean": statistics.mean(iters),
+                     "max_rel_residual": max(i["rel_residual"] for infos in infos_all for i in infos)}
+    h.close()
+    # baseline: one handle per system, rp_update_values_packed + rp_solve in a loop
+    handles = [repart.build_repartition([s]) for s in B.systems]
+    offs, so = [], 0
+    for m in B.meshes:
+        offs.append((so, so + m.staging_size()))
+        so += m.staging_size()
+    roffs, ro = [], 0
+    for m in B.meshes:
+        roffs.append((ro, ro + m.n_cells))
+        ro += m.n_cells
+
+    def loop_step(src):
+        for hh, (a0, a1), (r0, r1) in zip(handles, offs, roffs):
+            repart.update_values_packed(hh, src[a0:a1])
+            repart.solve(hh, b[r0:r1], x[r0:r1], tol=1e-9, wait=False)
+
+    loop_step(stg[0])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(loop_steps):
+        loop_step(stg[(1 + i) % draws])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["loop_of_single_solves_fp64_ms_per_step"] = round(e0.elapsed_time(e1) / loop_steps, 3)
+    for hh in handles:
+        hh.close()
+    del stg
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- ours
@@ -356,6 +431,10 @@ def run_ours(args):
     del stg_dev
     torch.cuda.empty_cache()
 
+    batched = None
+    if not args.no_batch:
+        batched = run_batch(args, dev, steps=max(1, min(args.steps, 5)), warmup=max(1, min(args.warmup, 2)))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and "fp64" in results:
         seeds = [100 + ((args.warmup + args.steps - 1) % draws)]
@@ -389,7 +468,7 @@ def run_ours(args):
         "roofline_other_spmv": {o: {"achieved": round(gbs(spmv_bytes(o), kern[o]["spmv"]), 1),
                                     "frac": round(gbs(spmv_bytes(o), kern[o]["spmv"]) / hbm_peak, 4)} for o in other},
         "map_build_ms": round(build_ms, 1), "input_setup_s": round(setup_s, 1),
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": results[head]["gpu_launches"],
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": results[head]["gpu_launches"], "batched": batched,
         "clocks": clocks[head], "clocks_other": {o: clocks[o] for o in other},
     }
     return line

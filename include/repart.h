@@ -199,6 +199,39 @@ typedef struct rp_solve_info {
 rp_status rp_solve(rp_handle* h, const double* b, double* x, double tol, int32_t precision,
                    int32_t x_is_guess, int32_t where, rp_solve_info* info, void* stream);
 
+/* ---- Batched form: many independent systems in one persistent launch ----
+ * Each system is one LDU matrix without interfaces (n_iface = 0); system s
+ * becomes GPU part s (n_parts = count, alpha = 1, Sec. 3). Rows, buffers and
+ * vectors of the systems follow each other in system order.
+ * rp_batch_build: as rp_build_repartition with n_parts = count. Errors as
+ * there, plus RP_EINVAL if a system has interface entries. Blocks the host. */
+rp_status rp_batch_build(const rp_ldu_desc* systems, int32_t count, const rp_options* opts, rp_handle** out);
+
+/* One batched time step: the value update of every system from `buffer`
+ * (all systems' continuous buffers concatenated; where = host or device)
+ * and the solve of every system to its own ||b_s - A_s x_s|| <= tol ||b_s||
+ * from x_s = 0 (precision RP_FP64 or RP_MIXED), all in ONE persistent kernel
+ * launched from a CUDA graph (instantiated on first use per precision).
+ * b and x are device pointers (n_rows doubles, system order). Thread-block
+ * clusters act as teams that take systems largest first from a device work
+ * queue; a team's CTAs synchronise with cluster barriers only. If info is not
+ * NULL (host array of count entries) the call waits and fills it, returning
+ * the first non-OK system status. */
+rp_status rp_batch_update_solve(rp_handle* h, const double* buffer, int32_t where, const double* b, double* x,
+                                double tol, int32_t precision, rp_solve_info* info, void* stream);
+
+/* Launch shape of the batched kernel: cluster size (1, 2, 4, 8, 16 CTAs per
+ * team) and threads per CTA (multiple of 32, <= 512). RP_EUNSUPPORTED if
+ * the shape cannot be scheduled. Default 8 x 512. */
+rp_status rp_batch_set_config(rp_handle* h, int32_t cluster, int32_t threads);
+
+/* Autotuner: times rp_batch_update_solve (device buffer, precision) for every
+ * cluster size in {2, 4, 8, 16} and CTA size in {128, 256, 512}, keeps the
+ * fastest shape in the handle and reports it. Overwrites x. Blocks. */
+rp_status rp_batch_autotune(rp_handle* h, const double* buffer, const double* b, double* x, double tol,
+                            int32_t precision, int32_t* best_cluster, int32_t* best_threads, float* best_ms,
+                            void* stream);
+
 /* Kernel timing: starts a CG run from x = 0 on right-hand side b (device)
  * with the current values and launches `iters` iterations of the three
  * iteration kernels of `precision` on the stream (outside any graph, with no

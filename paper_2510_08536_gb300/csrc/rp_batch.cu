@@ -1,0 +1,562 @@
+// Batched form: many independent systems (each one CPU rank's LDU matrix,
+// its own GPU part) updated and solved in ONE persistent launch.
+//
+// The grid is launched as thread-block clusters of T CTAs. A cluster is a
+// team: its leader takes the next system from a work queue ordered by size
+// (largest first), the team runs the value update and the whole Jacobi-PCG
+// (FP64, or FP32-inner / FP64-outer refinement) of that system, writes the
+// system's status, and takes the next one. Teams never wait on each other.
+//
+// Inside a team the rows of the system are split into T contiguous blocks.
+// The two reductions of each CG iteration go through distributed shared
+// memory: every CTA publishes its partial sums in its own shared memory and,
+// after a hardware cluster barrier, every CTA reads all T partials in rank
+// order, so all CTAs hold bit-identical scalars and take identical control
+// decisions (loop trip counts match, every barrier is reached by all).
+// Three cluster barriers per iteration: after the p update (the SpMV reads
+// neighbour rows of other CTAs) and one per reduction. Vectors written inside
+// the kernel are read with plain (coherent) loads; the barriers carry
+// release/acquire semantics at cluster scope. Every loop is capped by the
+// iteration limits; there is no spin wait.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <numeric>
+
+#include "rp_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rp {
+
+
+
+namespace {
+
+constexpr int kBatchMaxThreads = 512;
+
+// Block-wide sum of NV values, then cluster-wide through DSMEM; every thread
+// of every CTA returns the same totals.
+template <int NV>
+__device__ __forceinline__ void team_sum(double (&v)[NV], double (&tot)[NV], cg::cluster_group& cl,
+                                         double (*spart)[kMaxPartials], double (*swarp)[32], int& parity) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = warp_sum(v[i]);
+    if (lane == 0) swarp[i][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = lane < nw ? swarp[i][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) spart[parity][i] = s;
+    }
+  }
+  cl.sync();
+  const unsigned T = cl.num_blocks();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double t = 0.0;
+    for (unsigned r = 0; r < T; ++r) t += *cl.map_shared_rank(&spart[parity][i], r);
+    tot[i] = t;
+  }
+  parity ^= 1;
+}
+
+template <typename T>
+__device__ __forceinline__ T row_dot_coherent(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                              const T* vals, const T* x, int64_t i) {
+  const int s = rp[i], e = rp[i + 1];
+  T sum = T(0);
+  for (int j = s; j < e; ++j) sum = fma(vals[j], x[col[j]], sum);
+  return sum;
+}
+
+}  // namespace
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned T = cl.num_blocks();
+  const unsigned me = cl.block_rank();
+  __shared__ double spart[2][kMaxPartials];
+  __shared__ double swarp[kMaxPartials][32];
+  __shared__ int s_next;
+  int parity = 0;
+  const double tol = a.io->tol;
+  const double* __restrict__ bufall = a.io->buf;
+  const double* __restrict__ ball = a.io->b;
+  double* __restrict__ xall = a.io->x;
+
+  for (;;) {
+    if (me == 0 && threadIdx.x == 0) s_next = (int)atomicAdd(a.queue, 1u);
+    cl.sync();
+    const int k = *cl.map_shared_rank(&s_next, 0);
+    cl.sync();
+    if (k >= a.n_sys) break;
+    const int s = a.order[k];
+    const int64_t ro = a.row_off[s];
+    const int64_t n = a.row_off[s + 1] - ro;
+    const int32_t* __restrict__ rp = a.row_ptr + ro + s;
+    const int64_t no = a.nnz_off[s];
+    const int32_t* __restrict__ col = a.col + no;
+    const int32_t* __restrict__ src = a.src_of + no;
+    const double* __restrict__ buf = bufall + a.buf_off[s];
+    double* vals = a.vals + no;
+    float* vals32 = MIXED ? a.vals32 + no : nullptr;
+    double* dinv = a.dinv + ro;
+    float* dinv32 = MIXED ? a.dinv32 + ro : nullptr;
+    const double* b = ball + ro;
+    double* x = xall + ro;
+    const int64_t chunk = (n + T - 1) / T;
+    const int64_t i0 = min((int64_t)me * chunk, n), i1 = min(i0 + chunk, n);
+    const int tid = threadIdx.x, nth = blockDim.x;
+
+    // value update of this CTA's rows (Sec. 3 update procedure) and the Jacobi diagonal
+    for (int64_t pp = rp[i0] + tid; pp < rp[i1]; pp += nth) {
+      const double v = buf[src[pp]];
+      vals[pp] = v;
+      if (MIXED) vals32[pp] = (float)v;
+    }
+    for (int64_t i = i0 + tid; i < i1; i += nth) {
+      const double d = buf[i];  // diagonal block leads the system's buffer
+      dinv[i] = 1.0 / d;
+      if (MIXED) dinv32[i] = 1.0f / (float)d;
+    }
+    __syncthreads();
+
+    int status = -1, iters = 0, passes = 0, restarts = 0, outer = 0;
+    double bb = 0.0, thresh = 0.0, rr = 0.0;
+
+    if (!MIXED) {
+      double* r = a.r + ro;
+      double* p = a.p + ro;
+      double* q = a.q + ro;
+      double rz = 0.0;
+      for (;;) {
+        // residual pass: r = b - A x (x = 0 on the first pass), p = z = D^-1 r
+        double v3[3] = {0.0, 0.0, 0.0}, t3[3];
+        for (int64_t i = i0 + tid; i < i1; i += nth) {
+          double ri;
+          if (passes == 0) {
+            ri = b[i];
+            x[i] = 0.0;
+            v3[2] = fma(ri, ri, v3[2]);
+          } else {
+            ri = b[i] - row_dot_coherent<double>(rp, col, vals, x, i);
+          }
+          r[i] = ri;
+          const double zi = dinv[i] * ri;
+          p[i] = zi;
+          v3[0] = fma(ri, zi, v3[0]);
+          v3[1] = fma(ri, ri, v3[1]);
+        }
+        team_sum<3>(v3, t3, cl, spart, swarp, parity);
+        if (passes == 0) {
+          bb = t3[2];
+          thresh = tol * tol * bb;
+        }
+        rz = t3[0];
+        rr = t3[1];
+        const bool first = passes == 0;
+        ++passes;
+        if (rr <= thresh) { status = RP_OK; break; }
+        if (status == RP_BREAKDOWN) break;
+        if (!isfinite(rr)) { status = RP_BREAKDOWN; break; }
+        if (iters >= a.max_iter || (!first && restarts >= a.max_restarts)) { status = RP_NOT_CONVERGED; break; }
+        if (!first) ++restarts;
+        // CG iterations
+        for (;;) {
+          cl.sync();  // p of every row visible to the team
+          double v1[1] = {0.0}, t1[1];
+          for (int64_t i = i0 + tid; i < i1; i += nth) {
+            const double qi = row_dot_coherent<double>(rp, col, vals, p, i);
+            q[i] = qi;
+            v1[0] = fma(p[i], qi, v1[0]);
+          }
+          team_sum<1>(v1, t1, cl, spart, swarp, parity);
+          if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; break; }
+          const double alpha = rz / t1[0];
+          double v2[2] = {0.0, 0.0}, t2[2];
+          for (int64_t i = i0 + tid; i < i1; i += nth) {
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            v2[0] = fma(ri, dinv[i] * ri, v2[0]);
+            v2[1] = fma(ri, ri, v2[1]);
+          }
+          team_sum<2>(v2, t2, cl, spart, swarp, parity);
+          ++iters;
+          rr = t2[1];
+          bool stop = false;
+          double beta = 0.0;
+          if (t2[1] <= thresh || iters >= a.max_iter) stop = true;
+          else if (!(t2[0] > 0.0) || !isfinite(t2[0])) { stop = true; status = RP_BREAKDOWN; }
+          else { beta = t2[0] / rz; rz = t2[0]; }
+          for (int64_t i = i0 + tid; i < i1; i += nth) {
+            const double pi = p[i];
+            x[i] = fma(alpha, pi, x[i]);
+            if (!stop) p[i] = fma(beta, pi, dinv[i] * r[i]);
+          }
+          if (stop) break;
+        }
+        cl.sync();  // x of every row visible before the residual pass
+      }
+    } else {
+      float* r = a.r32 + ro;
+      float* p = a.p32 + ro;
+      float* q = a.q32 + ro;
+      float* d = a.d32 + ro;
+      for (;;) {
+        // FP64 residual pass with FP64 values; FP32 copy starts the inner solve
+        double v4[4] = {0.0, 0.0, 0.0, 0.0}, t4[4];
+        float rzf = 0.f, rr32f = 0.f;
+        for (int64_t i = i0 + tid; i < i1; i += nth) {
+          double ri;
+          if (passes == 0) {
+            ri = b[i];
+            x[i] = 0.0;
+            v4[2] = fma(ri, ri, v4[2]);
+          } else {
+            ri = b[i] - row_dot_coherent<double>(rp, col, vals, x, i);
+          }
+          const float r32 = (float)ri;
+          r[i] = r32;
+          d[i] = 0.f;
+          const float z32 = dinv32[i] * r32;
+          p[i] = z32;
+          rzf = fmaf(r32, z32, rzf);
+          rr32f = fmaf(r32, r32, rr32f);
+          v4[1] = fma(ri, ri, v4[1]);
+        }
+        v4[0] = rzf;
+        v4[3] = rr32f;
+        team_sum<4>(v4, t4, cl, spart, swarp, parity);
+        if (passes == 0) {
+          bb = t4[2];
+          thresh = tol * tol * bb;
+        }
+        rr = t4[1];
+        ++passes;
+        if (rr <= thresh) { status = RP_OK; break; }
+        if (status == RP_BREAKDOWN) break;
+        if (!isfinite(rr)) { status = RP_BREAKDOWN; break; }
+        if (outer >= a.max_outer) { status = RP_NOT_CONVERGED; break; }
+        ++outer;
+        double rz = t4[0];
+        const double ithresh = a.inner_tol * a.inner_tol * t4[3];
+        int it = 0;
+        bool broke = false;
+        for (;;) {
+          cl.sync();
+          float acc = 0.f;
+          for (int64_t i = i0 + tid; i < i1; i += nth) {
+            const float qi = row_dot_coherent<float>(rp, col, vals32, p, i);
+            q[i] = qi;
+            acc = fmaf(p[i], qi, acc);
+          }
+          double v1[1] = {(double)acc}, t1[1];
+          team_sum<1>(v1, t1, cl, spart, swarp, parity);
+          if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; broke = true; break; }
+          const float alpha = (float)(rz / t1[0]);
+          float a0 = 0.f, a1 = 0.f;
+          for (int64_t i = i0 + tid; i < i1; i += nth) {
+            const float ri = fmaf(-alpha, q[i], r[i]);
+            r[i] = ri;
+            a0 = fmaf(ri, dinv32[i] * ri, a0);
+            a1 = fmaf(ri, ri, a1);
+          }
+          double v2[2] = {(double)a0, (double)a1}, t2[2];
+          team_sum<2>(v2, t2, cl, spart, swarp, parity);
+          ++it;
+          ++iters;
+          bool stop = false;
+          float beta = 0.f;
+          if (t2[1] <= ithresh || it >= a.max_iter) stop = true;
+          else if (!(t2[0] > 0.0) || !isfinite(t2[0])) { stop = true; status = RP_BREAKDOWN; broke = true; }
+          else { beta = (float)(t2[0] / rz); rz = t2[0]; }
+          for (int64_t i = i0 + tid; i < i1; i += nth) {
+            const float pi = p[i];
+            d[i] = fmaf(alpha, pi, d[i]);
+            if (!stop) p[i] = fmaf(beta, pi, dinv32[i] * r[i]);
+          }
+          if (stop) break;
+        }
+        if (!broke) {
+          for (int64_t i = i0 + tid; i < i1; i += nth) x[i] += (double)d[i];
+        }
+        cl.sync();  // x visible before the next residual pass
+      }
+    }
+    if (me == 0 && threadIdx.x == 0) {
+      rp_solve_info inf;
+      inf.status = status < 0 ? RP_NOT_CONVERGED : status;
+      inf.iterations = iters;
+      inf.outer_iterations = outer;
+      inf.restarts = restarts;
+      inf.passes = passes;
+      inf.rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+      a.info[s] = inf;
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+__global__ void k_batch_setup(BatchIO* io, const double* buf, const double* b, double* x, double tol) {
+  io->buf = buf;
+  io->b = b;
+  io->x = x;
+  io->tol = tol;
+}
+
+namespace {
+
+template <typename T>
+rp_status balloc(T** p, int64_t count) {
+  if (*p) return RP_OK;
+  if (count <= 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, (size_t)count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(RP_ENOMEM, "cudaMalloc of %lld bytes failed", (long long)(count * sizeof(T)));
+  }
+  return RP_OK;
+}
+
+void* batch_kernel(bool mixed) { return mixed ? (void*)k_batch<true> : (void*)k_batch<false>; }
+
+rp_status launch_config(rp_handle* h, bool mixed, int cluster, int threads, cudaLaunchConfig_t* cfg,
+                        cudaLaunchAttribute* attr, int* n_clusters) {
+  void* fn = batch_kernel(mixed);
+  if (cluster > 8) RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  *cfg = cudaLaunchConfig_t{};
+  cfg->blockDim = dim3((unsigned)threads);
+  cfg->gridDim = dim3((unsigned)cluster);
+  cfg->dynamicSmemBytes = 0;
+  attr->id = cudaLaunchAttributeClusterDimension;
+  attr->val.clusterDim.x = (unsigned)cluster;
+  attr->val.clusterDim.y = 1;
+  attr->val.clusterDim.z = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  int nc = 0;
+  RP_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nc, fn, cfg));
+  if (nc < 1) return fail(RP_EUNSUPPORTED, "cluster size %d with %d threads cannot be scheduled", cluster, threads);
+  *n_clusters = nc;
+  cfg->gridDim = dim3((unsigned)(nc * cluster));
+  return RP_OK;
+}
+
+rp_status build_batch_graph(rp_handle* h, bool mixed, int cluster, int threads, cudaGraphExec_t* exec) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr;
+  int nc = 0;
+  RP_TRY(launch_config(h, mixed, cluster, threads, &cfg, &attr, &nc));
+  cudaStream_t cs;
+  RP_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cfg.stream = cs;
+  BatchArgs ba = h->batch_args;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(h->batch_queue, 0, sizeof(unsigned int), cs);
+    if (mixed) cudaLaunchKernelEx(&cfg, k_batch<true>, ba);
+    else cudaLaunchKernelEx(&cfg, k_batch<false>, ba);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RP_ECUDA, "building the batch graph failed: %s", cudaGetErrorString(e));
+  }
+  return RP_OK;
+}
+
+}  // namespace
+
+rp_status batch_prepare(rp_handle* h) {
+  if (h->batch_ready) return RP_OK;
+  if (h->n_parts != h->k) return fail(RP_EINVAL, "batched solves need one system per part (n_parts == k)");
+  if (h->nl_nnz != 0) return fail(RP_EINVAL, "batched systems must be independent (no processor interfaces)");
+  const int ns = h->n_parts;
+  std::vector<int32_t> order(ns);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return h->part_nnz_off[a + 1] - h->part_nnz_off[a] > h->part_nnz_off[b + 1] - h->part_nnz_off[b];
+  });
+  int32_t* d_order = nullptr;
+  int64_t *d_ro = nullptr, *d_no = nullptr, *d_bo = nullptr;
+  RP_TRY(balloc(&d_order, ns));
+  RP_TRY(balloc(&d_ro, ns + 1));
+  RP_TRY(balloc(&d_no, ns + 1));
+  RP_TRY(balloc(&d_bo, ns + 1));
+  h->batch_order = d_order;
+  h->batch_row_off = d_ro;
+  h->batch_nnz_off = d_no;
+  h->batch_buf_off = d_bo;
+  RP_TRY_CUDA(cudaMemcpy(d_order, order.data(), 4 * ns, cudaMemcpyHostToDevice));
+  RP_TRY_CUDA(cudaMemcpy(d_ro, h->part_row_off.data(), 8 * (ns + 1), cudaMemcpyHostToDevice));
+  RP_TRY_CUDA(cudaMemcpy(d_no, h->part_nnz_off.data(), 8 * (ns + 1), cudaMemcpyHostToDevice));
+  RP_TRY_CUDA(cudaMemcpy(d_bo, h->part_buf_off.data(), 8 * (ns + 1), cudaMemcpyHostToDevice));
+  RP_TRY(balloc(&h->batch_queue, 4));
+  RP_TRY(balloc(&h->batch_info, ns));
+  RP_TRY(balloc(&h->batch_io, 1));
+  BatchArgs& a = h->batch_args;
+  a.n_sys = ns;
+  a.order = d_order;
+  a.row_off = d_ro;
+  a.nnz_off = d_no;
+  a.buf_off = d_bo;
+  a.row_ptr = h->row_ptr;
+  a.col = h->col_idx;
+  a.src_of = h->src_of;
+  a.vals = h->vals;
+  a.vals32 = h->vals32;
+  a.dinv = h->dinv;
+  a.dinv32 = h->dinv32;
+  a.r = h->r;
+  a.p = h->p;
+  a.q = h->q;
+  a.r32 = h->r32;
+  a.p32 = h->p32;
+  a.q32 = h->q32;
+  a.d32 = h->d32;
+  a.queue = h->batch_queue;
+  a.info = h->batch_info;
+  a.io = h->batch_io;
+  a.max_iter = h->opts.max_iter;
+  a.max_restarts = h->opts.max_restarts;
+  a.max_outer = h->opts.max_outer;
+  a.inner_tol = h->opts.inner_tol;
+  h->batch_ready = true;
+  return RP_OK;
+}
+
+void free_batch(rp_handle* h) {
+  void* ptrs[] = {h->batch_order, h->batch_row_off, h->batch_nnz_off, h->batch_buf_off, h->batch_queue,
+                  h->batch_info, h->batch_io};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& g : h->batch_graphs)
+    if (g) cudaGraphExecDestroy(g);
+}
+
+static rp_status batch_run(rp_handle* h, const double* buffer, int32_t where, const double* b, double* x,
+                           double tol, int32_t precision, rp_solve_info* info, cudaStream_t s) {
+  const bool mixed = precision == RP_MIXED;
+  RP_TRY(batch_prepare(h));
+  cudaGraphExec_t& ex = h->batch_graphs[mixed ? 1 : 0];
+  if (!ex) RP_TRY(build_batch_graph(h, mixed, h->batch_cluster, h->batch_threads, &ex));
+  const double* src = buffer;
+  if (where == RP_MEM_HOST) {
+    RP_TRY_CUDA(cudaMemcpyAsync(h->staging, buffer, sizeof(double) * h->n_slots, cudaMemcpyHostToDevice, s));
+    src = h->staging;
+  }
+  k_batch_setup<<<1, 1, 0, s>>>(h->batch_io, src, b, x, tol);
+  RP_TRY_CUDA(cudaGetLastError());
+  RP_TRY_CUDA(cudaGraphLaunch(ex, s));
+  if (info) {
+    RP_TRY_CUDA(cudaMemcpyAsync(info, h->batch_info, sizeof(rp_solve_info) * h->n_parts, cudaMemcpyDeviceToHost, s));
+    RP_TRY_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < h->n_parts; ++i)
+      if (info[i].status != RP_OK) return (rp_status)info[i].status;
+  }
+  return RP_OK;
+}
+
+}  // namespace rp
+
+using namespace rp;
+
+extern "C" rp_status rp_batch_build(const rp_ldu_desc* systems, int32_t count, const rp_options* opts,
+                                    rp_handle** out) {
+  if (!systems || count < 1 || !out) return fail(RP_EINVAL, "invalid argument");
+  for (int i = 0; i < count; ++i)
+    if (systems[i].n_iface != 0) return fail(RP_EINVAL, "system %d has interface entries; batched systems are independent", i);
+  rp_options o;
+  if (opts) o = *opts; else rp_default_options(&o);
+  o.n_parts = count;
+  RP_TRY(rp_build_repartition(systems, count, &o, out));
+  rp_status s = batch_prepare(*out);
+  if (s != RP_OK) {
+    rp_destroy(*out);
+    *out = nullptr;
+  }
+  return s;
+}
+
+extern "C" rp_status rp_batch_update_solve(rp_handle* h, const double* buffer, int32_t where, const double* b,
+                                           double* x, double tol, int32_t precision, rp_solve_info* info,
+                                           void* stream) {
+  if (!h || !buffer || !b || !x) return fail(RP_EINVAL, "null argument");
+  if (!(tol >= 0.0)) return fail(RP_EINVAL, "tol must be >= 0");
+  if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
+  if (precision != RP_FP64 && precision != RP_MIXED) return fail(RP_EINVAL, "precision must be RP_FP64 or RP_MIXED");
+  if (precision == RP_MIXED && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
+  return batch_run(h, buffer, where, b, x, tol, precision, info, (cudaStream_t)stream);
+}
+
+extern "C" rp_status rp_batch_set_config(rp_handle* h, int32_t cluster, int32_t threads) {
+  if (!h) return fail(RP_EINVAL, "null handle");
+  if (cluster < 1 || cluster > 16 || (cluster & (cluster - 1)))
+    return fail(RP_EINVAL, "cluster size must be 1, 2, 4, 8 or 16");
+  if (threads < 64 || threads > kBatchMaxThreads || threads % 32)
+    return fail(RP_EINVAL, "threads must be a multiple of 32 in [64, %d]", kBatchMaxThreads);
+  RP_TRY(batch_prepare(h));
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr;
+  int nc = 0;
+  RP_TRY(launch_config(h, h->want_fp32, cluster, threads, &cfg, &attr, &nc));
+  for (auto& g : h->batch_graphs)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  h->batch_cluster = cluster;
+  h->batch_threads = threads;
+  return RP_OK;
+}
+
+extern "C" rp_status rp_batch_autotune(rp_handle* h, const double* buffer, const double* b, double* x, double tol,
+                                       int32_t precision, int32_t* best_cluster, int32_t* best_threads,
+                                       float* best_ms, void* stream) {
+  if (!h || !buffer || !b || !x) return fail(RP_EINVAL, "null argument");
+  RP_TRY(batch_prepare(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int clusters[] = {2, 4, 8, 16};
+  const int threads[] = {128, 256, 512};
+  cudaEvent_t e0, e1;
+  RP_TRY_CUDA(cudaEventCreate(&e0));
+  RP_TRY_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bc = h->batch_cluster, bt = h->batch_threads;
+  for (int c : clusters)
+    for (int t : threads) {
+      if (rp_batch_set_config(h, c, t) != RP_OK) continue;
+      // one untimed run (graph build, warm caches), then one timed run
+      if (batch_run(h, buffer, RP_MEM_DEVICE, b, x, tol, precision, nullptr, s) != RP_OK) continue;
+      cudaEventRecord(e0, s);
+      if (batch_run(h, buffer, RP_MEM_DEVICE, b, x, tol, precision, nullptr, s) != RP_OK) continue;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bc = c;
+        bt = t;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  RP_TRY(rp_batch_set_config(h, bc, bt));
+  if (best_cluster) *best_cluster = bc;
+  if (best_threads) *best_threads = bt;
+  if (best_ms) *best_ms = best;
+  return RP_OK;
+}

@@ -81,6 +81,37 @@ struct Graphs {
   cudaGraphExec_t adjoint = nullptr;
 };
 
+// Per-call pointers of the batched solve (read by the captured kernel).
+struct BatchIO {
+  const double* buf;
+  const double* b;
+  double* x;
+  double tol;
+};
+
+// Arguments of the persistent batched kernel (fixed per handle).
+struct BatchArgs {
+  int32_t n_sys;
+  const int32_t* order;    // systems, largest first
+  const int64_t* row_off;  // [n_sys+1] first merged row of each system
+  const int64_t* nnz_off;  // [n_sys+1]
+  const int64_t* buf_off;  // [n_sys+1]
+  const int32_t* row_ptr;  // per-part segments (row_off[s] + s)
+  const int32_t* col;
+  const int32_t* src_of;
+  double* vals;
+  float* vals32;
+  double* dinv;
+  float* dinv32;
+  double *r, *p, *q;
+  float *r32, *p32, *q32, *d32;
+  unsigned int* queue;
+  rp_solve_info* info;  // [n_sys]
+  const BatchIO* io;
+  int32_t max_iter, max_restarts, max_outer;
+  double inner_tol;
+};
+
 }  // namespace rp
 
 // ---------------------------------------------------------------- handle
@@ -146,6 +177,17 @@ struct rp_handle {
   int grid = 0;                    // blocks of every streaming kernel
   rp::Graphs graphs;
   cudaStream_t capture_stream = nullptr;
+
+  // batched form (one system per part)
+  bool batch_ready = false;
+  int batch_cluster = 8, batch_threads = 512;  // autotuned by rp_batch_autotune
+  int32_t* batch_order = nullptr;
+  int64_t *batch_row_off = nullptr, *batch_nnz_off = nullptr, *batch_buf_off = nullptr;
+  unsigned int* batch_queue = nullptr;
+  rp_solve_info* batch_info = nullptr;
+  rp::BatchIO* batch_io = nullptr;
+  rp::BatchArgs batch_args{};
+  cudaGraphExec_t batch_graphs[2] = {nullptr, nullptr};
 };
 
 namespace rp {
@@ -161,6 +203,7 @@ inline int grid_for(const rp_handle* h, int64_t n) {
 rp_status ensure_solver_buffers(rp_handle* h);
 rp_status build_graphs(rp_handle* h);
 void free_solver(rp_handle* h);
+void free_batch(rp_handle* h);
 
 }  // namespace rp
 

@@ -462,6 +462,7 @@ static void free_handle_memory(rp_handle* h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_solver(h);
+  free_batch(h);
 }
 
 extern "C" void rp_destroy(rp_handle* h) {

@@ -79,6 +79,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rp_get_values": (i32, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "rp_spmv": (i32, [vp, vp, vp, vp, vp]),
         "rp_spmv_noalloc": (i32, [i64, vp, vp, vp, vp, vp, vp, vp]),
+        "rp_batch_build": (i32, [ctypes.POINTER(LduDesc), i32, ctypes.POINTER(Options), ctypes.POINTER(vp)]),
+        "rp_batch_update_solve": (i32, [vp, vp, i32, vp, vp, dbl, i32, ctypes.POINTER(SolveInfo), vp]),
+        "rp_batch_set_config": (i32, [vp, i32, i32]),
+        "rp_batch_autotune": (i32, [vp, vp, vp, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                    ctypes.POINTER(ctypes.c_float), vp]),
         "rp_solve": (i32, [vp, vp, vp, dbl, i32, i32, i32, ctypes.POINTER(SolveInfo), vp]),
         "rp_solve_adjoint": (i32, [vp, vp, vp, dbl, ctypes.POINTER(SolveInfo), vp]),
         "rp_profile_iteration": (i32, [vp, vp, i32, i32, ctypes.POINTER(ctypes.c_float), vp]),
@@ -244,6 +249,52 @@ def spmv(h: Handle, x, y, xy=None, stream=None):
     _check(load().rp_spmv(h.ptr, _ptr(x), _ptr(y), _ptr(xy), _stream(stream)), "rp_spmv")
 
 
+def batch_build(systems, want_fp32: bool = True, **opts) -> Handle:
+    """rp_batch_build: one handle holding every independent system (one part each)."""
+    lib = load()
+    k = len(systems)
+    descs = (LduDesc * k)()
+    keep = []
+    for i, r in enumerate(systems):
+        lo = np.ascontiguousarray(r.lower_addr, dtype=np.int32)
+        up = np.ascontiguousarray(r.upper_addr, dtype=np.int32)
+        keep.append((lo, up))
+        descs[i] = LduDesc(int(r.n_cells), lo.shape[0], lo.ctypes.data_as(_i32p), up.ctypes.data_as(_i32p), 0,
+                           None, None, None)
+    o = default_options()
+    o.want_fp32 = int(want_fp32)
+    for key, val in opts.items():
+        setattr(o, key, val)
+    out = ctypes.c_void_p()
+    _check(lib.rp_batch_build(descs, k, ctypes.byref(o), ctypes.byref(out)), "rp_batch_build")
+    return Handle(out.value, False)
+
+
+def batch_update_solve(h: Handle, buffer, b, x, tol: float = 1e-9, precision: str = "fp64", stream=None,
+                       wait: bool = True):
+    """rp_batch_update_solve; returns per-system SolveInfo dicts when ``wait``."""
+    _f64(buffer, "buffer"); _f64(b, "b"); _f64(x, "x")
+    prec = {"fp64": RP_FP64, "mixed": RP_MIXED}[precision]
+    infos = (SolveInfo * h.n_parts)() if wait else None
+    st = load().rp_batch_update_solve(h.ptr, _ptr(buffer), _where(buffer), _ptr(b), _ptr(x), float(tol), prec,
+                                      infos, _stream(stream))
+    _check(st, "rp_batch_update_solve", ok=(RP_OK, RP_NOT_CONVERGED, RP_BREAKDOWN))
+    return [i.as_dict() for i in infos] if wait else None
+
+
+def batch_set_config(h: Handle, cluster: int, threads: int):
+    _check(load().rp_batch_set_config(h.ptr, int(cluster), int(threads)), "rp_batch_set_config")
+
+
+def batch_autotune(h: Handle, buffer, b, x, tol: float = 1e-9, precision: str = "fp64", stream=None):
+    """rp_batch_autotune: returns (cluster, threads, ms) of the fastest launch shape."""
+    c, t, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    prec = {"fp64": RP_FP64, "mixed": RP_MIXED}[precision]
+    _check(load().rp_batch_autotune(h.ptr, _ptr(buffer), _ptr(b), _ptr(x), float(tol), prec, ctypes.byref(c),
+                                    ctypes.byref(t), ctypes.byref(ms), _stream(stream)), "rp_batch_autotune")
+    return c.value, t.value, ms.value
+
+
 def spmv_noalloc(n: int, row_ptr, col_idx, vals, x, y, xy=None, stream=None):
     """rp_spmv_noalloc: the same product for a caller-owned CSR matrix, with no
     device allocation (for callers that cannot allocate device memory)."""
@@ -295,4 +346,5 @@ class Exports:
     names: tuple = ("rp_default_options", "rp_build_repartition", "rp_get_part_map", "rp_get_sizes",
                     "rp_update_values_packed", "rp_update_values", "rp_get_values", "rp_spmv", "rp_solve",
                     "rp_solve_adjoint", "rp_profile_iteration", "rp_entry_grad", "rp_face_grad", "rp_destroy", "rp_status_str",
-                    "rp_last_error", "rp_spmv_noalloc")
+                    "rp_last_error", "rp_spmv_noalloc", "rp_batch_build", "rp_batch_update_solve",
+                    "rp_batch_set_config", "rp_batch_autotune")

@@ -341,3 +341,31 @@ WORKLOADS = {
 def workload_mesh(name: str) -> BoxMesh:
     w = WORKLOADS[name]
     return box_mesh(*w["n"], *w["p"])
+
+
+class Batch:
+    """Independent box systems (one rank each, Dirichlet at each x = 0 face)
+    for the batched form: shapes from ``batch_shapes``; every draw uses one
+    generator per step, systems in order."""
+
+    def __init__(self, count: int = 256, lo: int = 8000, hi: int = 300000, seed: int = 0):
+        self.dims = batch_shapes(count, lo, hi, seed)
+        self.meshes = [box_mesh(*d) for d in self.dims]
+        self.systems = [m.ranks[0] for m in self.meshes]
+        self.assemblers = [Assembler(m) for m in self.meshes]
+
+    @property
+    def n_rows(self) -> int:
+        return sum(m.n_cells for m in self.meshes)
+
+    def staging(self, sigma: float = 0.5, seed: int = 100) -> np.ndarray:
+        rng = np.random.default_rng(seed)
+        parts = []
+        for m, asm in zip(self.meshes, self.assemblers):
+            a = rng.lognormal(0.0, sigma, size=m.n_internal_faces + m.n_boundary_faces)
+            parts.append(asm.staging(a))
+        return np.concatenate(parts)
+
+    def rhs(self, seed: int = 0) -> np.ndarray:
+        rng = np.random.default_rng(seed)
+        return np.concatenate([rng.uniform(-1.0, 1.0, size=m.n_cells)[m.merged_gid()] for m in self.meshes])

@@ -99,3 +99,22 @@ def test_null_arguments(lib):
     assert lib.rp_update_values_packed(None, None, 0, None) == repart.RP_EINVAL
     assert b"null" in lib.rp_last_error()
     lib.rp_destroy(None)  # no-op
+
+
+def test_batch_rejects_coupled_systems(lib):
+    """Batched systems are independent: a system with interface entries is refused on the host."""
+    with pytest.raises(repart.RepartError) as e:
+        lib_ranks = _ranks()
+        descs = (repart.LduDesc * len(lib_ranks))()
+        keep = []
+        for i, r in enumerate(lib_ranks):
+            arrs = [np.ascontiguousarray(getattr(r, f), dtype=np.int32) for f in
+                    ("lower_addr", "upper_addr", "iface_row", "iface_nbr_rank", "iface_nbr_col")]
+            keep.append(arrs)
+            p = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for a in arrs]
+            descs[i] = repart.LduDesc(r.n_cells, arrs[0].size, p[0], p[1], arrs[2].size, p[2], p[3], p[4])
+        out = ctypes.c_void_p()
+        repart._check(lib.rp_batch_build(descs, len(lib_ranks), None, ctypes.byref(out)), "rp_batch_build")
+    assert e.value.status == repart.RP_EINVAL
+    assert b"interface" in lib.rp_last_error()
+    assert lib.rp_batch_set_config(None, 8, 256) == repart.RP_EINVAL

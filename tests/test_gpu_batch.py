@@ -1,0 +1,130 @@
+"""Batched form: many independent systems updated and solved in one
+persistent launch, each compared with the oracle solving that system alone.
+
+Tolerances as in the single-system parity tests: maps and values bit-exact;
+FP64 ||x_s - x_ref,s|| / ||x_ref,s|| <= 1e-7 against the oracle PCG at the same
+tolerance, iteration counts within 2; every system's true residual <= 1e-9;
+mixed: error against the FP64 solution <= 1e-6.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import repart_oracle as O
+from paper_2510_08536_gb300 import build, repart, synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    repart.load()
+    torch.cuda.set_device(0)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    B = synth.Batch(count=12, lo=300, hi=4000, seed=3)
+    stg = B.staging(0.5, 100)
+    b = B.rhs(0)
+    refs = []
+    so = ro = 0
+    for mesh in B.meshes:
+        (m,) = O.repartition_map(mesh.ranks, 1)
+        nslot = mesh.staging_size()
+        vals = O.update_values(m.src_of, stg[so:so + nslot])
+        A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
+        dinv = O.jacobi_inverse(m.row_ptr, m.col_idx, vals, m.diag_pos)
+        bs = b[ro:ro + mesh.n_cells]
+        refs.append(dict(map=m, vals=vals, A=A, dinv=dinv, b=bs, ro=ro, n=mesh.n_cells,
+                         fp64=O.pcg(A, dinv, bs, tol=1e-9), exact=O.pcg(A, dinv, bs, tol=1e-13).x))
+        so += nslot
+        ro += mesh.n_cells
+    return B, stg, b, refs
+
+
+def test_batch_maps_and_values_bit_exact(batch):
+    B, stg, b, refs = batch
+    h = repart.batch_build(B.systems)
+    assert h.n_parts == len(B.systems)
+    x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
+    repart.batch_update_solve(h, _t(stg), _t(b), x, tol=1e-9)
+    vals = repart.get_values(h)["vals"].cpu().numpy()
+    off = 0
+    for s, ref in enumerate(refs):
+        got = repart.get_part_map(h, s)
+        for key in ("row_ptr", "col_idx", "src_of", "diag_pos"):
+            np.testing.assert_array_equal(got[key].cpu().numpy(), getattr(ref["map"], key), err_msg=f"{s} {key}")
+        np.testing.assert_array_equal(vals[off:off + ref["vals"].size], ref["vals"])
+        off += ref["vals"].size
+    h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_solves_match_oracle(batch, precision):
+    B, stg, b, refs = batch
+    h = repart.batch_build(B.systems)
+    x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
+    infos = repart.batch_update_solve(h, _t(stg), _t(b), x, tol=1e-9, precision=precision)
+    xs = x.cpu().numpy()
+    for s, ref in enumerate(refs):
+        inf = infos[s]
+        assert inf["status"] == 0, (s, inf)
+        xi = xs[ref["ro"]:ref["ro"] + ref["n"]]
+        tr = np.linalg.norm(ref["b"] - ref["A"] @ xi) / np.linalg.norm(ref["b"])
+        assert tr <= 1e-9, (s, tr)
+        assert abs(inf["rel_residual"] - tr) <= 1e-12
+        if precision == "fp64":
+            assert np.linalg.norm(xi - ref["fp64"].x) / np.linalg.norm(ref["fp64"].x) <= 1e-7
+            assert abs(inf["iterations"] - ref["fp64"].iterations) <= 2, (s, inf, ref["fp64"].iterations)
+        else:
+            assert np.linalg.norm(xi - ref["exact"]) / np.linalg.norm(ref["exact"]) <= 1e-6
+            assert inf["outer_iterations"] >= 1
+    h.close()
+
+
+@pytest.mark.parametrize("cluster,threads", [(1, 128), (2, 256), (4, 512), (8, 256), (16, 128)])
+def test_batch_launch_shapes(batch, cluster, threads):
+    B, stg, b, refs = batch
+    h = repart.batch_build(B.systems)
+    try:
+        repart.batch_set_config(h, cluster, threads)
+    except repart.RepartError as e:
+        if e.status == repart.RP_EUNSUPPORTED:
+            pytest.skip(f"cluster {cluster} x {threads} cannot be scheduled here")
+        raise
+    for precision in ("fp64", "mixed"):
+        x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
+        infos = repart.batch_update_solve(h, _t(stg), _t(b), x, tol=1e-9, precision=precision)
+        xs = x.cpu().numpy()
+        for s, ref in enumerate(refs):
+            assert infos[s]["status"] == 0
+            xi = xs[ref["ro"]:ref["ro"] + ref["n"]]
+            assert np.linalg.norm(ref["b"] - ref["A"] @ xi) / np.linalg.norm(ref["b"]) <= 1e-9
+    h.close()
+
+
+def test_batch_autotune_and_host_buffer(batch):
+    B, stg, b, refs = batch
+    h = repart.batch_build(B.systems)
+    bd = _t(b)
+    x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
+    c, t, ms = repart.batch_autotune(h, _t(stg), bd, x, tol=1e-9, precision="fp64")
+    assert c in (2, 4, 8, 16) and t in (128, 256, 512) and ms > 0
+    xd = torch.zeros_like(x)
+    repart.batch_update_solve(h, _t(stg), bd, xd, tol=1e-9)
+    xh = torch.zeros_like(x)
+    infos = repart.batch_update_solve(h, torch.from_numpy(stg).pin_memory(), bd, xh, tol=1e-9)
+    assert all(i["status"] == 0 for i in infos)
+    assert torch.equal(xd, xh)
+    # deterministic: the same launch shape gives the same bits
+    x2 = torch.zeros_like(x)
+    repart.batch_update_solve(h, _t(stg), bd, x2, tol=1e-9)
+    assert torch.equal(xd, x2)
+    h.close()
