@@ -53,7 +53,14 @@ typedef enum rp_status {
 } rp_status;
 
 enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1 };   /* where a buffer lives       */
-enum { RP_FP64 = 0, RP_MIXED = 1 };            /* solve precision            */
+/* Solve precision. RP_MIXED: FP64 iterative refinement around an FP32 PCG
+ * that is restarted (p = z) at every refinement and solved to inner_tol.
+ * RP_MIXED_RU: the same FP32 values, iterations and FP64 residual / update /
+ * convergence test, but the FP32 PCG is not restarted: when its recursive
+ * residual has fallen by inner_tol (or reaches the outer target) its iterate
+ * is added to x in FP64, the FP64 residual replaces the FP32 one and the
+ * search direction continues (p = z + beta p). */
+enum { RP_FP64 = 0, RP_MIXED = 1, RP_MIXED_RU = 2 };
 
 typedef struct rp_handle rp_handle;
 
@@ -92,7 +99,14 @@ typedef struct rp_options {
                              (slow; for profilers that cannot look inside
                              graphs with conditional nodes)                       */
   int32_t reserved;
+  double ru_delta;        /* RP_MIXED_RU: residual reduction between two FP64
+                             refinements (0: use inner_tol)                       */
 } rp_options;
+
+/* Replace the solver settings of a handle (max_iter, max_outer, max_restarts,
+ * inner_tol, ru_delta, host_loop); structural fields are ignored. Takes
+ * effect at the next solve. */
+rp_status rp_set_solver_options(rp_handle* h, const rp_options* opts);
 
 /* Defaults: n_parts 1, general (non-symmetric) storage, FP32 copy on,
  * transpose off, max_iter 20000, max_outer 30, max_restarts 8, current

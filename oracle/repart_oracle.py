@@ -441,6 +441,72 @@ def mixed_ir(A64, A32, dinv32, b, tol=1e-9, inner_tol=1e-5, max_outer=50, max_in
     return SolveResult(x, inner_total, status, rel, rel, outer)
 
 
+def mixed_reliable(A64, A_in, dinv_in, b, tol=1e-9, delta=1e-5, max_iter=20000, max_updates=100,
+                   dtype=np.float32) -> SolveResult:
+    """Refinement whose inner CG is not restarted ("reliable updates").
+
+    The inner CG runs in ``dtype`` on A_in (values, vectors, products; dot
+    products accumulated in FP64, alpha and beta rounded to ``dtype``). When
+    its recursive residual has fallen below ``delta`` times the residual at the
+    last refinement (or below the outer target tol ||b||), the inner iterate d
+    is added to the FP64 solution
+    (x += d, d = 0), the FP64 residual r = b - A64 x is computed and the
+    convergence test ||r|| <= tol ||b|| is taken on it; otherwise r replaces
+    the inner residual and the iteration CONTINUES with p = z + beta p,
+    beta = (r.z)_new / (r.z)_old (no restart of the search direction)."""
+    f = dtype
+    b = np.asarray(b, np.float64)
+    bb = float(b @ b)
+    x = np.zeros_like(b)
+    if bb == 0.0:
+        return SolveResult(x, 0, OK, 0.0, 0.0, 0)
+    thresh = tol * tol * bb
+    r = b.astype(f)
+    r64 = r.astype(np.float64)
+    inner = delta * delta * float(r64 @ r64)
+    z = dinv_in * r
+    p = z.copy()
+    rz = float(r64 @ z.astype(np.float64))
+    d = np.zeros_like(r)
+    it = updates = 0
+    status = NOT_CONVERGED
+    rr = bb
+    while True:
+        q = A_in @ p
+        pq = float(p.astype(np.float64) @ q.astype(np.float64))
+        if not pq > 0.0:
+            status = BREAKDOWN
+            break
+        alpha = f(rz / pq)
+        d += alpha * p
+        r -= alpha * q
+        it += 1
+        r64 = r.astype(np.float64)
+        # a phase ends at the inner tolerance, or when the inner residual
+        # already meets the outer target (then the FP64 test decides)
+        if float(r64 @ r64) <= max(inner, thresh) or it >= max_iter:
+            x += d.astype(np.float64)
+            d[:] = 0
+            res = b - A64 @ x
+            rr = float(res @ res)
+            updates += 1
+            if rr <= thresh:
+                status = OK
+                break
+            if it >= max_iter or updates >= max_updates:
+                break
+            r = res.astype(f)
+            r64 = r.astype(np.float64)
+            inner = delta * delta * float(r64 @ r64)
+        z = dinv_in * r
+        rz_new = float(r64 @ z.astype(np.float64))
+        beta = f(rz_new / rz)
+        p = z + beta * p
+        rz = rz_new
+    rel = float(np.sqrt(rr / bb))
+    return SolveResult(x, it, status, rel, rel, updates)
+
+
 # --------------------------------------------------------------------------
 # Adjoint and gradients
 # --------------------------------------------------------------------------

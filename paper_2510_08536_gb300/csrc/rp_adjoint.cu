@@ -9,7 +9,7 @@
 
 namespace rp {
 
-rp_status solve_common(rp_handle* h, bool mixed, const double* vals, const double* dinv, cudaGraphExec_t* slot,
+rp_status solve_common(rp_handle* h, int mode, const double* vals, const double* dinv, cudaGraphExec_t* slot,
                         const double* b, double* x, double tol, int32_t x_is_guess, int32_t where,
                         rp_solve_info* info, cudaStream_t s);
 

@@ -77,8 +77,10 @@ __device__ __forceinline__ T row_dot_coherent(const int32_t* __restrict__ rp, co
 
 }  // namespace
 
-template <bool MIXED>
+// MODE: 0 FP64 PCG, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG
+template <int MODE>
 __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
+  constexpr bool MIXED = MODE != 0;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned T = cl.num_blocks();
   const unsigned me = cl.block_rank();
@@ -209,6 +211,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
       float* p = a.p32 + ro;
       float* q = a.q32 + ro;
       float* d = a.d32 + ro;
+      constexpr bool RU = MODE == 2;
+      double rz = 0.0;  // continued refinement carries (r, z) across passes
       for (;;) {
         // FP64 residual pass with FP64 values; FP32 copy starts the inner solve
         double v4[4] = {0.0, 0.0, 0.0, 0.0}, t4[4];
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           r[i] = r32;
           d[i] = 0.f;
           const float z32 = dinv32[i] * r32;
-          p[i] = z32;
+          if (!RU || passes == 0) p[i] = z32;
           rzf = fmaf(r32, z32, rzf);
           rr32f = fmaf(r32, r32, rr32f);
           v4[1] = fma(ri, ri, v4[1]);
@@ -239,14 +243,21 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           thresh = tol * tol * bb;
         }
         rr = t4[1];
+        const bool first = passes == 0;
         ++passes;
         if (rr <= thresh) { status = RP_OK; break; }
         if (status == RP_BREAKDOWN) break;
         if (!isfinite(rr)) { status = RP_BREAKDOWN; break; }
-        if (outer >= a.max_outer) { status = RP_NOT_CONVERGED; break; }
+        if (outer >= a.max_outer || (RU && iters >= a.max_iter)) { status = RP_NOT_CONVERGED; break; }
         ++outer;
-        double rz = t4[0];
-        const double ithresh = a.inner_tol * a.inner_tol * t4[3];
+        if (RU && !first) {
+          // the FP64 residual replaced the FP32 one: continue the search direction
+          const float beta = (float)(t4[0] / rz);
+          for (int64_t i = i0 + tid; i < i1; i += nth) p[i] = fmaf(beta, p[i], dinv32[i] * r[i]);
+        }
+        rz = t4[0];
+        const double ithresh = RU ? fmax(a.ru_delta * a.ru_delta * t4[3], thresh)
+                                  : a.inner_tol * a.inner_tol * t4[3];
         int it = 0;
         bool broke = false;
         for (;;) {
@@ -274,7 +285,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           ++iters;
           bool stop = false;
           float beta = 0.f;
-          if (t2[1] <= ithresh || it >= a.max_iter) stop = true;
+          if (t2[1] <= ithresh || (RU ? iters : it) >= a.max_iter) stop = true;
           else if (!(t2[0] > 0.0) || !isfinite(t2[0])) { stop = true; status = RP_BREAKDOWN; broke = true; }
           else { beta = (float)(t2[0] / rz); rz = t2[0]; }
           for (int64_t i = i0 + tid; i < i1; i += nth) {
@@ -326,11 +337,13 @@ rp_status balloc(T** p, int64_t count) {
   return RP_OK;
 }
 
-void* batch_kernel(bool mixed) { return mixed ? (void*)k_batch<true> : (void*)k_batch<false>; }
+void* batch_kernel(int mode) {
+  return mode == 2 ? (void*)k_batch<2> : mode == 1 ? (void*)k_batch<1> : (void*)k_batch<0>;
+}
 
-rp_status launch_config(rp_handle* h, bool mixed, int cluster, int threads, cudaLaunchConfig_t* cfg,
+rp_status launch_config(rp_handle* h, int mode, int cluster, int threads, cudaLaunchConfig_t* cfg,
                         cudaLaunchAttribute* attr, int* n_clusters) {
-  void* fn = batch_kernel(mixed);
+  void* fn = batch_kernel(mode);
   if (cluster > 8) RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   *cfg = cudaLaunchConfig_t{};
   cfg->blockDim = dim3((unsigned)threads);
@@ -350,11 +363,11 @@ rp_status launch_config(rp_handle* h, bool mixed, int cluster, int threads, cuda
   return RP_OK;
 }
 
-rp_status build_batch_graph(rp_handle* h, bool mixed, int cluster, int threads, cudaGraphExec_t* exec) {
+rp_status build_batch_graph(rp_handle* h, int mode, int cluster, int threads, cudaGraphExec_t* exec) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr;
   int nc = 0;
-  RP_TRY(launch_config(h, mixed, cluster, threads, &cfg, &attr, &nc));
+  RP_TRY(launch_config(h, mode, cluster, threads, &cfg, &attr, &nc));
   cudaStream_t cs;
   RP_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cfg.stream = cs;
@@ -363,8 +376,9 @@ rp_status build_batch_graph(rp_handle* h, bool mixed, int cluster, int threads, 
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(h->batch_queue, 0, sizeof(unsigned int), cs);
-    if (mixed) cudaLaunchKernelEx(&cfg, k_batch<true>, ba);
-    else cudaLaunchKernelEx(&cfg, k_batch<false>, ba);
+    if (mode == 2) cudaLaunchKernelEx(&cfg, k_batch<2>, ba);
+    else if (mode == 1) cudaLaunchKernelEx(&cfg, k_batch<1>, ba);
+    else cudaLaunchKernelEx(&cfg, k_batch<0>, ba);
     e = cudaStreamEndCapture(cs, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
@@ -433,6 +447,7 @@ rp_status batch_prepare(rp_handle* h) {
   a.max_restarts = h->opts.max_restarts;
   a.max_outer = h->opts.max_outer;
   a.inner_tol = h->opts.inner_tol;
+  a.ru_delta = h->opts.ru_delta > 0.0 ? h->opts.ru_delta : h->opts.inner_tol;
   h->batch_ready = true;
   return RP_OK;
 }
@@ -448,10 +463,10 @@ void free_batch(rp_handle* h) {
 
 static rp_status batch_run(rp_handle* h, const double* buffer, int32_t where, const double* b, double* x,
                            double tol, int32_t precision, rp_solve_info* info, cudaStream_t s) {
-  const bool mixed = precision == RP_MIXED;
+  const int mode = precision == RP_MIXED_RU ? 2 : precision == RP_MIXED ? 1 : 0;
   RP_TRY(batch_prepare(h));
-  cudaGraphExec_t& ex = h->batch_graphs[mixed ? 1 : 0];
-  if (!ex) RP_TRY(build_batch_graph(h, mixed, h->batch_cluster, h->batch_threads, &ex));
+  cudaGraphExec_t& ex = h->batch_graphs[mode];
+  if (!ex) RP_TRY(build_batch_graph(h, mode, h->batch_cluster, h->batch_threads, &ex));
   const double* src = buffer;
   if (where == RP_MEM_HOST) {
     RP_TRY_CUDA(cudaMemcpyAsync(h->staging, buffer, sizeof(double) * h->n_slots, cudaMemcpyHostToDevice, s));
@@ -496,8 +511,9 @@ extern "C" rp_status rp_batch_update_solve(rp_handle* h, const double* buffer, i
   if (!h || !buffer || !b || !x) return fail(RP_EINVAL, "null argument");
   if (!(tol >= 0.0)) return fail(RP_EINVAL, "tol must be >= 0");
   if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
-  if (precision != RP_FP64 && precision != RP_MIXED) return fail(RP_EINVAL, "precision must be RP_FP64 or RP_MIXED");
-  if (precision == RP_MIXED && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
+  if (precision != RP_FP64 && precision != RP_MIXED && precision != RP_MIXED_RU)
+    return fail(RP_EINVAL, "precision must be RP_FP64, RP_MIXED or RP_MIXED_RU");
+  if (precision != RP_FP64 && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
   return batch_run(h, buffer, where, b, x, tol, precision, info, (cudaStream_t)stream);
 }
 
@@ -511,7 +527,8 @@ extern "C" rp_status rp_batch_set_config(rp_handle* h, int32_t cluster, int32_t 
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr;
   int nc = 0;
-  RP_TRY(launch_config(h, h->want_fp32, cluster, threads, &cfg, &attr, &nc));
+  RP_TRY(launch_config(h, 0, cluster, threads, &cfg, &attr, &nc));
+  if (h->want_fp32) RP_TRY(launch_config(h, 1, cluster, threads, &cfg, &attr, &nc));
   for (auto& g : h->batch_graphs)
     if (g) {
       cudaGraphExecDestroy(g);

@@ -66,6 +66,9 @@ struct Ctl {
   int32_t x_zero;       // first pass starts from x = 0
   int32_t skip_correct; // mixed: no correction to add this pass
   unsigned int ticket;  // last-block election counter (reset by the last block)
+  int32_t ru_apply;     // continued refinement: p = z + beta_ru p before the next run
+  double beta_ru;
+  double ru_delta;      // continued refinement: residual reduction per refinement
 };
 
 // Pointers that change between calls (user buffers); the captured graphs
@@ -78,6 +81,7 @@ struct SolveIO {
 struct Graphs {
   cudaGraphExec_t fp64 = nullptr;
   cudaGraphExec_t mixed = nullptr;
+  cudaGraphExec_t mixed_ru = nullptr;
   cudaGraphExec_t adjoint = nullptr;
 };
 
@@ -110,6 +114,7 @@ struct BatchArgs {
   const BatchIO* io;
   int32_t max_iter, max_restarts, max_outer;
   double inner_tol;
+  double ru_delta;
 };
 
 }  // namespace rp
@@ -187,7 +192,7 @@ struct rp_handle {
   rp_solve_info* batch_info = nullptr;
   rp::BatchIO* batch_io = nullptr;
   rp::BatchArgs batch_args{};
-  cudaGraphExec_t batch_graphs[2] = {nullptr, nullptr};
+  cudaGraphExec_t batch_graphs[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace rp {

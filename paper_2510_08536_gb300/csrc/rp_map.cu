@@ -364,7 +364,7 @@ rp_status validate(const rp_ldu_desc* ranks, int32_t k, const rp_options& o) {
   if (!ranks || k < 1) return fail(RP_EINVAL, "need k >= 1 rank descriptors");
   if (o.n_parts < 1 || k % o.n_parts) return fail(RP_EINVAL, "n_parts=%d must divide k=%d", o.n_parts, k);
   if (o.max_iter < 0 || o.max_outer < 0 || o.max_restarts < 0 || !(o.inner_tol > 0.0) ||
-      o.spin_limit < 1)
+      o.spin_limit < 1 || !(o.ru_delta >= 0.0 && o.ru_delta < 1.0))
     return fail(RP_EINVAL, "invalid solver options");
   int64_t n = 0, nnz = 0, slots = 0;
   for (int r = 0; r < k; ++r) {
@@ -433,6 +433,7 @@ extern "C" void rp_default_options(rp_options* o) {
   o->device = -1;
   o->inner_tol = 1e-5;
   o->spin_limit = 1LL << 26;
+  o->ru_delta = 0.0;
 }
 
 extern "C" const char* rp_last_error(void) { return rp::g_last_error.c_str(); }

@@ -57,6 +57,7 @@ struct ResArgs {
   cudaGraphConditionalHandle inner;
   cudaGraphConditionalHandle outer;
   int in_graph;
+  int ru;  // mixed: continued (not restarted) inner PCG across refinements
 };
 
 template <typename T>
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
     a.r32[i] = r32;
     a.d32[i] = 0.0f;
     const float z32 = a.dinv32[i] * r32;
-    a.p32[i] = z32;
+    if (!a.ru || first) a.p32[i] = z32;  // continued refinement keeps p after the first pass
     rz += (double)r32 * (double)z32;
     rr32 += (double)r32 * (double)r32;
     rr += ri * ri;
@@ -322,13 +323,23 @@ __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
       c->status = RP_BREAKDOWN;
     } else if (c->outer >= c->max_outer) {
       c->status = RP_NOT_CONVERGED;
+    } else if (a.ru && c->iter_total >= c->max_iter) {
+      c->status = RP_NOT_CONVERGED;
     } else {
       go = true;
       c->outer += 1;
+      if (a.ru) {
+        // the FP64 residual replaces the FP32 one; the search direction continues
+        c->ru_apply = first ? 0 : 1;
+        c->beta_ru = first ? 0.0 : tot[0] / c->rz;
+        c->inner_thresh = fmax(c->ru_delta * c->ru_delta * tot[3], c->thresh);
+      } else {
+        c->inner_thresh = c->inner_tol * c->inner_tol * tot[3];
+        c->iter = 0;
+      }
       c->rz = tot[0];
-      c->inner_thresh = c->inner_tol * c->inner_tol * tot[3];
-      c->iter = 0;
     }
+    if (!go) c->ru_apply = 0;
     c->stop = go ? 0 : 1;
     c->skip_x = 0;
     c->skip_correct = go ? 0 : 1;
@@ -346,6 +357,22 @@ struct CorrectArgs {
   SolveIO* io;
 };
 
+struct RuArgs {
+  int64_t n;
+  const float* dinv32;
+  const float* r32;
+  float* p32;
+  Ctl* c;
+};
+
+// continued refinement: p = D32^-1 r32 + beta p after the residual was replaced
+__global__ void __launch_bounds__(kThreads) k_ru_p(RuArgs a) {
+  if (!a.c->ru_apply) return;
+  const float beta = (float)a.c->beta_ru;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+    a.p32[i] = fmaf(beta, a.p32[i], a.dinv32[i] * a.r32[i]);
+}
+
 // x += d (FP64) after an inner FP32 solve.
 __global__ void __launch_bounds__(kThreads) k_correct(CorrectArgs a) {
   if (a.c->skip_correct || a.c->status == RP_BREAKDOWN) return;
@@ -355,11 +382,12 @@ __global__ void __launch_bounds__(kThreads) k_correct(CorrectArgs a) {
 }
 
 __global__ void k_setup(Ctl* c, SolveIO* io, const double* b, double* x, double tol, double inner_tol, int x_zero,
-                        int max_iter, int max_restarts, int max_outer) {
+                        int max_iter, int max_restarts, int max_outer, double ru_delta = 0.0) {
   io->b = b;
   io->x = x;
   c->tol = tol;
   c->inner_tol = inner_tol;
+  c->ru_delta = ru_delta > 0.0 ? ru_delta : inner_tol;
   c->x_zero = x_zero;
   c->max_iter = max_iter;
   c->max_restarts = max_restarts;
@@ -430,9 +458,11 @@ struct GraphGuard {
   }
 };
 
-// while (outer) { residual pass; while (inner) { K1; K2; K3 }; [x += d] }
-rp_status build_solve_graph(rp_handle* h, bool mixed, const double* vals, const double* dinv,
+// while (outer) { residual pass; [p = z + beta p]; while (inner) { K1; K2; K3 }; [x += d] }
+// mode: 0 FP64, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG
+rp_status build_solve_graph(rp_handle* h, int mode, const double* vals, const double* dinv,
                             cudaGraphExec_t* exec) {
+  const bool mixed = mode != 0;
   GraphGuard top;
   RP_TRY_CUDA(cudaGraphCreate(&top.g, 0));
   cudaGraphConditionalHandle hout, hin;
@@ -460,8 +490,15 @@ rp_status build_solve_graph(rp_handle* h, bool mixed, const double* vals, const 
   ra.inner = hin;
   ra.outer = hout;
   ra.in_graph = 1;
+  ra.ru = mode == 2;
   RP_TRY(add_kernel(obody, &nres, nullptr, mixed ? (void*)k_res_mixed : (void*)k_res64, h->grid, &ra));
-  RP_TRY(add_while(obody, &win, &nres, hin, &ibody));
+  cudaGraphNode_t before_inner = nres, nru;
+  if (mode == 2) {
+    RuArgs ru{h->n, h->dinv32, h->r32, h->p32, h->ctl};
+    RP_TRY(add_kernel(obody, &nru, &nres, (void*)k_ru_p, h->grid, &ru));
+    before_inner = nru;
+  }
+  RP_TRY(add_while(obody, &win, &before_inner, hin, &ibody));
   if (mixed) {
     IterArgs<float> ia{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
                        h->ctl, h->io, h->partials, hin, 1};
@@ -530,6 +567,7 @@ void free_solver(rp_handle* h) {
   h->ticket = nullptr;
   if (h->graphs.fp64) cudaGraphExecDestroy(h->graphs.fp64);
   if (h->graphs.mixed) cudaGraphExecDestroy(h->graphs.mixed);
+  if (h->graphs.mixed_ru) cudaGraphExecDestroy(h->graphs.mixed_ru);
   if (h->graphs.adjoint) cudaGraphExecDestroy(h->graphs.adjoint);
   h->graphs = Graphs{};
 }
@@ -537,7 +575,7 @@ void free_solver(rp_handle* h) {
 rp_status launch_solve(rp_handle* h, cudaGraphExec_t exec, const double* b, double* x, double tol, bool x_zero,
                        int max_iter, rp_solve_info* info, cudaStream_t s) {
   k_setup<<<1, 1, 0, s>>>(h->ctl, h->io, b, x, tol, h->opts.inner_tol, x_zero ? 1 : 0, max_iter,
-                          h->opts.max_restarts, h->opts.max_outer);
+                          h->opts.max_restarts, h->opts.max_outer, h->opts.ru_delta);
   RP_TRY_CUDA(cudaGetLastError());
   RP_TRY_CUDA(cudaGraphLaunch(exec, s));
   (void)info;
@@ -559,8 +597,11 @@ rp_status read_info(rp_handle* h, rp_solve_info* info, cudaStream_t s) {
 
 // The kernel sequence of the solve graph, launched from the host: the
 // control block is read back after every residual pass and every iteration.
-rp_status host_loop_solve(rp_handle* h, bool mixed, const double* vals, const double* dinv, cudaStream_t s) {
+rp_status host_loop_solve(rp_handle* h, int mode, const double* vals, const double* dinv, cudaStream_t s) {
+  const bool mixed = mode != 0;
   ResArgs ra{};
+  ra.ru = mode == 2;
+  RuArgs ru{h->n, h->dinv32, h->r32, h->p32, h->ctl};
   ra.n = h->n;
   ra.row_ptr = h->row_ptr;
   ra.col = h->col_idx;
@@ -591,6 +632,7 @@ rp_status host_loop_solve(rp_handle* h, bool mixed, const double* vals, const do
   for (;;) {
     if (mixed) k_res_mixed<<<h->grid, kThreads, 0, s>>>(ra);
     else k_res64<<<h->grid, kThreads, 0, s>>>(ra);
+    if (mode == 2) k_ru_p<<<h->grid, kThreads, 0, s>>>(ru);
     RP_TRY_CUDA(cudaGetLastError());
     RP_TRY(read());
     const bool go = !c.stop;
@@ -614,10 +656,10 @@ rp_status host_loop_solve(rp_handle* h, bool mixed, const double* vals, const do
   return RP_OK;
 }
 
-rp_status solve_common(rp_handle* h, bool mixed, const double* vals, const double* dinv, cudaGraphExec_t* slot,
+rp_status solve_common(rp_handle* h, int mode, const double* vals, const double* dinv, cudaGraphExec_t* slot,
                        const double* b, double* x, double tol, int32_t x_is_guess, int32_t where,
                        rp_solve_info* info, cudaStream_t s) {
-  if (!*slot && !h->opts.host_loop) RP_TRY(build_solve_graph(h, mixed, vals, dinv, slot));
+  if (!*slot && !h->opts.host_loop) RP_TRY(build_solve_graph(h, mode, vals, dinv, slot));
   const double* bd = b;
   double* xd = x;
   if (where == RP_MEM_HOST) {
@@ -630,8 +672,8 @@ rp_status solve_common(rp_handle* h, bool mixed, const double* vals, const doubl
   }
   if (h->opts.host_loop) {
     k_setup<<<1, 1, 0, s>>>(h->ctl, h->io, bd, xd, tol, h->opts.inner_tol, x_is_guess ? 0 : 1, h->opts.max_iter,
-                            h->opts.max_restarts, h->opts.max_outer);
-    RP_TRY(host_loop_solve(h, mixed, vals, dinv, s));
+                            h->opts.max_restarts, h->opts.max_outer, h->opts.ru_delta);
+    RP_TRY(host_loop_solve(h, mode, vals, dinv, s));
   } else {
     RP_TRY(launch_solve(h, *slot, bd, xd, tol, !x_is_guess, h->opts.max_iter, info, s));
   }
@@ -653,16 +695,45 @@ extern "C" rp_status rp_solve(rp_handle* h, const double* b, double* x, double t
   if (!(tol >= 0.0)) return fail(RP_EINVAL, "tol must be >= 0");
   if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
   if (h->n_parts != 1) return fail(RP_EUNSUPPORTED, "solve needs n_parts == 1 (one merged matrix per GPU)");
-  if (precision != RP_FP64 && precision != RP_MIXED) return fail(RP_EINVAL, "precision must be RP_FP64 or RP_MIXED");
-  if (precision == RP_MIXED && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
+  if (precision != RP_FP64 && precision != RP_MIXED && precision != RP_MIXED_RU)
+    return fail(RP_EINVAL, "precision must be RP_FP64, RP_MIXED or RP_MIXED_RU");
+  if (precision != RP_FP64 && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
   if (h->n == 0) {
     if (info) *info = rp_solve_info{RP_OK, 0, 0, 0, 0, 0.0};
     return RP_OK;
   }
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == RP_MIXED)
-    return solve_common(h, true, h->vals, h->dinv, &h->graphs.mixed, b, x, tol, x_is_guess, where, info, s);
-  return solve_common(h, false, h->vals, h->dinv, &h->graphs.fp64, b, x, tol, x_is_guess, where, info, s);
+    return solve_common(h, 1, h->vals, h->dinv, &h->graphs.mixed, b, x, tol, x_is_guess, where, info, s);
+  if (precision == RP_MIXED_RU)
+    return solve_common(h, 2, h->vals, h->dinv, &h->graphs.mixed_ru, b, x, tol, x_is_guess, where, info, s);
+  return solve_common(h, 0, h->vals, h->dinv, &h->graphs.fp64, b, x, tol, x_is_guess, where, info, s);
+}
+
+extern "C" rp_status rp_set_solver_options(rp_handle* h, const rp_options* o) {
+  if (!h || !o) return fail(RP_EINVAL, "null argument");
+  if (o->max_iter < 0 || o->max_outer < 0 || o->max_restarts < 0 || !(o->inner_tol > 0.0) ||
+      !(o->ru_delta >= 0.0 && o->ru_delta < 1.0))
+    return fail(RP_EINVAL, "invalid solver options");
+  h->opts.max_iter = o->max_iter;
+  h->opts.max_outer = o->max_outer;
+  h->opts.max_restarts = o->max_restarts;
+  h->opts.inner_tol = o->inner_tol;
+  h->opts.ru_delta = o->ru_delta;
+  h->opts.host_loop = o->host_loop;
+  if (h->batch_ready) {  // the batched kernel's arguments are part of its graphs
+    h->batch_args.max_iter = o->max_iter;
+    h->batch_args.max_outer = o->max_outer;
+    h->batch_args.max_restarts = o->max_restarts;
+    h->batch_args.inner_tol = o->inner_tol;
+    h->batch_args.ru_delta = o->ru_delta > 0.0 ? o->ru_delta : o->inner_tol;
+    for (auto& g : h->batch_graphs)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  }
+  return RP_OK;
 }
 
 extern "C" rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* xy, void* stream) {
@@ -679,11 +750,12 @@ extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t
                                           float* ms_out, void* stream) {
   if (!h || !b || !ms_out || iters < 1) return fail(RP_EINVAL, "invalid argument");
   if (h->n_parts != 1) return fail(RP_EUNSUPPORTED, "needs n_parts == 1");
-  if (precision != RP_FP64 && precision != RP_MIXED) return fail(RP_EINVAL, "precision must be RP_FP64 or RP_MIXED");
-  if (precision == RP_MIXED && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
+  if (precision != RP_FP64 && precision != RP_MIXED && precision != RP_MIXED_RU)
+    return fail(RP_EINVAL, "precision must be RP_FP64, RP_MIXED or RP_MIXED_RU");
+  if (precision != RP_FP64 && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
   if (h->n == 0) return fail(RP_EINVAL, "empty system");
   cudaStream_t s = (cudaStream_t)stream;
-  const bool mixed = precision == RP_MIXED;
+  const bool mixed = precision != RP_FP64;  // both mixed modes run the same FP32 iteration kernels
   RP_TRY(dalloc(&h->x_host_stage, h->n + 64));
   // a fresh CG run from x = 0 that never meets its tolerance (tol = 0)
   k_setup<<<1, 1, 0, s>>>(h->ctl, h->io, b, h->x_host_stage, 0.0, 0.0, 1, iters + 2, 0, 1);

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "librepart.so")
 RP_OK, RP_EINVAL, RP_EDUP, RP_ERANGE, RP_EOVERFLOW, RP_ENOMEM, RP_ECUDA = range(7)
 RP_NOT_CONVERGED, RP_BREAKDOWN, RP_DEVICE_TIMEOUT, RP_EUNSUPPORTED = 7, 8, 9, 10
 RP_MEM_DEVICE, RP_MEM_HOST = 0, 1
-RP_FP64, RP_MIXED = 0, 1
+RP_FP64, RP_MIXED, RP_MIXED_RU = 0, 1, 2
+PRECISIONS = {"fp64": RP_FP64, "mixed": RP_MIXED, "mixed_ru": RP_MIXED_RU}
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 
@@ -39,7 +40,7 @@ class Options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("spin_limit", ctypes.c_int64),
-                ("host_loop", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("host_loop", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ru_delta", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -82,6 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rp_batch_build": (i32, [ctypes.POINTER(LduDesc), i32, ctypes.POINTER(Options), ctypes.POINTER(vp)]),
         "rp_batch_update_solve": (i32, [vp, vp, i32, vp, vp, dbl, i32, ctypes.POINTER(SolveInfo), vp]),
         "rp_batch_set_config": (i32, [vp, i32, i32]),
+        "rp_set_solver_options": (i32, [vp, ctypes.POINTER(Options)]),
         "rp_batch_autotune": (i32, [vp, vp, vp, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_float), vp]),
         "rp_solve": (i32, [vp, vp, vp, dbl, i32, i32, i32, ctypes.POINTER(SolveInfo), vp]),
@@ -183,7 +185,9 @@ def build_repartition(ranks, n_parts: int = 1, symmetric: bool = False, want_fp3
         setattr(o, key, val)
     out = ctypes.c_void_p()
     _check(lib.rp_build_repartition(descs, k, ctypes.byref(o), ctypes.byref(out)), "rp_build_repartition")
-    return Handle(out.value, symmetric)
+    h = Handle(out.value, symmetric)
+    h.options = o
+    return h
 
 
 class _CudaArray:
@@ -267,19 +271,31 @@ def batch_build(systems, want_fp32: bool = True, **opts) -> Handle:
         setattr(o, key, val)
     out = ctypes.c_void_p()
     _check(lib.rp_batch_build(descs, k, ctypes.byref(o), ctypes.byref(out)), "rp_batch_build")
-    return Handle(out.value, False)
+    h = Handle(out.value, False)
+    h.options = o
+    return h
 
 
 def batch_update_solve(h: Handle, buffer, b, x, tol: float = 1e-9, precision: str = "fp64", stream=None,
                        wait: bool = True):
     """rp_batch_update_solve; returns per-system SolveInfo dicts when ``wait``."""
     _f64(buffer, "buffer"); _f64(b, "b"); _f64(x, "x")
-    prec = {"fp64": RP_FP64, "mixed": RP_MIXED}[precision]
+    prec = PRECISIONS[precision]
     infos = (SolveInfo * h.n_parts)() if wait else None
     st = load().rp_batch_update_solve(h.ptr, _ptr(buffer), _where(buffer), _ptr(b), _ptr(x), float(tol), prec,
                                       infos, _stream(stream))
     _check(st, "rp_batch_update_solve", ok=(RP_OK, RP_NOT_CONVERGED, RP_BREAKDOWN))
     return [i.as_dict() for i in infos] if wait else None
+
+
+def set_solver_options(h: Handle, **kw):
+    """rp_set_solver_options: change max_iter / max_outer / max_restarts /
+    inner_tol / ru_delta / host_loop of an existing handle."""
+    o = h.options if getattr(h, "options", None) is not None else default_options()
+    for key, val in kw.items():
+        setattr(o, key, val)
+    _check(load().rp_set_solver_options(h.ptr, ctypes.byref(o)), "rp_set_solver_options")
+    h.options = o
 
 
 def batch_set_config(h: Handle, cluster: int, threads: int):
@@ -289,7 +305,7 @@ def batch_set_config(h: Handle, cluster: int, threads: int):
 def batch_autotune(h: Handle, buffer, b, x, tol: float = 1e-9, precision: str = "fp64", stream=None):
     """rp_batch_autotune: returns (cluster, threads, ms) of the fastest launch shape."""
     c, t, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
-    prec = {"fp64": RP_FP64, "mixed": RP_MIXED}[precision]
+    prec = PRECISIONS[precision]
     _check(load().rp_batch_autotune(h.ptr, _ptr(buffer), _ptr(b), _ptr(x), float(tol), prec, ctypes.byref(c),
                                     ctypes.byref(t), ctypes.byref(ms), _stream(stream)), "rp_batch_autotune")
     return c.value, t.value, ms.value
@@ -308,7 +324,7 @@ def solve(h: Handle, b, x, tol: float = 1e-9, precision: str = "fp64", x_is_gues
     _f64(b, "b"); _f64(x, "x")
     if b.is_cuda != x.is_cuda:
         raise ValueError("b and x must both live on the device or both on the host")
-    prec = {"fp64": RP_FP64, "mixed": RP_MIXED}[precision]
+    prec = PRECISIONS[precision]
     info = SolveInfo()
     st = load().rp_solve(h.ptr, _ptr(b), _ptr(x), float(tol), prec, int(x_is_guess), _where(b),
                          ctypes.byref(info) if wait else None, _stream(stream))
@@ -319,7 +335,7 @@ def solve(h: Handle, b, x, tol: float = 1e-9, precision: str = "fp64", x_is_gues
 def profile_iteration(h: Handle, b, precision: str = "fp64", iters: int = 20, stream=None):
     """rp_profile_iteration: average ms of the SpMV, residual and x/p kernels."""
     ms = (ctypes.c_float * 3)()
-    prec = {"fp64": RP_FP64, "mixed": RP_MIXED}[precision]
+    prec = PRECISIONS[precision]
     _check(load().rp_profile_iteration(h.ptr, _ptr(b), prec, int(iters), ms, _stream(stream)), "rp_profile_iteration")
     return dict(spmv=ms[0], resid=ms[1], xp=ms[2])
 
@@ -347,4 +363,4 @@ class Exports:
                     "rp_update_values_packed", "rp_update_values", "rp_get_values", "rp_spmv", "rp_solve",
                     "rp_solve_adjoint", "rp_profile_iteration", "rp_entry_grad", "rp_face_grad", "rp_destroy", "rp_status_str",
                     "rp_last_error", "rp_spmv_noalloc", "rp_batch_build", "rp_batch_update_solve",
-                    "rp_batch_set_config", "rp_batch_autotune")
+                    "rp_batch_set_config", "rp_batch_autotune", "rp_set_solver_options")

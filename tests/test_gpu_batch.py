@@ -66,7 +66,7 @@ def test_batch_maps_and_values_bit_exact(batch):
     h.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ru"])
 def test_batch_solves_match_oracle(batch, precision):
     B, stg, b, refs = batch
     h = repart.batch_build(B.systems)
@@ -99,7 +99,7 @@ def test_batch_launch_shapes(batch, cluster, threads):
         if e.status == repart.RP_EUNSUPPORTED:
             pytest.skip(f"cluster {cluster} x {threads} cannot be scheduled here")
         raise
-    for precision in ("fp64", "mixed"):
+    for precision in ("fp64", "mixed", "mixed_ru"):
         x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
         infos = repart.batch_update_solve(h, _t(stg), _t(b), x, tol=1e-9, precision=precision)
         xs = x.cpu().numpy()

@@ -170,6 +170,28 @@ def test_mixed_solve_parity():
     h.close()
 
 
+@pytest.mark.parametrize("sigma", [None, 1.0])
+def test_mixed_continued_solve_parity(sigma):
+    """RP_MIXED_RU against the oracle's refinement with a continued inner PCG."""
+    c = Case((32, 32, 32), (2, 2, 2), sigma=sigma)
+    h = repart.build_repartition(c.mesh.ranks)
+    repart.update_values_packed(h, _t(c.staging))
+    x = torch.zeros(c.mesh.n_cells, dtype=torch.float64, device=DEV)
+    info = repart.solve(h, _t(c.b), x, tol=1e-9, precision="mixed_ru")
+    xs = x.cpu().numpy()
+    assert info["status"] == repart.RP_OK, info
+    assert c.true_rel_residual(xs) <= 1e-9
+    v32 = O.to_fp32(c.vals)
+    A32 = O.csr_matrix(c.map.row_ptr, c.map.col_idx, v32)
+    ref = O.mixed_reliable(c.A, A32, np.float32(1) / v32[c.map.diag_pos], c.b, tol=1e-9, delta=1e-5)
+    assert ref.status == O.OK
+    x64 = O.pcg(c.A, c.dinv, c.b, tol=1e-12).x
+    assert np.linalg.norm(xs - x64) / np.linalg.norm(x64) <= 1e-6
+    # FP32 rounding order differs from the oracle's: iteration counts agree loosely
+    assert abs(info["iterations"] - ref.iterations) <= 5 + 0.05 * ref.iterations, (info, ref.iterations)
+    h.close()
+
+
 def test_solve_edge_cases():
     c = Case((12, 10, 8), (2, 2, 1), sigma=0.5)
     h = repart.build_repartition(c.mesh.ranks, max_iter=5000)
@@ -251,7 +273,7 @@ def test_adjoint_and_gradients(symmetric):
     h.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ru"])
 def test_host_loop_matches_graph(precision):
     """The profiler-friendly host-driven loop runs the graph's kernels in the same order."""
     c = Case((20, 18, 16), (2, 2, 2), sigma=1.0, oracle_map=False)

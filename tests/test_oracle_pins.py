@@ -307,6 +307,53 @@ def test_mixed_refinement_reaches_fp64_residual():
     assert np.linalg.norm(b - A @ d.astype(np.float64)) / np.linalg.norm(b) > 1e-9
 
 
+def test_reliable_refinement_with_exact_inner_is_plain_pcg():
+    """With FP64 inner arithmetic every replaced residual equals the recursive
+    one up to rounding, so continuing the search direction must reproduce the
+    plain PCG run (iterations and solution); a restart or a wrong beta after a
+    replacement would not."""
+    mesh = synth.box_mesh(16, 14, 12, 2, 2, 1)
+    m, vals, A, dinv, _, _ = _system(mesh, 1.0)
+    b = synth.uniform_vector(mesh, 0)
+    ref = O.pcg(A, dinv, b, tol=1e-10)
+    for delta in (1e-1, 1e-3, 1e-5):
+        res = O.mixed_reliable(A, A, dinv, b, tol=1e-10, delta=delta, dtype=np.float64)
+        assert res.status == O.OK
+        # each replacement perturbs the residual by rounding only: at most ~1 extra iteration per two
+        assert abs(res.iterations - ref.iterations) <= 2 + res.outer_iterations // 2, \
+            (delta, res.iterations, ref.iterations, res.outer_iterations)
+        assert np.linalg.norm(res.x - ref.x) / np.linalg.norm(ref.x) < 1e-8
+        assert res.outer_iterations >= 1
+    # restarting the search direction at every refinement costs far more
+    # (the same steps with p = z after each replacement, written out here)
+    f = np.float64
+    x = np.zeros_like(b)
+    total = 0
+    for _ in range(50):
+        res_ = b - A @ x
+        if np.linalg.norm(res_) <= 1e-10 * np.linalg.norm(b):
+            break
+        d, it, _st = O.pcg_fp32(A, dinv, res_.astype(f), 1e-1, 10000)
+        x += d
+        total += it
+    assert total > ref.iterations + 20
+
+
+def test_reliable_refinement_fp32_reaches_fp64_residual():
+    mesh = synth.box_mesh(16, 16, 16, 2, 2, 2)
+    m, vals, A, dinv, _, _ = _system(mesh, 1.0)
+    v32 = O.to_fp32(vals)
+    A32 = O.csr_matrix(m.row_ptr, m.col_idx, v32)
+    dinv32 = np.float32(1.0) / v32[m.diag_pos]
+    b = synth.uniform_vector(mesh, 0)
+    x = np.linalg.solve(A.toarray(), b)
+    for delta in (1e-1, 1e-5):
+        res = O.mixed_reliable(A, A32, dinv32, b, tol=1e-9, delta=delta)
+        assert res.status == O.OK
+        assert np.linalg.norm(b - A @ res.x) / np.linalg.norm(b) <= 1e-9
+        assert np.linalg.norm(res.x - x) / np.linalg.norm(x) < 1e-6
+
+
 # ---------------------------------------------------------------- adjoint
 
 
