@@ -216,6 +216,8 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
     out = {"workload": "256 independent box systems, cells log-uniform in [8k, 300k], aspect ratios U[1,4], "
                        "lognormal(0,0.5) faces, Dirichlet at x=0, rhs U[-1,1], rel. residual 1e-9 from x=0",
            "systems": len(B.systems), "rows": B.n_rows, "nnz": h.nnz, "input_setup_s": round(setup_s, 1)}
+    sizes = [(m.n_cells, m.nnz()) for m in B.meshes]
+    hbm_peak, _ = load_peaks()
     c, t, ms = repart.batch_autotune(h, stg[0], b, x, tol=1e-9, precision="fp64")
     out["autotuned"] = {"cluster": c, "threads": t, "tuning_ms": round(ms, 2)}
     stream = torch.cuda.current_stream()
@@ -233,8 +235,20 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
         ms = e0.elapsed_time(e1) / steps
         bad = sum(1 for infos in infos_all for i in infos if i["status"] != 0)
         iters = [sum(i["iterations"] for i in infos) for infos in infos_all]
+        # algorithmic bytes of one step: update (24 B/entry + 20 B/row), every iteration
+        # (FP64: SpMV + 80 B/row; FP32: SpMV + 40 B/row), every FP64 residual pass
+        w = 8 if prec == "fp64" else 4
+        moved = 0.0
+        for infos in infos_all:
+            for s, inf in enumerate(infos):
+                nn, nz = sizes[s]
+                spmv = (w + 4) * nz + 4 * (nn + 1) + 2 * w * nn
+                res = 12 * nz + 4 * (nn + 1) + 40 * nn
+                moved += 24 * nz + 20 * nn + inf["iterations"] * (spmv + 10 * w * nn) + inf["passes"] * res
+        gbps = moved / len(infos_all) / (ms * 1e-3) / 1e9
         out[prec] = {"ms_per_step": round(ms, 3), "not_converged_systems": bad,
                      "iterations_sum_mean": statistics.mean(iters),
+                     "algorithmic_GBps": round(gbps, 1), "frac_of_hbm": round(gbps / hbm_peak, 4),
                      "max_rel_residual": max(i["rel_residual"] for infos in infos_all for i in infos)}
     h.close()
     # baseline: one handle per system, rp_update_values_packed + rp_solve in a loop
@@ -424,10 +438,27 @@ def run_ours(args):
     kernels["update"] = {"ms": round(upd_ms, 4), "GB/s": round(gbs(upd_bytes, upd_ms), 1),
                          "frac": round(gbs(upd_bytes, upd_ms) / hbm_peak, 4)}
 
+    # value update from a host buffer: H2D copy + permutation vs the permutation kernel
+    # gathering from host memory in place over the CPU-GPU link
+    update_paths = None
+    stg_pin = None
+    if not args.no_e2e:
+        stg_pin = [torch.from_numpy(s).pin_memory() for s in stg_host]
+        update_paths = {"device_buffer_ms": round(upd_ms, 3)}
+        for name, direct in (("host_copy_then_permute_ms", False), ("host_direct_gather_ms", True)):
+            repart.update_values_packed(h, stg_pin[0], direct=direct)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for t in range(reps):
+                repart.update_values_packed(h, stg_pin[t % draws], direct=direct)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            update_paths[name] = round(ev[0].elapsed_time(ev[1]) / reps, 3)
+        update_paths["host_bytes_per_update"] = 8 * n_slots
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        stg_pin = [torch.from_numpy(s).pin_memory() for s in stg_host]
         b_pin = torch.from_numpy(b_np).pin_memory()
         x_pin = torch.zeros(n, dtype=torch.float64).pin_memory()
         for t in range(max(1, args.warmup)):
@@ -494,7 +525,7 @@ def run_ours(args):
         "per_precision": results, "kernels": kernels, "roofline": roof,
         "roofline_other_spmv": {o: {"achieved": round(gbs(spmv_bytes(o), kern[o]["spmv"]), 1),
                                     "frac": round(gbs(spmv_bytes(o), kern[o]["spmv"]) / hbm_peak, 4)} for o in other},
-        "map_build_ms": round(build_ms, 1), "input_setup_s": round(setup_s, 1),
+        "map_build_ms": round(build_ms, 1), "input_setup_s": round(setup_s, 1), "update_paths": update_paths,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": results[head]["gpu_launches"], "batched": batched,
         "clocks": clocks[head], "clocks_other": {o: clocks[o] for o in other},
     }

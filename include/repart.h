@@ -52,7 +52,12 @@ typedef enum rp_status {
   RP_EUNSUPPORTED = 10   /* valid request this build does not serve           */
 } rp_status;
 
-enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1 };   /* where a buffer lives       */
+/* Where a buffer lives. RP_MEM_HOST_DIRECT (value updates only): host memory
+ * the GPU reads in place over the CPU-GPU link (pinned memory, or any host
+ * memory on systems with pageable-memory access such as Grace), with no copy
+ * into the staging buffer -- the analogue of sending the coefficients
+ * straight into the device buffer (Sec. 3, update procedure). */
+enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1, RP_MEM_HOST_DIRECT = 2 };
 /* Solve precision. RP_MIXED: FP64 iterative refinement around an FP32 PCG
  * that is restarted (p = z) at every refinement and solved to inner_tol.
  * RP_MIXED_RU: the same FP32 values, iterations and FP64 residual / update /

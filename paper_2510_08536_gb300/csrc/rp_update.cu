@@ -87,11 +87,29 @@ static rp_status permute_all(rp_handle* h, const double* buf, cudaStream_t s) {
 
 using namespace rp;
 
+// Can the current device read this host pointer in place?
+static rp_status check_host_direct(const void* p) {
+  cudaPointerAttributes attr{};
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) cudaGetLastError();
+  if (e == cudaSuccess && (attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeManaged ||
+                           attr.type == cudaMemoryTypeDevice))
+    return RP_OK;
+  int dev = 0, pageable = 0;
+  RP_TRY_CUDA(cudaGetDevice(&dev));
+  RP_TRY_CUDA(cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev));
+  if (!pageable)
+    return fail(RP_EUNSUPPORTED, "RP_MEM_HOST_DIRECT needs pinned host memory on a device without pageable-memory access");
+  return RP_OK;
+}
+
 extern "C" rp_status rp_update_values_packed(rp_handle* h, const double* buffer, int32_t where, void* stream) {
   if (!h || (!buffer && h->n_slots > 0)) return fail(RP_EINVAL, "null argument");
-  if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
+  if (where != RP_MEM_DEVICE && where != RP_MEM_HOST && where != RP_MEM_HOST_DIRECT)
+    return fail(RP_EINVAL, "where must be RP_MEM_DEVICE, RP_MEM_HOST or RP_MEM_HOST_DIRECT");
   cudaStream_t s = (cudaStream_t)stream;
   const double* src = buffer;
+  if (where == RP_MEM_HOST_DIRECT && h->n_slots > 0) RP_TRY(check_host_direct(buffer));
   if (where == RP_MEM_HOST) {
     if (h->n_slots > 0)
       RP_TRY_CUDA(cudaMemcpyAsync(h->staging, buffer, sizeof(double) * h->n_slots, cudaMemcpyHostToDevice, s));

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "librepart.so")
 
 RP_OK, RP_EINVAL, RP_EDUP, RP_ERANGE, RP_EOVERFLOW, RP_ENOMEM, RP_ECUDA = range(7)
 RP_NOT_CONVERGED, RP_BREAKDOWN, RP_DEVICE_TIMEOUT, RP_EUNSUPPORTED = 7, 8, 9, 10
-RP_MEM_DEVICE, RP_MEM_HOST = 0, 1
+RP_MEM_DEVICE, RP_MEM_HOST, RP_MEM_HOST_DIRECT = 0, 1, 2
 RP_FP64, RP_MIXED, RP_MIXED_RU = 0, 1, 2
 PRECISIONS = {"fp64": RP_FP64, "mixed": RP_MIXED, "mixed_ru": RP_MIXED_RU}
 
@@ -231,12 +231,14 @@ def get_values(h: Handle) -> dict:
                 dinv=_view(dinv.value, h.n, "<f8"))
 
 
-def update_values_packed(h: Handle, buffer, stream=None):
+def update_values_packed(h: Handle, buffer, stream=None, direct: bool = False):
+    """rp_update_values_packed; a host buffer is copied to the device first, or
+    read in place by the permutation kernel when ``direct``."""
     _f64(buffer, "buffer")
     if buffer.numel() != h.n_slots:
         raise ValueError(f"buffer has {buffer.numel()} values, the handle needs {h.n_slots}")
-    _check(load().rp_update_values_packed(h.ptr, _ptr(buffer), _where(buffer), _stream(stream)),
-           "rp_update_values_packed")
+    where = RP_MEM_HOST_DIRECT if (direct and not buffer.is_cuda) else _where(buffer)
+    _check(load().rp_update_values_packed(h.ptr, _ptr(buffer), where, _stream(stream)), "rp_update_values_packed")
 
 
 def update_values(h: Handle, diag, upper, lower, iface, stream=None):

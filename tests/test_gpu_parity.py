@@ -108,6 +108,27 @@ def test_update_bit_exact(symmetric):
     h.close()
 
 
+def test_update_reads_host_memory_in_place():
+    """RP_MEM_HOST_DIRECT: the permutation kernel gathers from host memory over
+    the CPU-GPU link; the values are the same bits as from a device buffer."""
+    c = Case((24, 20, 16), (3, 2, 2), sigma=1.0)
+    h = repart.build_repartition(c.mesh.ranks)
+    repart.update_values_packed(h, torch.from_numpy(c.staging).pin_memory(), direct=True)
+    v = repart.get_values(h)
+    np.testing.assert_array_equal(v["vals"].cpu().numpy(), c.vals)
+    np.testing.assert_array_equal(v["dinv"].cpu().numpy(), c.dinv)
+    # pageable memory: read in place where the device can (Grace), refused otherwise
+    stg2 = c.asm.staging(synth.face_coeffs(c.mesh, 1.0, 101))
+    try:
+        repart.update_values_packed(h, torch.from_numpy(stg2), direct=True)
+    except repart.RepartError as e:
+        assert e.status == repart.RP_EUNSUPPORTED
+    else:
+        np.testing.assert_array_equal(repart.get_values(h)["vals"].cpu().numpy(),
+                                      O.update_values(c.map.src_of, stg2))
+    h.close()
+
+
 def test_spmv_parity():
     c = Case((30, 20, 17), (3, 2, 1), sigma=1.0)
     h = repart.build_repartition(c.mesh.ranks)
