@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="run only the batched form (default launch shape, no loop baseline): profiling runs")
+    ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solve kernels from the host (for profilers; not a timing mode)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -206,22 +209,24 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
 
     from paper_2510_08536_gb300 import repart, synth
     t0 = time.time()
-    B = synth.Batch(256, 8000, 300000, seed=0)
+    B = synth.Batch(args.batch_systems, 8000, 300000, seed=0)
     draws = 2
     stg = [torch.from_numpy(B.staging(0.5, 100 + t)).to(dev) for t in range(draws)]
     b = torch.from_numpy(B.rhs(0)).to(dev)
     x = torch.zeros(B.n_rows, dtype=torch.float64, device=dev)
     setup_s = time.time() - t0
     h = repart.batch_build(B.systems)
-    out = {"workload": "256 independent box systems, cells log-uniform in [8k, 300k], aspect ratios U[1,4], "
-                       "lognormal(0,0.5) faces, Dirichlet at x=0, rhs U[-1,1], rel. residual 1e-9 from x=0",
+    out = {"workload": f"{len(B.systems)} independent box systems, cells log-uniform in [8k, 300k], aspect "
+                       "ratios U[1,4], lognormal(0,0.5) faces, Dirichlet at x=0, rhs U[-1,1], rel. residual 1e-9 "
+                       "from x=0",
            "systems": len(B.systems), "rows": B.n_rows, "nnz": h.nnz, "input_setup_s": round(setup_s, 1)}
     sizes = [(m.n_cells, m.nnz()) for m in B.meshes]
     hbm_peak, _ = load_peaks()
-    c, t, ms = repart.batch_autotune(h, stg[0], b, x, tol=1e-9, precision="fp64")
-    out["autotuned"] = {"cluster": c, "threads": t, "tuning_ms": round(ms, 2)}
+    if not args.only_batch:
+        c, t, ms = repart.batch_autotune(h, stg[0], b, x, tol=1e-9, precision="fp64")
+        out["autotuned"] = {"cluster": c, "threads": t, "tuning_ms": round(ms, 2)}
     stream = torch.cuda.current_stream()
-    for prec in ("fp64", "mixed", "mixed_ru"):
+    for prec in ([args.only] if args.only else ("fp64", "mixed", "mixed_ru")):
         for i in range(warmup):
             repart.batch_update_solve(h, stg[i % draws], b, x, 1e-9, prec)
         torch.cuda.synchronize()
@@ -251,6 +256,8 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
                      "algorithmic_GBps": round(gbps, 1), "frac_of_hbm": round(gbps / hbm_peak, 4),
                      "max_rel_residual": max(i["rel_residual"] for infos in infos_all for i in infos)}
     h.close()
+    if args.only_batch:
+        return out
     # baseline: one handle per system, rp_update_values_packed + rp_solve in a loop
     handles = [repart.build_repartition([s]) for s in B.systems]
     offs, so = [], 0
@@ -374,28 +381,6 @@ def run_ours(args):
             "not_converged_steps": len(bad),
             "gpu_launches": sum(launches(prec, i) for i in infos),
         }
-
-    # continued refinement with a residual replacement every decade (delta = 0.1) instead of
-    # the configured inner tolerance: a tuned variant, reported next to the headline
-    ru_tuned = None
-    if "mixed_ru" in precs and not args.only:
-        repart.set_solver_options(h, ru_delta=0.1)
-        for t in range(max(1, args.warmup)):
-            step(t, "mixed_ru", stg_dev, b, x)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        infos = []
-        e0.record(stream)
-        for t in range(args.steps):
-            infos.append(step(args.warmup + t, "mixed_ru", stg_dev, b, x))
-        e1.record(stream)
-        barrier()
-        ru_tuned = {"ru_delta": 0.1, "ms_per_step": round(e0.elapsed_time(e1) / (args.steps * world), 3),
-                    "iterations_mean": statistics.mean(i["iterations"] for i in infos),
-                    "outer_mean": statistics.mean(i["outer_iterations"] for i in infos),
-                    "max_rel_residual": max(i["rel_residual"] for i in infos),
-                    "not_converged_steps": sum(1 for i in infos if i["status"] != 0)}
-        repart.set_solver_options(h, ru_delta=0.0)
 
     # kernel durations (CUDA events on the launching stream, same kernels as the graph runs)
     kern = {}
@@ -521,7 +506,7 @@ def run_ours(args):
         "fp64_ms_per_step": round(results["fp64"]["ms_per_step"], 3) if "fp64" in results else None,
         "mixed_ms_per_step": round(results["mixed"]["ms_per_step"], 3) if "mixed" in results else None,
         "mixed_ru_ms_per_step": round(results["mixed_ru"]["ms_per_step"], 3) if "mixed_ru" in results else None,
-        "mixed_ru_delta_0.1": ru_tuned,
+        "mixed_ru_delta": 0.1,
         "per_precision": results, "kernels": kernels, "roofline": roof,
         "roofline_other_spmv": {o: {"achieved": round(gbs(spmv_bytes(o), kern[o]["spmv"]), 1),
                                     "frac": round(gbs(spmv_bytes(o), kern[o]["spmv"]) / hbm_peak, 4)} for o in other},
@@ -565,6 +550,13 @@ def main():
     if args.oracle_sample:
         a = json.loads(args.oracle_sample)
         print(json.dumps(oracle_sample(a["workload"], a["seeds"], a["iters"], a["counts"])))
+        return
+    if args.only_batch and args.impl == "ours":
+        import torch
+        from paper_2510_08536_gb300 import repart
+        torch.cuda.set_device(0)
+        repart.load()
+        print(json.dumps({"batched": run_batch(args, torch.device("cuda", 0), steps=args.steps, warmup=args.warmup)}))
         return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

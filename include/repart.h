@@ -62,9 +62,9 @@ enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1, RP_MEM_HOST_DIRECT = 2 };
  * that is restarted (p = z) at every refinement and solved to inner_tol.
  * RP_MIXED_RU: the same FP32 values, iterations and FP64 residual / update /
  * convergence test, but the FP32 PCG is not restarted: when its recursive
- * residual has fallen by inner_tol (or reaches the outer target) its iterate
- * is added to x in FP64, the FP64 residual replaces the FP32 one and the
- * search direction continues (p = z + beta p). */
+ * residual has fallen by ru_delta (or below half the outer target) its
+ * iterate is added to x in FP64, the FP64 residual replaces the FP32 one and
+ * the search direction continues (p = z + beta p). */
 enum { RP_FP64 = 0, RP_MIXED = 1, RP_MIXED_RU = 2 };
 
 typedef struct rp_handle rp_handle;
@@ -105,7 +105,7 @@ typedef struct rp_options {
                              graphs with conditional nodes)                       */
   int32_t reserved;
   double ru_delta;        /* RP_MIXED_RU: residual reduction between two FP64
-                             refinements (0: use inner_tol)                       */
+                             refinements (default 0.1; 0: use inner_tol)          */
 } rp_options;
 
 /* Replace the solver settings of a handle (max_iter, max_outer, max_restarts,
@@ -115,7 +115,7 @@ rp_status rp_set_solver_options(rp_handle* h, const rp_options* opts);
 
 /* Defaults: n_parts 1, general (non-symmetric) storage, FP32 copy on,
  * transpose off, max_iter 20000, max_outer 30, max_restarts 8, current
- * device, inner_tol 1e-5, spin_limit 1<<26. */
+ * device, inner_tol 1e-5, spin_limit 1<<26, host_loop 0, ru_delta 0.1. */
 void rp_default_options(rp_options* opts);
 
 /* Sec. 3 steps 1-3 and the three outputs (sparsity pattern, update pattern,

@@ -448,8 +448,8 @@ def mixed_reliable(A64, A_in, dinv_in, b, tol=1e-9, delta=1e-5, max_iter=20000, 
     The inner CG runs in ``dtype`` on A_in (values, vectors, products; dot
     products accumulated in FP64, alpha and beta rounded to ``dtype``). When
     its recursive residual has fallen below ``delta`` times the residual at the
-    last refinement (or below the outer target tol ||b||), the inner iterate d
-    is added to the FP64 solution
+    last refinement (or below half the outer target tol ||b||), the inner
+    iterate d is added to the FP64 solution
     (x += d, d = 0), the FP64 residual r = b - A64 x is computed and the
     convergence test ||r|| <= tol ||b|| is taken on it; otherwise r replaces
     the inner residual and the iteration CONTINUES with p = z + beta p,
@@ -463,7 +463,14 @@ def mixed_reliable(A64, A_in, dinv_in, b, tol=1e-9, delta=1e-5, max_iter=20000, 
     thresh = tol * tol * bb
     r = b.astype(f)
     r64 = r.astype(np.float64)
-    inner = delta * delta * float(r64 @ r64)
+
+    def phase_end(start_rr):
+        # the inner tolerance, or half the outer target: a residual just above
+        # the target must still make real progress, so it cannot trigger
+        # endless one-step phases
+        return max(delta * delta * start_rr, 0.25 * thresh)
+
+    inner = phase_end(float(r64 @ r64))
     z = dinv_in * r
     p = z.copy()
     rz = float(r64 @ z.astype(np.float64))
@@ -482,9 +489,7 @@ def mixed_reliable(A64, A_in, dinv_in, b, tol=1e-9, delta=1e-5, max_iter=20000, 
         r -= alpha * q
         it += 1
         r64 = r.astype(np.float64)
-        # a phase ends at the inner tolerance, or when the inner residual
-        # already meets the outer target (then the FP64 test decides)
-        if float(r64 @ r64) <= max(inner, thresh) or it >= max_iter:
+        if float(r64 @ r64) <= inner or it >= max_iter:
             x += d.astype(np.float64)
             d[:] = 0
             res = b - A64 @ x
@@ -497,7 +502,7 @@ def mixed_reliable(A64, A_in, dinv_in, b, tol=1e-9, delta=1e-5, max_iter=20000, 
                 break
             r = res.astype(f)
             r64 = r.astype(np.float64)
-            inner = delta * delta * float(r64 @ r64)
+            inner = phase_end(float(r64 @ r64))
         z = dinv_in * r
         rz_new = float(r64 @ z.astype(np.float64))
         beta = f(rz_new / rz)

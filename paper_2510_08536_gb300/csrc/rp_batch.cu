@@ -66,20 +66,66 @@ __device__ __forceinline__ void team_sum(double (&v)[NV], double (&tot)[NV], cg:
   parity ^= 1;
 }
 
+// Index arrays are never written in the kernel (read-only path); values and
+// vectors are written inside it and are read with coherent loads.
 template <typename T>
 __device__ __forceinline__ T row_dot_coherent(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                               const T* vals, const T* x, int64_t i) {
-  const int s = rp[i], e = rp[i + 1];
+  const int s = __ldg(rp + i), e = __ldg(rp + i + 1);
   T sum = T(0);
-  for (int j = s; j < e; ++j) sum = fma(vals[j], x[col[j]], sum);
+  for (int j = s; j < e; ++j) sum = fma(vals[j], x[__ldg(col + j)], sum);
   return sum;
+}
+
+// y_i = (A x)_i for rows [i0, i1) of this CTA, two independent rows per thread
+// in flight (rows i and i + blockDim, so each warp stays coalesced); f(i, y_i)
+// consumes every result.
+template <typename T, typename F>
+__device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                          const T* vals, const T* x, int64_t i0, int64_t i1, F&& f) {
+  const int64_t nth = blockDim.x;
+  int64_t i = i0 + threadIdx.x;
+  for (; i + nth < i1; i += 2 * nth) {
+    const int64_t k = i + nth;
+    const int s0 = __ldg(rp + i), e0 = __ldg(rp + i + 1);
+    const int s1 = __ldg(rp + k), e1 = __ldg(rp + k + 1);
+    T a0 = T(0), a1 = T(0);
+    const int m = max(e0 - s0, e1 - s1);
+    for (int t = 0; t < m; ++t) {
+      if (s0 + t < e0) a0 = fma(vals[s0 + t], x[__ldg(col + s0 + t)], a0);
+      if (s1 + t < e1) a1 = fma(vals[s1 + t], x[__ldg(col + s1 + t)], a1);
+    }
+    f(i, a0);
+    f(k, a1);
+  }
+  for (; i < i1; i += nth) f(i, row_dot_coherent<T>(rp, col, vals, x, i));
+}
+
+// Visit rows [i0, i1) of a system whose first row has global index ro: fv(v)
+// for every W-wide vector v (global vector index, 16-byte aligned) inside the
+// range, fs(i) for the ragged rows at either end.
+template <int W, typename FS, typename FV>
+__device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, FS&& fs, FV&& fv) {
+  const int64_t nth = blockDim.x, tid = threadIdx.x;
+  const int64_t g0 = ro + i0, g1 = ro + i1;
+  const int64_t v0 = (g0 + W - 1) / W, v1 = g1 / W;
+  if (v0 >= v1) {
+    for (int64_t i = i0 + tid; i < i1; i += nth) fs(i);
+    return;
+  }
+  for (int64_t g = g0 + tid; g < v0 * W; g += nth) fs(g - ro);
+  for (int64_t v = v0 + tid; v < v1; v += nth) fv(v);
+  for (int64_t g = v1 * W + tid; g < g1; g += nth) fs(g - ro);
 }
 
 }  // namespace
 
 // MODE: 0 FP64 PCG, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG
 template <int MODE>
-__global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
+#ifndef RP_BATCH_MIN_BLOCKS
+#define RP_BATCH_MIN_BLOCKS 2  // CTAs of kBatchMaxThreads per SM the register budget must allow
+#endif
+__global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch(BatchArgs a) {
   constexpr bool MIXED = MODE != 0;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned T = cl.num_blocks();
@@ -92,6 +138,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
   const double* __restrict__ bufall = a.io->buf;
   const double* __restrict__ ball = a.io->b;
   double* __restrict__ xall = a.io->x;
+  const bool xvec = (reinterpret_cast<uintptr_t>(xall) & 15) == 0;  // caller's x: vectorise only if aligned
 
   for (;;) {
     if (me == 0 && threadIdx.x == 0) s_next = (int)atomicAdd(a.queue, 1u);
@@ -174,21 +221,34 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
         for (;;) {
           cl.sync();  // p of every row visible to the team
           double v1[1] = {0.0}, t1[1];
-          for (int64_t i = i0 + tid; i < i1; i += nth) {
-            const double qi = row_dot_coherent<double>(rp, col, vals, p, i);
+          spmv_rows<double>(rp, col, vals, p, i0, i1, [&](int64_t i, double qi) {
             q[i] = qi;
             v1[0] = fma(p[i], qi, v1[0]);
-          }
+          });
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; break; }
           const double alpha = rz / t1[0];
           double v2[2] = {0.0, 0.0}, t2[2];
-          for (int64_t i = i0 + tid; i < i1; i += nth) {
-            const double ri = fma(-alpha, q[i], r[i]);
-            r[i] = ri;
-            v2[0] = fma(ri, dinv[i] * ri, v2[0]);
-            v2[1] = fma(ri, ri, v2[1]);
-          }
+          rows_vec<2>(
+              ro, i0, i1,
+              [&](int64_t i) {
+                const double ri = fma(-alpha, q[i], r[i]);
+                r[i] = ri;
+                v2[0] = fma(ri, dinv[i] * ri, v2[0]);
+                v2[1] = fma(ri, ri, v2[1]);
+              },
+              [&](int64_t v) {
+                const double2 qv = reinterpret_cast<const double2*>(a.q)[v];
+                double2 rv = reinterpret_cast<const double2*>(a.r)[v];
+                const double2 dv = reinterpret_cast<const double2*>(a.dinv)[v];
+                rv.x = fma(-alpha, qv.x, rv.x);
+                rv.y = fma(-alpha, qv.y, rv.y);
+                reinterpret_cast<double2*>(a.r)[v] = rv;
+                v2[0] = fma(rv.x, dv.x * rv.x, v2[0]);
+                v2[0] = fma(rv.y, dv.y * rv.y, v2[0]);
+                v2[1] = fma(rv.x, rv.x, v2[1]);
+                v2[1] = fma(rv.y, rv.y, v2[1]);
+              });
           team_sum<2>(v2, t2, cl, spart, swarp, parity);
           ++iters;
           rr = t2[1];
@@ -197,10 +257,28 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           if (t2[1] <= thresh || iters >= a.max_iter) stop = true;
           else if (!(t2[0] > 0.0) || !isfinite(t2[0])) { stop = true; status = RP_BREAKDOWN; }
           else { beta = t2[0] / rz; rz = t2[0]; }
-          for (int64_t i = i0 + tid; i < i1; i += nth) {
+          auto upd = [&](int64_t i) {
             const double pi = p[i];
             x[i] = fma(alpha, pi, x[i]);
             if (!stop) p[i] = fma(beta, pi, dinv[i] * r[i]);
+          };
+          if (xvec) {
+            rows_vec<2>(ro, i0, i1, upd, [&](int64_t v) {
+              double2 pv = reinterpret_cast<const double2*>(a.p)[v];
+              double2 xv = reinterpret_cast<const double2*>(xall)[v];
+              xv.x = fma(alpha, pv.x, xv.x);
+              xv.y = fma(alpha, pv.y, xv.y);
+              reinterpret_cast<double2*>(xall)[v] = xv;
+              if (!stop) {
+                const double2 rv = reinterpret_cast<const double2*>(a.r)[v];
+                const double2 dv = reinterpret_cast<const double2*>(a.dinv)[v];
+                pv.x = fma(beta, pv.x, dv.x * rv.x);
+                pv.y = fma(beta, pv.y, dv.y * rv.y);
+                reinterpret_cast<double2*>(a.p)[v] = pv;
+              }
+            });
+          } else {
+            for (int64_t i = i0 + tid; i < i1; i += nth) upd(i);
           }
           if (stop) break;
         }
@@ -256,29 +334,44 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           for (int64_t i = i0 + tid; i < i1; i += nth) p[i] = fmaf(beta, p[i], dinv32[i] * r[i]);
         }
         rz = t4[0];
-        const double ithresh = RU ? fmax(a.ru_delta * a.ru_delta * t4[3], thresh)
+        const double ithresh = RU ? fmax(a.ru_delta * a.ru_delta * t4[3], 0.25 * thresh)
                                   : a.inner_tol * a.inner_tol * t4[3];
         int it = 0;
         bool broke = false;
         for (;;) {
           cl.sync();
           float acc = 0.f;
-          for (int64_t i = i0 + tid; i < i1; i += nth) {
-            const float qi = row_dot_coherent<float>(rp, col, vals32, p, i);
+          spmv_rows<float>(rp, col, vals32, p, i0, i1, [&](int64_t i, float qi) {
             q[i] = qi;
             acc = fmaf(p[i], qi, acc);
-          }
+          });
           double v1[1] = {(double)acc}, t1[1];
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; broke = true; break; }
           const float alpha = (float)(rz / t1[0]);
           float a0 = 0.f, a1 = 0.f;
-          for (int64_t i = i0 + tid; i < i1; i += nth) {
-            const float ri = fmaf(-alpha, q[i], r[i]);
-            r[i] = ri;
-            a0 = fmaf(ri, dinv32[i] * ri, a0);
-            a1 = fmaf(ri, ri, a1);
-          }
+          auto rstep = [&](float& rv, float qv, float dv) {
+            rv = fmaf(-alpha, qv, rv);
+            a0 = fmaf(rv, dv * rv, a0);
+            a1 = fmaf(rv, rv, a1);
+          };
+          rows_vec<4>(
+              ro, i0, i1,
+              [&](int64_t i) {
+                float ri = r[i];
+                rstep(ri, q[i], dinv32[i]);
+                r[i] = ri;
+              },
+              [&](int64_t v) {
+                const float4 qv = reinterpret_cast<const float4*>(a.q32)[v];
+                float4 rv = reinterpret_cast<const float4*>(a.r32)[v];
+                const float4 dv = reinterpret_cast<const float4*>(a.dinv32)[v];
+                rstep(rv.x, qv.x, dv.x);
+                rstep(rv.y, qv.y, dv.y);
+                rstep(rv.z, qv.z, dv.z);
+                rstep(rv.w, qv.w, dv.w);
+                reinterpret_cast<float4*>(a.r32)[v] = rv;
+              });
           double v2[2] = {(double)a0, (double)a1}, t2[2];
           team_sum<2>(v2, t2, cl, spart, swarp, parity);
           ++it;
@@ -288,13 +381,36 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           if (t2[1] <= ithresh || (RU ? iters : it) >= a.max_iter) stop = true;
           else if (!(t2[0] > 0.0) || !isfinite(t2[0])) { stop = true; status = RP_BREAKDOWN; broke = true; }
           else { beta = (float)(t2[0] / rz); rz = t2[0]; }
-          for (int64_t i = i0 + tid; i < i1; i += nth) {
-            const float pi = p[i];
-            d[i] = fmaf(alpha, pi, d[i]);
-            if (!stop) p[i] = fmaf(beta, pi, dinv32[i] * r[i]);
-          }
+          rows_vec<4>(
+              ro, i0, i1,
+              [&](int64_t i) {
+                const float pi = p[i];
+                d[i] = fmaf(alpha, pi, d[i]);
+                if (!stop) p[i] = fmaf(beta, pi, dinv32[i] * r[i]);
+              },
+              [&](int64_t v) {
+                float4 pv = reinterpret_cast<const float4*>(a.p32)[v];
+                float4 dd = reinterpret_cast<const float4*>(a.d32)[v];
+                dd.x = fmaf(alpha, pv.x, dd.x);
+                dd.y = fmaf(alpha, pv.y, dd.y);
+                dd.z = fmaf(alpha, pv.z, dd.z);
+                dd.w = fmaf(alpha, pv.w, dd.w);
+                reinterpret_cast<float4*>(a.d32)[v] = dd;
+                if (!stop) {
+                  const float4 rv = reinterpret_cast<const float4*>(a.r32)[v];
+                  const float4 iv = reinterpret_cast<const float4*>(a.dinv32)[v];
+                  pv.x = fmaf(beta, pv.x, iv.x * rv.x);
+                  pv.y = fmaf(beta, pv.y, iv.y * rv.y);
+                  pv.z = fmaf(beta, pv.z, iv.z * rv.z);
+                  pv.w = fmaf(beta, pv.w, iv.w * rv.w);
+                  reinterpret_cast<float4*>(a.p32)[v] = pv;
+                }
+              });
           if (stop) break;
         }
+        // d was written with the vector mapping of rows_vec; the correction reads it
+        // row by row, so every thread of the CTA must have finished its writes
+        __syncthreads();
         if (!broke) {
           for (int64_t i = i0 + tid; i < i1; i += nth) x[i] += (double)d[i];
         }

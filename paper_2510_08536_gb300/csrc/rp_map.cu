@@ -433,7 +433,7 @@ extern "C" void rp_default_options(rp_options* o) {
   o->device = -1;
   o->inner_tol = 1e-5;
   o->spin_limit = 1LL << 26;
-  o->ru_delta = 0.0;
+  o->ru_delta = 0.1;
 }
 
 extern "C" const char* rp_last_error(void) { return rp::g_last_error.c_str(); }

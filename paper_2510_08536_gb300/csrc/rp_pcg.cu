@@ -332,7 +332,9 @@ __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
         // the FP64 residual replaces the FP32 one; the search direction continues
         c->ru_apply = first ? 0 : 1;
         c->beta_ru = first ? 0.0 : tot[0] / c->rz;
-        c->inner_thresh = fmax(c->ru_delta * c->ru_delta * tot[3], c->thresh);
+        // inner tolerance, or half the outer target (a residual just above the
+        // target must still make progress: no endless one-step phases)
+        c->inner_thresh = fmax(c->ru_delta * c->ru_delta * tot[3], 0.25 * c->thresh);
       } else {
         c->inner_thresh = c->inner_tol * c->inner_tol * tot[3];
         c->iter = 0;
