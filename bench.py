@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--only-batch", action="store_true",
                     help="run only the batched form (default launch shape, no loop baseline): profiling runs")
     ap.add_argument("--batch-systems", type=int, default=256)
+    ap.add_argument("--alpha-sweep", action="store_true",
+                    help="repartitioning-ratio study at 128^3: GPU parts and CPU ranks merged")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solve kernels from the host (for profilers; not a timing mode)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -288,6 +290,59 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
     del stg
     torch.cuda.empty_cache()
     return out
+
+
+# ---------------------------------------------------------------- alpha sweep
+
+
+def run_alpha_sweep(args, dev):
+    """Single-GPU analogue of the paper's repartitioning-ratio study (Sec. 4): the
+    128^3 mesh decomposed into k = 64 CPU ranks, solved as n_parts = 64 / alpha GPU
+    parts (local + non-local matrices, halo gathered on the device), and, at one part,
+    with k = 1 .. 512 CPU ranks merged."""
+    import torch
+
+    from paper_2510_08536_gb300 import repart, synth
+    stream = torch.cuda.current_stream()
+
+    def measure(mesh, n_parts, stg, b):
+        t0 = time.perf_counter()
+        h = repart.build_repartition(mesh.ranks, n_parts=n_parts)
+        build_ms = 1e3 * (time.perf_counter() - t0)
+        nl = sum(repart.get_part_map(h, p)["nl_nnz"] for p in range(n_parts))
+        repart.update_values_packed(h, stg)
+        out = {"n_parts": n_parts, "k": mesh.k, "map_build_ms": round(build_ms, 1), "nonlocal_entries": nl,
+               "spmv_fp64_ms": round(repart.profile_iteration(h, b, "fp64", iters=10)["spmv"], 4),
+               "spmv_fp32_ms": round(repart.profile_iteration(h, b, "mixed", iters=10)["spmv"], 4)}
+        x = torch.zeros(mesh.n_cells, dtype=torch.float64, device=dev)
+        for prec in ("fp64", "mixed_ru"):
+            repart.solve(h, b, x, tol=1e-9, precision=prec)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = repart.solve(h, b, x, tol=1e-9, precision=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[prec] = {"ms": round(e0.elapsed_time(e1), 2), "iterations": info["iterations"],
+                         "status": info["status"]}
+        h.close()
+        return out
+
+    res = {"workload": "128^3 cells, lognormal(0,0.5) faces seed 100, rhs U[-1,1] seed 0, rel. residual 1e-9",
+           "alpha_sweep": [], "k_sweep": []}
+    mesh = synth.box_mesh(128, 128, 128, 4, 4, 4)
+    a = synth.face_coeffs(mesh, 0.5, 100)
+    stg = torch.from_numpy(synth.Assembler(mesh).staging(a)).to(dev)
+    b = torch.from_numpy(synth.uniform_vector(mesh, 0)).to(dev)
+    for n_parts in (1, 2, 4, 8, 16, 32, 64):
+        r = measure(mesh, n_parts, stg, b)
+        r["alpha"] = mesh.k // n_parts
+        res["alpha_sweep"].append(r)
+    for p in ((1, 1, 1), (2, 2, 2), (4, 4, 4), (8, 8, 8)):
+        mesh = synth.box_mesh(128, 128, 128, *p)
+        stg = torch.from_numpy(synth.Assembler(mesh).staging(a)).to(dev)
+        b = torch.from_numpy(synth.uniform_vector(mesh, 0)).to(dev)
+        res["k_sweep"].append(measure(mesh, 1, stg, b))
+    return res
 
 
 # ---------------------------------------------------------------- ours
@@ -550,6 +605,13 @@ def main():
     if args.oracle_sample:
         a = json.loads(args.oracle_sample)
         print(json.dumps(oracle_sample(a["workload"], a["seeds"], a["iters"], a["counts"])))
+        return
+    if args.alpha_sweep and args.impl == "ours":
+        import torch
+        from paper_2510_08536_gb300 import repart
+        torch.cuda.set_device(0)
+        repart.load()
+        print(json.dumps(run_alpha_sweep(args, torch.device("cuda", 0))))
         return
     if args.only_batch and args.impl == "ours":
         import torch

@@ -173,7 +173,7 @@ rp_status rp_update_values(rp_handle* h, const double* const* diag, const double
 rp_status rp_get_values(const rp_handle* h, const double** vals, const float** vals32,
                         const double** dinv);
 
-/* y = A x with the merged FP64 matrix (n_parts == 1); if xy is not NULL the
+/* y = A x with the FP64 values (local + non-local for n_parts > 1); if xy is not NULL the
  * device double *xy receives x.y. x, y, xy are device pointers. Uses the
  * handle's reduction scratch. Asynchronous. */
 rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* xy, void* stream);
@@ -206,8 +206,11 @@ typedef struct rp_solve_info {
   double rel_residual;      /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
 } rp_solve_info;
 
-/* Solve A x = b for the merged matrix (n_parts == 1) to
- * ||b - A x||_2 <= tol ||b||_2 (true residual, FP64).
+/* Solve A x = b to ||b - A x||_2 <= tol ||b||_2 (true residual, FP64).
+ * With n_parts > 1 every product runs over each part's local matrix plus
+ * its non-local matrix, whose halo values are gathered from x on the device
+ * (the distributed layout of Sec. 3 on one GPU); the result is the same
+ * system's solution.
  * precision RP_FP64: Jacobi-PCG in FP64. RP_MIXED: iterative refinement with
  * the residual, the update x += d and the convergence test in FP64 and the
  * inner Jacobi-PCG on the FP32 values to inner_tol (needs want_fp32).

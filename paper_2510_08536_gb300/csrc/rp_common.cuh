@@ -85,6 +85,23 @@ struct Graphs {
   cudaGraphExec_t adjoint = nullptr;
 };
 
+// The matrix split into GPU parts (Sec. 3): per part a local CSR over the
+// part's own rows and columns and a non-local CSR whose compressed columns
+// map to global rows through nl_cols (the halo). n == 1: merged matrix, the
+// other fields are unused.
+template <typename T>
+struct Parts {
+  int32_t n;
+  const int64_t* row_off;    // [n+1] first global row of each part
+  const int64_t* nnz_off;    // [n+1] local entries
+  const int64_t* nl_off;     // [n+1] non-local entries
+  const int64_t* nlcol_off;  // [n+1] compressed non-local columns
+  const int32_t* nl_row_ptr; // per-part segments (row_off[p] + p)
+  const int32_t* nl_col;     // compressed column of each non-local entry
+  const int32_t* nl_cols;    // global row behind each compressed column
+  const T* nl_vals;
+};
+
 // Per-call pointers of the batched solve (read by the captured kernel).
 struct BatchIO {
   const double* buf;
@@ -165,6 +182,9 @@ struct rp_handle {
   double* vals = nullptr;     // nnz (+pad)
   float* vals32 = nullptr;    // nnz (+pad)
   double* nl_vals = nullptr;
+  float* nl_vals32 = nullptr;
+  int64_t *d_part_row_off = nullptr, *d_part_nnz_off = nullptr;  // part tables on the device
+  int64_t *d_part_nl_off = nullptr, *d_part_nlcol_off = nullptr;
   double* valsT = nullptr;    // transposed values (adjoint, on demand)
   double* dinv = nullptr;     // n
   float* dinv32 = nullptr;    // n

@@ -459,7 +459,8 @@ static void free_handle_memory(rp_handle* h) {
   void* ptrs[] = {h->row_ptr, h->col_idx, h->src_of, h->diag_pos, h->tpos, h->nl_row_ptr, h->nl_col_idx,
                   h->nl_src_of, h->nl_cols, h->d_row_off, h->d_slot_off, h->d_face_off, h->d_iface_off,
                   h->d_lower, h->d_upper, h->d_iface_row, h->d_iface_gcol, h->d_out_off, h->staging, h->vals,
-                  h->vals32, h->nl_vals, h->valsT, h->dinv, h->dinv32, h->dinvT};
+                  h->vals32, h->nl_vals, h->valsT, h->dinv, h->dinv32, h->dinvT, h->nl_vals32,
+                  h->d_part_row_off, h->d_part_nnz_off, h->d_part_nl_off, h->d_part_nlcol_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_solver(h);
@@ -750,8 +751,22 @@ extern "C" rp_status rp_build_repartition(const rp_ldu_desc* ranks, int32_t k, c
   CU(cudaMemsetAsync(H->staging, 0, 8 * (H->n_slots + pad), st));
   if (H->want_fp32) {
     ALLOC(H->vals32, H->nnz + pad);
+    ALLOC(H->nl_vals32, H->nl_nnz + pad);
     ALLOC(H->dinv32, n + pad);
     CU(cudaMemsetAsync(H->vals32, 0, 4 * (H->nnz + pad), st));
+  }
+  // part tables for solves over the local + non-local matrices
+  {
+    const int np1 = o.n_parts + 1;
+    std::vector<int64_t> nlcol(H->part_nlcol_off.begin(), H->part_nlcol_off.end());
+    ALLOC(H->d_part_row_off, np1);
+    ALLOC(H->d_part_nnz_off, np1);
+    ALLOC(H->d_part_nl_off, np1);
+    ALLOC(H->d_part_nlcol_off, np1);
+    CU(cudaMemcpyAsync(H->d_part_row_off, H->part_row_off.data(), 8 * np1, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(H->d_part_nnz_off, H->part_nnz_off.data(), 8 * np1, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(H->d_part_nl_off, H->part_nl_off.data(), 8 * np1, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(H->d_part_nlcol_off, nlcol.data(), 8 * np1, cudaMemcpyHostToDevice, st));
   }
   CU(cudaStreamSynchronize(st));
   H->grid = grid_for(H, n);

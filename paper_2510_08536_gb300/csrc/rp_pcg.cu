@@ -37,6 +37,7 @@ struct IterArgs {
   double* partials;
   cudaGraphConditionalHandle inner;
   int in_graph;  // 0: launched on a stream (kernel timing), no condition to set
+  Parts<T> parts;
 };
 
 struct ResArgs {
@@ -58,6 +59,7 @@ struct ResArgs {
   cudaGraphConditionalHandle outer;
   int in_graph;
   int ru;  // mixed: continued (not restarted) inner PCG across refinements
+  Parts<double> parts;
 };
 
 template <typename T>
@@ -67,6 +69,43 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ row_ptr, const 
   T sum = T(0);
   for (int j = s; j < e; ++j) sum = fma(__ldg(vals + j), __ldg(x + __ldg(col + j)), sum);
   return sum;
+}
+
+// Row i of the matrix split into parts (Sec. 3): the part's local CSR (part-
+// local columns) plus its non-local CSR, whose compressed columns name the
+// halo rows -- on one GPU the halo exchange is this gather from x.
+template <typename T>
+__device__ __forceinline__ T row_dot_parts(const Parts<T>& P, const int32_t* __restrict__ row_ptr,
+                                           const int32_t* __restrict__ col, const T* __restrict__ vals,
+                                           const T* __restrict__ x, int64_t i) {
+  const int p = find_rank(P.row_off, P.n, i);
+  const int64_t r0 = __ldg(P.row_off + p), li = i - r0;
+  const int32_t* rp = row_ptr + r0 + p;
+  const int64_t no = __ldg(P.nnz_off + p);
+  T sum = T(0);
+  for (int j = __ldg(rp + li); j < __ldg(rp + li + 1); ++j)
+    sum = fma(__ldg(vals + no + j), __ldg(x + r0 + __ldg(col + no + j)), sum);
+  const int32_t* nrp = P.nl_row_ptr + r0 + p;
+  const int64_t nlo = __ldg(P.nl_off + p), nco = __ldg(P.nlcol_off + p);
+  for (int j = __ldg(nrp + li); j < __ldg(nrp + li + 1); ++j)
+    sum = fma(__ldg(P.nl_vals + nlo + j), __ldg(x + __ldg(P.nl_cols + nco + __ldg(P.nl_col + nlo + j))), sum);
+  return sum;
+}
+
+inline Parts<double> parts64(const rp_handle* h) {
+  return Parts<double>{h->n_parts, h->d_part_row_off, h->d_part_nnz_off, h->d_part_nl_off, h->d_part_nlcol_off,
+                       h->nl_row_ptr, h->nl_col_idx, h->nl_cols, h->nl_vals};
+}
+inline Parts<float> parts32(const rp_handle* h) {
+  return Parts<float>{h->n_parts, h->d_part_row_off, h->d_part_nnz_off, h->d_part_nl_off, h->d_part_nlcol_off,
+                      h->nl_row_ptr, h->nl_col_idx, h->nl_cols, h->nl_vals32};
+}
+
+template <typename T>
+__device__ __forceinline__ T row_dot_any(const Parts<T>& P, const int32_t* __restrict__ row_ptr,
+                                         const int32_t* __restrict__ col, const T* __restrict__ vals,
+                                         const T* __restrict__ x, int64_t i) {
+  return P.n > 1 ? row_dot_parts<T>(P, row_ptr, col, vals, x, i) : row_dot<T>(row_ptr, col, vals, x, i);
 }
 
 // 16-byte vectors of the streaming kernels
@@ -111,7 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_it_spmv(IterArgs<T> a) {
   if (c->stop) return;
   T acc = T(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    T s = row_dot<T>(a.row_ptr, a.col, a.vals, a.p, i);
+    T s = row_dot_any<T>(a.parts, a.row_ptr, a.col, a.vals, a.p, i);
     a.q[i] = s;
     acc = fma(a.p[i], s, acc);
   }
@@ -240,7 +279,7 @@ __global__ void __launch_bounds__(kThreads) k_res64(ResArgs a) {
       ri = bi;
       x[i] = 0.0;
     } else {
-      ri = bi - row_dot<double>(a.row_ptr, a.col, a.vals, x, i);
+      ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
     }
     a.r[i] = ri;
     const double zi = a.dinv[i] * ri;
@@ -295,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
       ri = bi;
       x[i] = 0.0;
     } else {
-      ri = bi - row_dot<double>(a.row_ptr, a.col, a.vals, x, i);
+      ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
     }
     const float r32 = (float)ri;
     a.r32[i] = r32;
@@ -411,10 +450,10 @@ __global__ void k_setup(Ctl* c, SolveIO* io, const double* b, double* x, double 
 __global__ void __launch_bounds__(kThreads)
     k_spmv_plain(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                  const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y,
-                 double* xy, double* partials, unsigned int* ticket) {
+                 double* xy, double* partials, unsigned int* ticket, Parts<double> parts) {
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = row_dot<double>(row_ptr, col, vals, x, i);
+    double s = row_dot_any<double>(parts, row_ptr, col, vals, x, i);
     y[i] = s;
     acc += x[i] * s;
   }
@@ -493,6 +532,7 @@ rp_status build_solve_graph(rp_handle* h, int mode, const double* vals, const do
   ra.outer = hout;
   ra.in_graph = 1;
   ra.ru = mode == 2;
+  ra.parts = parts64(h);
   RP_TRY(add_kernel(obody, &nres, nullptr, mixed ? (void*)k_res_mixed : (void*)k_res64, h->grid, &ra));
   cudaGraphNode_t before_inner = nres, nru;
   if (mode == 2) {
@@ -503,7 +543,7 @@ rp_status build_solve_graph(rp_handle* h, int mode, const double* vals, const do
   RP_TRY(add_while(obody, &win, &before_inner, hin, &ibody));
   if (mixed) {
     IterArgs<float> ia{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
-                       h->ctl, h->io, h->partials, hin, 1};
+                       h->ctl, h->io, h->partials, hin, 1, parts32(h)};
     RP_TRY(add_kernel(ibody, &n1, nullptr, (void*)k_it_spmv<float>, h->grid, &ia));
     RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<float>, h->grid, &ia));
     RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<float>, h->grid, &ia));
@@ -511,7 +551,7 @@ rp_status build_solve_graph(rp_handle* h, int mode, const double* vals, const do
     RP_TRY(add_kernel(obody, &ncor, &win, (void*)k_correct, h->grid, &ca));
   } else {
     IterArgs<double> ia{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
-                        h->ctl, h->io, h->partials, hin, 1};
+                        h->ctl, h->io, h->partials, hin, 1, parts64(h)};
     RP_TRY(add_kernel(ibody, &n1, nullptr, (void*)k_it_spmv<double>, h->grid, &ia));
     RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<double>, h->grid, &ia));
     RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<double>, h->grid, &ia));
@@ -619,10 +659,11 @@ rp_status host_loop_solve(rp_handle* h, int mode, const double* vals, const doub
   ra.io = h->io;
   ra.partials = h->partials;
   ra.in_graph = 0;
+  ra.parts = parts64(h);
   IterArgs<double> a64{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
-                       h->ctl, h->io, h->partials, 0, 0};
+                       h->ctl, h->io, h->partials, 0, 0, parts64(h)};
   IterArgs<float> a32{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
-                      h->ctl, h->io, h->partials, 0, 0};
+                      h->ctl, h->io, h->partials, 0, 0, parts32(h)};
   CorrectArgs ca{h->n, h->d32, h->ctl, h->io};
   Ctl c;
   auto read = [&]() -> rp_status {
@@ -696,7 +737,6 @@ extern "C" rp_status rp_solve(rp_handle* h, const double* b, double* x, double t
   if (!h || (!b && h->n) || (!x && h->n)) return fail(RP_EINVAL, "null argument");
   if (!(tol >= 0.0)) return fail(RP_EINVAL, "tol must be >= 0");
   if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
-  if (h->n_parts != 1) return fail(RP_EUNSUPPORTED, "solve needs n_parts == 1 (one merged matrix per GPU)");
   if (precision != RP_FP64 && precision != RP_MIXED && precision != RP_MIXED_RU)
     return fail(RP_EINVAL, "precision must be RP_FP64, RP_MIXED or RP_MIXED_RU");
   if (precision != RP_FP64 && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
@@ -740,10 +780,10 @@ extern "C" rp_status rp_set_solver_options(rp_handle* h, const rp_options* o) {
 
 extern "C" rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* xy, void* stream) {
   if (!h || (!x && h->n) || (!y && h->n)) return fail(RP_EINVAL, "null argument");
-  if (h->n_parts != 1) return fail(RP_EUNSUPPORTED, "rp_spmv needs n_parts == 1");
   if (h->n == 0) return RP_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  k_spmv_plain<<<h->grid, kThreads, 0, s>>>(h->n, h->row_ptr, h->col_idx, h->vals, x, y, xy, h->partials, h->ticket);
+  k_spmv_plain<<<h->grid, kThreads, 0, s>>>(h->n, h->row_ptr, h->col_idx, h->vals, x, y, xy, h->partials, h->ticket,
+                                            parts64(h));
   RP_TRY_CUDA(cudaGetLastError());
   return RP_OK;
 }
@@ -751,7 +791,6 @@ extern "C" rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* x
 extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t precision, int32_t iters,
                                           float* ms_out, void* stream) {
   if (!h || !b || !ms_out || iters < 1) return fail(RP_EINVAL, "invalid argument");
-  if (h->n_parts != 1) return fail(RP_EUNSUPPORTED, "needs n_parts == 1");
   if (precision != RP_FP64 && precision != RP_MIXED && precision != RP_MIXED_RU)
     return fail(RP_EINVAL, "precision must be RP_FP64, RP_MIXED or RP_MIXED_RU");
   if (precision != RP_FP64 && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
@@ -777,6 +816,7 @@ extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t
   ra.io = h->io;
   ra.partials = h->partials;
   ra.in_graph = 0;
+  ra.parts = parts64(h);
   if (mixed) k_res_mixed<<<h->grid, kThreads, 0, s>>>(ra);
   else k_res64<<<h->grid, kThreads, 0, s>>>(ra);
   RP_TRY_CUDA(cudaGetLastError());
@@ -790,9 +830,9 @@ extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t
   } evfree{ev};
   for (auto& e : ev) RP_TRY_CUDA(cudaEventCreate(&e));
   IterArgs<double> a64{h->n, h->row_ptr, h->col_idx, h->vals, h->dinv, h->r, h->p, h->q, nullptr,
-                       h->ctl, h->io, h->partials, 0, 0};
+                       h->ctl, h->io, h->partials, 0, 0, parts64(h)};
   IterArgs<float> a32{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
-                      h->ctl, h->io, h->partials, 0, 0};
+                      h->ctl, h->io, h->partials, 0, 0, parts32(h)};
   RP_TRY_CUDA(cudaEventRecord(ev[0], s));
   for (int it = 0; it < iters; ++it) {
     if (mixed) k_it_spmv<float><<<h->grid, kThreads, 0, s>>>(a32);

@@ -67,9 +67,14 @@ static rp_status permute_all(rp_handle* h, const double* buf, cudaStream_t s) {
         k_permute<false><<<g, kThreads, 0, s>>>(base, h->src_of + o, h->vals + o, nullptr, cnt);
     }
     int64_t no = h->part_nl_off[p], ncnt = h->part_nl_off[p + 1] - no;
-    if (ncnt > 0)
-      k_permute<false><<<grid_for(h, (ncnt + 3) / 4), kThreads, 0, s>>>(base, h->nl_src_of + no, h->nl_vals + no,
-                                                                        nullptr, ncnt);
+    if (ncnt > 0) {
+      if (h->want_fp32)
+        k_permute<true><<<grid_for(h, (ncnt + 3) / 4), kThreads, 0, s>>>(base, h->nl_src_of + no, h->nl_vals + no,
+                                                                         h->nl_vals32 + no, ncnt);
+      else
+        k_permute<false><<<grid_for(h, (ncnt + 3) / 4), kThreads, 0, s>>>(base, h->nl_src_of + no,
+                                                                          h->nl_vals + no, nullptr, ncnt);
+    }
   }
   if (h->n > 0) {
     if (h->want_fp32)

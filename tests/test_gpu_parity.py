@@ -73,6 +73,39 @@ def test_map_multi_part_bit_exact(n_parts):
     h.close()
 
 
+@pytest.mark.parametrize("n_parts", [2, 4, 8])
+def test_multi_part_spmv_and_solve(n_parts):
+    """Solving over the parts' local + non-local matrices (halo gathered on the
+    device) gives the merged system's product and solution."""
+    c = Case((24, 20, 16), (2, 2, 2), sigma=1.0)
+    h1 = repart.build_repartition(c.mesh.ranks)
+    hp = repart.build_repartition(c.mesh.ranks, n_parts=n_parts)
+    assert hp.n_parts == n_parts
+    stg = _t(c.staging)
+    repart.update_values_packed(h1, stg)
+    repart.update_values_packed(hp, stg)
+    n = c.mesh.n_cells
+    x = np.random.default_rng(4).standard_normal(n)
+    y = torch.empty(n, dtype=torch.float64, device=DEV)
+    repart.spmv(hp, _t(x), y)
+    ref = O.spmv(c.map.row_ptr, c.map.col_idx, c.vals, x)
+    scale = O.spmv(c.map.row_ptr, c.map.col_idx, np.abs(c.vals), np.abs(x))
+    assert (np.abs(y.cpu().numpy() - ref) <= 1e-13 * scale).all()
+    for precision in ("fp64", "mixed", "mixed_ru"):
+        x1 = torch.zeros(n, dtype=torch.float64, device=DEV)
+        xp = torch.zeros_like(x1)
+        i1 = repart.solve(h1, _t(c.b), x1, tol=1e-9, precision=precision)
+        ip = repart.solve(hp, _t(c.b), xp, tol=1e-9, precision=precision)
+        assert ip["status"] == 0, ip
+        xs = xp.cpu().numpy()
+        assert c.true_rel_residual(xs) <= 1e-9
+        assert np.linalg.norm(xs - x1.cpu().numpy()) / np.linalg.norm(xs) <= 1e-6
+        if precision == "fp64":
+            assert abs(ip["iterations"] - i1["iterations"]) <= 2
+    h1.close()
+    hp.close()
+
+
 def test_duplicate_face_rejected_on_device():
     mesh = synth.box_mesh(4, 3, 3, 2, 1, 1)
     r = mesh.ranks[1]
