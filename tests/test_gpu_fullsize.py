@@ -1,0 +1,176 @@
+"""Parity at the workloads' full sizes, in the bench's launch configuration.
+
+* 128^3, k = 64 CPU ranks (the repartition + update workload): the whole map
+  and the values of three coefficient draws bit-exact against the oracle;
+  FP64 solves against the oracle's solve (same tolerance, same recurrence).
+* 256^3, k = 128 (the headline workload): the whole map bit-exact; FP64
+  iteration counts against the oracle's own counts (tests/golden); the true
+  residual of every precision computed with the oracle's matrix.
+* 128^3 adjoint: dL/db and the face gradient against central finite
+  differences (h = 1e-6) on 50 cells and 50 faces, relative error
+  |g_fd - g| / max(|g|, 1e-3 max|g|) <= 1e-5.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import repart_oracle as O
+from paper_2510_08536_gb300 import build, repart, synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+DEV = "cuda:0"
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    repart.load()
+    torch.cuda.set_device(0)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _map_equal(h, m):
+    got = repart.get_part_map(h, 0)
+    for key in ("row_ptr", "col_idx", "src_of", "diag_pos"):
+        np.testing.assert_array_equal(got[key].cpu().numpy(), getattr(m, key), err_msg=key)
+
+
+def test_update_workload_128():
+    mesh = synth.workload_mesh("update_128")
+    asm = synth.Assembler(mesh)
+    (m,) = O.repartition_map(mesh.ranks, 1)
+    h = repart.build_repartition(mesh.ranks)
+    _map_equal(h, m)
+    b = synth.uniform_vector(mesh, 0)
+    bd = _t(b)
+    for t in range(3):
+        stg = asm.staging(synth.face_coeffs(mesh, 0.5, 100 + t))
+        repart.update_values_packed(h, _t(stg))
+        vals = O.update_values(m.src_of, stg)
+        np.testing.assert_array_equal(repart.get_values(h)["vals"].cpu().numpy(), vals)
+        A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
+        x = torch.zeros(mesh.n_cells, dtype=torch.float64, device=DEV)
+        info = repart.solve(h, bd, x, tol=1e-9)
+        xs = x.cpu().numpy()
+        assert info["status"] == 0
+        assert np.linalg.norm(b - A @ xs) / np.linalg.norm(b) <= 1e-9
+        if t == 0:
+            ref = O.pcg(A, O.jacobi_inverse(m.row_ptr, m.col_idx, vals, m.diag_pos), b, tol=1e-9)
+            assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-7
+            assert abs(info["iterations"] - ref.iterations) <= 2
+    h.close()
+
+
+def test_headline_workload_256():
+    mesh = synth.workload_mesh("mixed_256")
+    asm = synth.Assembler(mesh)
+    h = repart.build_repartition(mesh.ranks)
+    (m,) = O.repartition_map(mesh.ranks, 1)
+    _map_equal(h, m)
+    counts = json.load(open(os.path.join(GOLDEN, "iteration_counts.json")))["mixed_256"]
+    b = synth.uniform_vector(mesh, 0)
+    bd = _t(b)
+    seed = 100
+    stg = asm.staging(synth.face_coeffs(mesh, 1.0, seed))
+    repart.update_values_packed(h, _t(stg))
+    vals = O.update_values(m.src_of, stg)
+    del stg
+    A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
+    bn = np.linalg.norm(b)
+    for precision in ("fp64", "mixed", "mixed_ru"):
+        x = torch.zeros(mesh.n_cells, dtype=torch.float64, device=DEV)
+        info = repart.solve(h, bd, x, tol=1e-9, precision=precision)
+        assert info["status"] == 0, (precision, info)
+        assert np.linalg.norm(b - A @ x.cpu().numpy()) / bn <= 1e-9, precision
+        if precision == "fp64":
+            assert abs(info["iterations"] - counts[str(seed)]["iterations"]) <= 2
+    h.close()
+
+
+def test_adjoint_workload_128_finite_differences():
+    mesh = synth.workload_mesh("adjoint_128")
+    asm = synth.Assembler(mesh)
+    a = synth.face_coeffs(mesh, 0.5, 100)
+    stg = _t(asm.staging(a))
+    b = _t(synth.uniform_vector(mesh, 0))
+    xt = _t(synth.uniform_vector(mesh, 1))
+    h = repart.build_repartition(mesh.ranks, want_transpose=True)
+    n = mesh.n_cells
+
+    # The face gradient -(lam_l - lam_u)(x_l - x_u) differences neighbouring values, so
+    # x and lambda are solved close to the FP64 floor.
+    def solve(buf, rhs, tol):
+        repart.update_values_packed(h, buf)
+        x = torch.zeros(n, dtype=torch.float64, device=DEV)
+        info = repart.solve(h, rhs, x, tol=tol)
+        assert info["status"] == 0 or info["rel_residual"] < 5 * tol, info
+        return x
+
+    x = solve(stg, b, 3e-14)
+    lam = torch.zeros_like(x)
+    inf = repart.solve_adjoint(h, x - xt, lam, tol=1e-13)
+    assert inf["status"] == 0 or inf["rel_residual"] < 3e-13, inf
+    gf = torch.zeros(sum(r.n_faces + r.n_iface for r in mesh.ranks), dtype=torch.float64, device=DEV)
+    repart.face_grad(h, lam, x, gf)
+    lam_np, gf_np = lam.cpu().numpy(), gf.cpu().numpy()
+    hstep = 1e-6
+    rng = np.random.default_rng(7)
+
+    # L(q +- h) with q a coefficient or a rhs entry, from the FP64 solution x of the
+    # unperturbed system by residual correction: x_pm = x + d_pm with
+    # A_pm d_pm = rho -+ h dA x (or rho +- h e_i for b), rho = b - A x computed ONCE so
+    # its rounding noise is common to both signs and cancels in d_+ - d_- (computing
+    # b_pm - A_pm x separately leaves O(eps |A||x|) noise that does not cancel and
+    # grows like 1/h); each correction solved to 1e-12 of its own right-hand side;
+    # then L_+ - L_- = sum (d_+ - d_-)((x - x_t) + (d_+ + d_-)/2) exactly.
+    y = torch.empty_like(x)
+    repart.update_values_packed(h, stg)
+    repart.spmv(h, x, y)
+    rho = b - y
+
+    def fd(bufs, rhss):
+        ds = [solve(buf, rhs, 1e-12) for buf, rhs in zip(bufs, rhss)]
+        diff = float(torch.dot(ds[0] - ds[1], (x - xt) + 0.5 * (ds[0] + ds[1])))
+        return diff / (2 * hstep)
+
+    def rel(f, g, scale):
+        return abs(f - g) / max(abs(g), 1e-3 * scale)
+
+    # dL/db on 50 cells
+    for i in rng.choice(n, 50, replace=False):
+        e = torch.zeros_like(b)
+        e[i] = hstep
+        f = fd((stg, stg), (rho + e, rho - e))
+        assert rel(f, lam_np[i], np.abs(lam_np).max()) <= 1e-5, (i, f, lam_np[i])
+    # dL/da_f on 50 rank-internal faces: a_f sits in the two diagonal slots and the
+    # upper and lower slots of its rank
+    soff = O.slot_offsets(mesh.ranks, False)
+    off = O.rank_offsets(mesh.ranks)
+    foff = np.cumsum([0] + [r.n_faces + r.n_iface for r in mesh.ranks])
+    for _ in range(50):
+        r = int(rng.integers(mesh.k))
+        R = mesh.ranks[r]
+        f = int(rng.integers(R.n_faces))
+        nr, F = R.n_cells, R.n_faces
+        slots = [soff[r] + R.lower_addr[f], soff[r] + R.upper_addr[f], soff[r] + nr + f, soff[r] + nr + F + f]
+        sign = torch.tensor([1.0, 1.0, -1.0, -1.0], dtype=torch.float64, device=DEV)
+        idx = torch.tensor(slots, device=DEV)
+        up, dn = stg.clone(), stg.clone()
+        up[idx] += hstep * sign
+        dn[idx] -= hstep * sign
+        # dA x for this face: +(x_l - x_u) at l, -(x_l - x_u) at u
+        gl, gu = int(off[r] + R.lower_addr[f]), int(off[r] + R.upper_addr[f])
+        dax = torch.zeros_like(x)
+        dax[gl] = x[gl] - x[gu]
+        dax[gu] = x[gu] - x[gl]
+        fdv = fd((up, dn), (rho - hstep * dax, rho + hstep * dax))
+        g = gf_np[foff[r] + f]
+        assert rel(fdv, g, np.abs(gf_np).max()) <= 1e-5, (r, f, fdv, g)
+    h.close()
