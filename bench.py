@@ -385,6 +385,7 @@ def run_ours(args):
     h = repart.build_repartition(mesh.ranks, host_loop=int(args.host_loop))
     build_ms = 1e3 * (time.perf_counter() - tb)
     nnz, n_slots = h.nnz, h.n_slots
+    sliced = repart.sliced_sizes(h)  # (slices, padded entries, table + index words) or None
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -400,7 +401,7 @@ def run_ours(args):
     def launches(prec, info):
         per_pass = {"fp64": 1, "mixed": 2, "mixed_ru": 3}[prec]  # residual (+ correction, + p continuation)
         solve = 1 + 3 * info["iterations"] + per_pass * info["passes"]
-        return 2 + solve  # permutation + Jacobi diagonal
+        return 2 + (1 if sliced else 0) + solve  # permutation + Jacobi diagonal (+ sliced values)
 
     results = {}
     clocks = {}
@@ -455,13 +456,20 @@ def run_ours(args):
     upd_ms = ev[0].elapsed_time(ev[1]) / reps
 
     def spmv_bytes(prec):
-        return (12 * nnz + 4 * (n + 1) + 16 * n) if prec == "fp64" else (8 * nnz + 4 * (n + 1) + 8 * n)
+        w = 8 if prec == "fp64" else 4
+        if sliced:  # values + offset tables and index words + slice descriptors + p read + q write
+            slices, entries, ibuf_len = sliced
+            return w * entries + 4 * ibuf_len + 8 * (slices + 1) + 2 * w * n
+        return (w + 4) * nnz + 4 * (n + 1) + 2 * w * n
 
     def gbs(bytes_, ms):
         return bytes_ / (ms * 1e-3) / 1e9
 
     upd_bytes = 20 * nnz + 4 * nnz + 20 * n  # idx + gather + FP64 write + FP32 write; diag read + 2 writes
-    roof = {"bound": "hbm", "kernel": f"k_it_spmv<{'double' if head == 'fp64' else 'float'}>",
+    if sliced:  # sliced values: position + CSR value read, FP64 + FP32 write per padded entry
+        upd_bytes += 24 * sliced[1]
+    k1_name = "k_it_spmv_sl" if sliced else "k_it_spmv"
+    roof = {"bound": "hbm", "kernel": f"{k1_name}<{'double' if head == 'fp64' else 'float'}>",
             "achieved": round(gbs(spmv_bytes(head), kern[head]["spmv"]), 1), "peak": hbm_peak, "unit": "GB/s",
             "peak_kind": peak_kind}
     roof["frac"] = round(roof["achieved"] / hbm_peak, 4)
@@ -557,6 +565,8 @@ def run_ours(args):
         "dtype": "f64" if head == "fp64" else "f32-in-f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "headline": head,
                    "n_rows": n, "nnz": nnz, "draws_cycled": draws, "l2": "inputs larger than L2, no flush",
+                   "layout": ({"kind": "sliced", "slices": sliced[0], "padded_entries": sliced[1],
+                               "table_and_index_words": sliced[2]} if sliced else {"kind": "csr"}),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "fp64_ms_per_step": round(results["fp64"]["ms_per_step"], 3) if "fp64" in results else None,
         "mixed_ms_per_step": round(results["mixed"]["ms_per_step"], 3) if "mixed" in results else None,

@@ -66,6 +66,12 @@ enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1, RP_MEM_HOST_DIRECT = 2 };
  * iterate is added to x in FP64, the FP64 residual replaces the FP32 one and
  * the search direction continues (p = z + beta p). */
 enum { RP_FP64 = 0, RP_MIXED = 1, RP_MIXED_RU = 2 };
+/* Matrix layout of the PCG iteration (rp_options.layout). RP_LAYOUT_AUTO:
+ * the sliced layout (see rp_get_sliced_view) when the matrix is one part,
+ * no row has more than 32 entries and no 32-row slice more than 256
+ * distinct column offsets; else CSR. RP_LAYOUT_CSR: always CSR. Both give
+ * the same products row by row (same entries, same order). */
+enum { RP_LAYOUT_AUTO = 0, RP_LAYOUT_CSR = 1 };
 
 typedef struct rp_handle rp_handle;
 
@@ -103,7 +109,7 @@ typedef struct rp_options {
                              reading the control block after every iteration
                              (slow; for profilers that cannot look inside
                              graphs with conditional nodes)                       */
-  int32_t reserved;
+  int32_t layout;         /* RP_LAYOUT_AUTO or RP_LAYOUT_CSR                      */
   double ru_delta;        /* RP_MIXED_RU: residual reduction between two FP64
                              refinements (default 0.1; 0: use inner_tol)          */
 } rp_options;
@@ -115,7 +121,8 @@ rp_status rp_set_solver_options(rp_handle* h, const rp_options* opts);
 
 /* Defaults: n_parts 1, general (non-symmetric) storage, FP32 copy on,
  * transpose off, max_iter 20000, max_outer 30, max_restarts 8, current
- * device, inner_tol 1e-5, spin_limit 1<<26, host_loop 0, ru_delta 0.1. */
+ * device, inner_tol 1e-5, spin_limit 1<<26, host_loop 0, layout
+ * RP_LAYOUT_AUTO, ru_delta 0.1. */
 void rp_default_options(rp_options* opts);
 
 /* Sec. 3 steps 1-3 and the three outputs (sparsity pattern, update pattern,
@@ -196,6 +203,41 @@ rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* xy, void* st
  * the same per row as rp_spmv's; x.y agrees to rounding. Asynchronous. */
 rp_status rp_spmv_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
                           const double* x, double* y, double* xy, void* stream);
+
+/* The sliced layout the PCG iteration multiplies with (the paper has no
+ * counterpart: it is this library's device format of the merged matrix, built
+ * once next to the CSR map by rp_build_repartition and refilled from the CSR
+ * values by every value update). Rows in slices of 32 (n_slices = ceil(n/32),
+ * 0 when the layout is not in use), one row per lane. Slice s: desc[2s] = x_s,
+ * desc[2s+1] = y_s (uint32 pairs, desc[2 n_slices], desc[2 n_slices + 1]
+ * close the last slice); L_s = (x_{s+1} - x_s) / 32 entries per row, the
+ * longest row of the slice, shorter rows padded with zero values; values of
+ * entry k of lane j at vals[x_s + 32 k + j] (vals32 alike, NULL without
+ * want_fp32); ibuf[y_s ...] holds D_s int32 column offsets (col - row, padded
+ * with zeros to a multiple of 8), then ceil(L_s / 4) uint32 words per lane
+ * (word g of lane j at 32 g + j) whose byte e is the offset index of entry
+ * 4 g + e. pos[x_s + 32 k + j] is the CSR position of that entry, -1 for
+ * padding. Entry k of a row is its k-th CSR entry. Device views, owned by
+ * the handle; n_entries counts padded entries, ibuf_len int32 words. */
+typedef struct rp_sliced_view {
+  int64_t n_slices, n_entries, ibuf_len;
+  const uint32_t* desc;
+  const int32_t* ibuf;
+  const int32_t* pos;
+  const double* vals;
+  const float* vals32;
+} rp_sliced_view;
+rp_status rp_get_sliced_view(const rp_handle* h, rp_sliced_view* out);
+
+/* The SpMV of the PCG iteration, y = A x, in its working precision and
+ * layout (Sec. 4: the pressure solve's matrix product): precision RP_FP64
+ * reads double x, writes double y from the FP64 values; RP_MIXED or
+ * RP_MIXED_RU reads float x, writes float y from the FP32 values, summing
+ * each row in FP32. Same kernel the solve launches (sliced or CSR, n_parts
+ * parts); a row's products are accumulated with fused multiply-adds in the
+ * row's CSR order. x, y device pointers of n elements. Uses the handle's
+ * reduction scratch and a control block of its own. Asynchronous. */
+rp_status rp_iter_spmv(rp_handle* h, const void* x, void* y, int32_t precision, void* stream);
 
 typedef struct rp_solve_info {
   int32_t status;           /* RP_OK, RP_NOT_CONVERGED or RP_BREAKDOWN       */

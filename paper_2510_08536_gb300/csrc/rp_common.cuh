@@ -102,6 +102,36 @@ struct Parts {
   const T* nl_vals;
 };
 
+// Sliced layout of the merged matrix (one part): rows in slices of 32, one
+// row per lane. Slice s keeps its values column-major at vals[x_s + 32 k +
+// lane] (k < L_s, the longest row of the slice; shorter rows are padded with
+// zeros) and, at ibuf[y_s ...], a table of D_s distinct column offsets
+// col - row (padded to a multiple of 8) followed by ceil(L_s / 4) words per
+// lane of 8-bit table indices (word g of lane j at 32 g + j, entry 4 g + e in
+// byte e). desc[s] = (x_s, y_s), desc[n_slices] closes the last slice, so
+// L_s = (x_{s+1} - x_s) / 32 and D_s = y_{s+1} - y_s - 32 ceil(L_s / 4).
+// Entries keep the CSR order of their row, so a row's products are summed
+// exactly as over the CSR arrays.
+constexpr int kSliceRows = 32;
+constexpr int kSliceMaxDict = 256;   // 8-bit indices
+constexpr int kSliceMaxWidth = 32;   // longest row the layout takes
+
+template <typename T>
+struct Sliced {
+  int64_t n_slices;  // 0: not built (CSR only)
+  const uint2* desc; // n_slices + 1 entries, then kSliceDescPad zero entries
+  const int32_t* ibuf;
+  const T* vals;
+  int64_t spin;      // iteration limit of every shared-memory barrier wait
+};
+constexpr int kSliceDescPad = 8;  // bulk copies of descriptor runs may read past the end
+
+// Grids of the three PCG iteration kernels of one precision: blocks that
+// fit on the SMs at once (by each kernel's register use), capped by the rows.
+struct IterGrid {
+  int k1 = 1, k1s = 1, k2 = 1, k3 = 1;  // K1 on CSR, K1 on the sliced layout, K2, K3
+};
+
 // Per-call pointers of the batched solve (read by the captured kernel).
 struct BatchIO {
   const double* buf;
@@ -190,6 +220,16 @@ struct rp_handle {
   float* dinv32 = nullptr;    // n
   double* dinvT = nullptr;
 
+  // sliced layout (n_parts == 1, built when every slice fits; see Sliced)
+  int64_t sl_slices = 0;     // 0: the iteration runs on the CSR arrays
+  int64_t sl_entries = 0;    // padded entries (32 per slice and width unit)
+  int64_t sl_ibuf_len = 0;   // int32 words of tables and index words
+  uint2* sl_desc = nullptr;  // [sl_slices + 1]
+  int32_t* sl_ibuf = nullptr;
+  int32_t* sl_pos = nullptr;  // CSR position of each padded entry, -1 = padding
+  double* sl_vals = nullptr;
+  float* sl_vals32 = nullptr;
+
   // solver work space
   double *r = nullptr, *p = nullptr, *q = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
@@ -197,9 +237,11 @@ struct rp_handle {
   double* x_host_stage = nullptr;
   double* partials = nullptr;      // grid * kMaxPartials
   rp::Ctl* ctl = nullptr;          // device
+  rp::Ctl* ctl_spmv = nullptr;     // device, rp_iter_spmv's own
   rp::SolveIO* io = nullptr;       // device
   unsigned int* ticket = nullptr;  // spare ticket for rp_spmv
   int grid = 0;                    // blocks of every streaming kernel
+  rp::IterGrid igrid64, igrid32;   // blocks of the PCG iteration kernels
   rp::Graphs graphs;
   cudaStream_t capture_stream = nullptr;
 
@@ -226,6 +268,9 @@ inline int grid_for(const rp_handle* h, int64_t n) {
 }
 
 rp_status ensure_solver_buffers(rp_handle* h);
+rp_status build_sliced(rp_handle* h, cudaStream_t s);  // after the CSR map
+rp_status fill_sliced(rp_handle* h, cudaStream_t s);   // after every value update
+void free_sliced(rp_handle* h);
 rp_status build_graphs(rp_handle* h);
 void free_solver(rp_handle* h);
 void free_batch(rp_handle* h);

@@ -366,6 +366,8 @@ rp_status validate(const rp_ldu_desc* ranks, int32_t k, const rp_options& o) {
   if (o.max_iter < 0 || o.max_outer < 0 || o.max_restarts < 0 || !(o.inner_tol > 0.0) ||
       o.spin_limit < 1 || !(o.ru_delta >= 0.0 && o.ru_delta < 1.0))
     return fail(RP_EINVAL, "invalid solver options");
+  if (o.layout != RP_LAYOUT_AUTO && o.layout != RP_LAYOUT_CSR)
+    return fail(RP_EINVAL, "layout must be RP_LAYOUT_AUTO or RP_LAYOUT_CSR");
   int64_t n = 0, nnz = 0, slots = 0;
   for (int r = 0; r < k; ++r) {
     const rp_ldu_desc& d = ranks[r];
@@ -433,6 +435,7 @@ extern "C" void rp_default_options(rp_options* o) {
   o->device = -1;
   o->inner_tol = 1e-5;
   o->spin_limit = 1LL << 26;
+  o->layout = RP_LAYOUT_AUTO;
   o->ru_delta = 0.1;
 }
 
@@ -465,6 +468,7 @@ static void free_handle_memory(rp_handle* h) {
     if (p) cudaFree(p);
   free_solver(h);
   free_batch(h);
+  free_sliced(h);
 }
 
 extern "C" void rp_destroy(rp_handle* h) {
@@ -771,7 +775,9 @@ extern "C" rp_status rp_build_repartition(const rp_ldu_desc* ranks, int32_t k, c
   CU(cudaStreamSynchronize(st));
   H->grid = grid_for(H, n);
   {
-    rp_status s = ensure_solver_buffers(H);
+    rp_status s = build_sliced(H, st);
+    if (s != RP_OK) return fail_free(s);
+    s = ensure_solver_buffers(H);
     if (s != RP_OK) return fail_free(s);
   }
 #undef ALLOC

@@ -15,6 +15,7 @@
 // the recursive residual passes or the iteration cap is hit, the outer one
 // by the residual pass when the true residual passes (or a cap is hit).
 // Every loop is bounded by device-side counters.
+#include <algorithm>
 #include <type_traits>
 
 #include "rp_common.cuh"
@@ -38,6 +39,7 @@ struct IterArgs {
   cudaGraphConditionalHandle inner;
   int in_graph;  // 0: launched on a stream (kernel timing), no condition to set
   Parts<T> parts;
+  Sliced<T> sl;  // K1 runs k_it_spmv_sl when built (n_slices > 0)
 };
 
 struct ResArgs {
@@ -108,6 +110,15 @@ __device__ __forceinline__ T row_dot_any(const Parts<T>& P, const int32_t* __res
   return P.n > 1 ? row_dot_parts<T>(P, row_ptr, col, vals, x, i) : row_dot<T>(row_ptr, col, vals, x, i);
 }
 
+inline Sliced<double> sliced64(const rp_handle* h, const double* vals) {
+  if (h->sl_slices == 0 || vals != h->vals) return Sliced<double>{};  // e.g. transposed values
+  return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_ibuf, h->sl_vals, h->opts.spin_limit};
+}
+inline Sliced<float> sliced32(const rp_handle* h) {
+  if (h->sl_slices == 0 || !h->sl_vals32) return Sliced<float>{};
+  return Sliced<float>{h->sl_slices, h->sl_desc, h->sl_ibuf, h->sl_vals32, h->opts.spin_limit};
+}
+
 // 16-byte vectors of the streaming kernels
 template <typename T>
 struct Vec;
@@ -145,6 +156,9 @@ __device__ __forceinline__ void for_each_comp(F&& f) {
 // FP64 work (GB300 runs FP64 and float<->double conversions ~70x slower
 // than FP32); one conversion per thread feeds the FP64 block reduction.
 template <typename T>
+__device__ __forceinline__ void spmv_finish(const IterArgs<T>& a, T acc);
+
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_it_spmv(IterArgs<T> a) {
   Ctl* c = a.ctl;
   if (c->stop) return;
@@ -154,11 +168,282 @@ __global__ void __launch_bounds__(kThreads) k_it_spmv(IterArgs<T> a) {
     a.q[i] = s;
     acc = fma(a.p[i], s, acc);
   }
+  spmv_finish<T>(a, acc);
+}
+
+// ---- K1 over the sliced layout, staged through shared memory by TMA bulk copies.
+//
+// A block is kChunk consumer warps plus one producer warp. The block owns
+// chunks of kChunk consecutive slices (consumer warp w takes slice w of the
+// chunk: rows 256 c + 32 w + lane, as k_it_spmv's thread 32 w + lane of
+// block c maps rows). The producer keeps up to kStages chunks in flight:
+// once consumers have released a stage (its "empty" mbarrier), it posts the
+// byte count on the stage's "full" mbarrier and issues three cp.async.bulk
+// copies -- the chunk's values, its offset tables + index words and its run
+// of slice descriptors. Bytes in flight cost no registers, and consumer
+// warps wait only on their own chunk's data, not on each other; a slice
+// then waits on one memory round trip, its gathers of p. Offset tables of
+// up to 32 entries are read with a warp shuffle (source lane = index byte,
+// taken modulo 32 by the shuffle), longer ones from shared memory; rows of
+// up to 8 entries run a body unrolled for their exact width. A chunk larger
+// than a stage (rows over 8 entries, long tables) is read straight from
+// global memory by the same warps. Every barrier wait is bounded: after
+// spin iterations the block records RP_DEVICE_TIMEOUT, stops the solve,
+// waits (bounded) for its own copies and leaves.
+
+constexpr int kChunk = kThreads / 32;  // slices per chunk, one per consumer warp
+constexpr int kSlThreads = kThreads + 32;
+constexpr int kStageIdx = 3072;        // table + index word bytes a stage holds
+constexpr int kStageDesc = 128;        // descriptor run (kChunk + 1 entries, padded)
+
+// Stages per block: 3 for FP32 (34 KB), 2 for FP64 (38 KB; 3 would leave
+// room for only 3 blocks an SM).
+template <typename T>
+struct SlStage {
+  static constexpr int kStages = sizeof(T) == 4 ? 3 : 2;
+  static constexpr int kVals = kChunk * kSliceRows * 8 * (int)sizeof(T);  // rows of <= 8 entries
+  static constexpr int kBytes = kVals + kStageIdx + kStageDesc;
+  static constexpr int kSmem = kStages * kBytes;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int64_t limit) {
+  for (int64_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// global -> shared bulk copy completing on bar (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Offset of the entry whose index byte is byte e of wd. SHFL: tables of up to
+// 32 entries held one per lane in tv (warp-uniform choice, all lanes call).
+template <bool SHFL>
+__device__ __forceinline__ int slice_offset(uint32_t wd, int e, int32_t tv, const int32_t* tab) {
+  if (SHFL) return __shfl_sync(0xffffffffu, tv, (int)(wd >> (8 * e)));
+  return tab[(wd >> (8 * e)) & 255u];
+}
+
+// Sum of one row of a slice, L entries: values at v[32 k] (lane applied),
+// index words at iw[32 g]; the same fused multiply-adds in the same order as
+// row_dot over the row's CSR entries. Lanes without a row (valid false) run
+// the shuffles but load nothing.
+template <typename T, bool SHFL, int L>
+__device__ __forceinline__ T slice_row_exact(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab,
+                                             const T* x, bool valid) {
+  const uint32_t w0 = iw[0], w1 = L > 4 ? iw[kSliceRows] : 0u;
+  T vv[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) vv[k] = v[k * kSliceRows];
+  T sum = T(0);
+#pragma unroll
+  for (int k = 0; k < L; ++k) {
+    const int off = slice_offset<SHFL>(k < 4 ? w0 : w1, k & 3, tv, tab);
+    if (valid) sum = fma(vv[k], __ldg(x + off), sum);
+  }
+  return sum;
+}
+
+template <typename T, bool SHFL>
+__device__ __forceinline__ T slice_row(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab, const T* x,
+                                       bool valid, int L) {
+  switch (L) {
+    case 1: return slice_row_exact<T, SHFL, 1>(v, iw, tv, tab, x, valid);
+    case 2: return slice_row_exact<T, SHFL, 2>(v, iw, tv, tab, x, valid);
+    case 3: return slice_row_exact<T, SHFL, 3>(v, iw, tv, tab, x, valid);
+    case 4: return slice_row_exact<T, SHFL, 4>(v, iw, tv, tab, x, valid);
+    case 5: return slice_row_exact<T, SHFL, 5>(v, iw, tv, tab, x, valid);
+    case 6: return slice_row_exact<T, SHFL, 6>(v, iw, tv, tab, x, valid);
+    case 7: return slice_row_exact<T, SHFL, 7>(v, iw, tv, tab, x, valid);
+    case 8: return slice_row_exact<T, SHFL, 8>(v, iw, tv, tab, x, valid);
+    default: break;
+  }
+  T sum = T(0);
+  for (int g = 0; g < ((L + 3) >> 2); ++g) {
+    const uint32_t wd = iw[g * kSliceRows];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * g + e < L) {
+        const int off = slice_offset<SHFL>(wd, e, tv, tab);
+        if (valid) sum = fma(v[(4 * g + e) * kSliceRows], __ldg(x + off), sum);
+      }
+  }
+  return sum;
+}
+
+// One slice: descriptor pair (d0, d1), values v and table tab (shared or
+// global), gathers from x relative to the lane's row.
+template <typename T>
+__device__ __forceinline__ T slice_sum(uint2 d0, uint2 d1, const T* v, const int32_t* tab, const T* x, bool valid,
+                                       int lane) {
+  const int L = (int)((d1.x - d0.x) >> 5);
+  const int D = (int)(d1.y - d0.y) - kSliceRows * ((L + 3) >> 2);
+  const uint32_t* iw = reinterpret_cast<const uint32_t*>(tab + D) + lane;
+  if (D <= 32) {
+    // a slice holds >= 32 words of table + index words: lanes past D read one of them, unused
+    const int32_t tv = tab[lane];
+    return slice_row<T, true>(v, iw, tv, tab, x, valid, L);
+  }
+  return slice_row<T, false>(v, iw, 0, tab, x, valid, L);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
+  Ctl* c = a.ctl;
+  if (c->stop) return;
+  using St = SlStage<T>;
+  constexpr int kStages = St::kStages;
+  extern __shared__ __align__(128) unsigned char sbuf[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ uint32_t chunk_x[kStages], chunk_y[kStages];
+  __shared__ int staged[kStages];
+  __shared__ int timed_out, issued;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int S = (int)a.sl.n_slices, n = (int)a.n;
+  const int NC = (S + kChunk - 1) / kChunk, G = gridDim.x;
+  const uint2* desc = a.sl.desc;
+
+  if (tid == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kChunk);
+    }
+    timed_out = 0;
+    issued = 0;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  T acc = T(0);
+  if (w == kChunk) {
+    // producer warp: one lane posts every chunk of this block
+    if (lane == 0) {
+      uint2 nd0 = make_uint2(0u, 0u), nd1 = nd0;
+      if ((int)blockIdx.x < NC) {
+        nd0 = __ldg(desc + blockIdx.x * kChunk);
+        nd1 = __ldg(desc + min((int)blockIdx.x * kChunk + kChunk, S));
+      }
+      int i = 0;
+      for (int ch = blockIdx.x; ch < NC; ch += G, ++i) {
+        const int st = i % kStages;
+        if (i >= kStages && !mbar_wait(&empty[st], (uint32_t)((i / kStages - 1) & 1), a.sl.spin)) {
+          atomicExch(&timed_out, 1);
+          break;
+        }
+        const uint2 d0 = nd0, d1 = nd1;
+        if (ch + G < NC) {  // bounds of the next chunk, loaded while this one is posted
+          nd0 = __ldg(desc + (ch + G) * kChunk);
+          nd1 = __ldg(desc + min((ch + G) * kChunk + kChunk, S));
+        }
+        unsigned char* base = sbuf + st * St::kBytes;
+        const uint32_t vb = (d1.x - d0.x) * (uint32_t)sizeof(T), ib = (d1.y - d0.y) * 4u;
+        const bool fit = vb <= (uint32_t)St::kVals && ib <= (uint32_t)kStageIdx;
+        chunk_x[st] = d0.x;
+        chunk_y[st] = d0.y;
+        staged[st] = fit;
+        // consumers' generic-proxy reads of this stage (released through
+        // empty[st]) before the async-proxy writes of the copy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (fit) {
+          const uint32_t db = 16u * (uint32_t)((kChunk + 2) / 2);  // kChunk + 1 descriptors, 16-byte multiple
+          mbar_expect_tx(&full[st], vb + ib + db);
+          bulk_g2s(base, a.sl.vals + d0.x, vb, &full[st]);
+          bulk_g2s(base + St::kVals, a.sl.ibuf + d0.y, ib, &full[st]);
+          bulk_g2s(base + St::kVals + kStageIdx, desc + (int64_t)ch * kChunk, db, &full[st]);
+        } else {
+          mbar_arrive(&full[st]);
+        }
+      }
+      issued = i;
+    }
+  } else {
+    int i = 0;
+    for (int ch = blockIdx.x; ch < NC; ch += G, ++i) {
+      const int st = i % kStages;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((i / kStages) & 1), a.sl.spin));
+      if (!ok) {
+        if (lane == 0) atomicExch(&timed_out, 1);
+        break;
+      }
+      const int s = ch * kChunk + w;
+      if (s < S) {
+        const int row = s * kSliceRows + lane;
+        const bool valid = row < n;
+        const T* x = a.p + row;
+        const unsigned char* base = sbuf + st * St::kBytes;
+        T sum;
+        if (staged[st]) {
+          const uint2* sd = reinterpret_cast<const uint2*>(base + St::kVals + kStageIdx);
+          const uint2 d0 = sd[w], d1 = sd[w + 1];
+          sum = slice_sum<T>(d0, d1, reinterpret_cast<const T*>(base) + (d0.x - chunk_x[st]) + lane,
+                             reinterpret_cast<const int32_t*>(base + St::kVals) + (d0.y - chunk_y[st]), x, valid,
+                             lane);
+        } else {
+          const uint2 d0 = __ldg(desc + s), d1 = __ldg(desc + s + 1);
+          sum = slice_sum<T>(d0, d1, a.sl.vals + d0.x + lane, a.sl.ibuf + d0.y, x, valid, lane);
+        }
+        if (valid) {
+          a.q[row] = sum;
+          acc = fma(a.p[row], sum, acc);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+  }
+  __syncthreads();
+  if (timed_out) {
+    // wait (bounded) for the copies this block may still have in flight, then stop the solve
+    if (tid == kChunk * 32) {
+      for (int j = issued - kStages; j < issued; ++j)
+        if (j >= 0) mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1), a.sl.spin);
+      c->status = RP_DEVICE_TIMEOUT;
+      c->stop = 1;
+      c->skip_x = 1;
+    }
+    __syncthreads();
+  }
+  spmv_finish<T>(a, acc);
+}
+
+// K1 tail: (p, q) over the grid; the last block forms alpha.
+template <typename T>
+__device__ __forceinline__ void spmv_finish(const IterArgs<T>& a, T acc) {
+  Ctl* c = a.ctl;
   double v[1] = {(double)acc}, tot[1];
   if (reduce_last_block<1>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
     const double pq = tot[0];
     c->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
+    if (c->status == RP_DEVICE_TIMEOUT) {
+      c->stop = 1;
+    } else if (!(pq > 0.0) || !isfinite(pq)) {
       c->status = RP_BREAKDOWN;
       c->stop = 1;
       c->skip_x = 1;
@@ -166,6 +451,28 @@ __global__ void __launch_bounds__(kThreads) k_it_spmv(IterArgs<T> a) {
       c->alpha = c->rz / pq;
     }
   }
+}
+
+template <typename T>
+void* k1_kernel(const IterArgs<T>& a) {
+  return a.sl.n_slices > 0 ? (void*)k_it_spmv_sl<T> : (void*)k_it_spmv<T>;
+}
+template <typename T>
+int k1_grid(const IterArgs<T>& a, const IterGrid& g) {
+  return a.sl.n_slices > 0 ? g.k1s : g.k1;
+}
+template <typename T>
+int k1_smem(const IterArgs<T>& a) {
+  return a.sl.n_slices > 0 ? SlStage<T>::kSmem : 0;
+}
+template <typename T>
+int k1_threads(const IterArgs<T>& a) {
+  return a.sl.n_slices > 0 ? kSlThreads : kThreads;
+}
+template <typename T>
+void launch_k1(const IterArgs<T>& a, int grid, cudaStream_t s) {
+  if (a.sl.n_slices > 0) k_it_spmv_sl<T><<<grid, kSlThreads, SlStage<T>::kSmem, s>>>(a);
+  else k_it_spmv<T><<<grid, kThreads, 0, s>>>(a);
 }
 
 // K2: r -= alpha q; z = D^-1 r; (r, z), (r, r); stop test; beta.
@@ -467,13 +774,13 @@ __global__ void __launch_bounds__(kThreads)
 namespace {
 
 rp_status add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* dep, void* fn, int grid,
-                     void* argp) {
+                     void* argp, int smem = 0, int threads = kThreads) {
   cudaGraphNodeParams np = {};
   np.type = cudaGraphNodeTypeKernel;
   np.kernel.func = fn;
   np.kernel.gridDim = dim3((unsigned)grid);
-  np.kernel.blockDim = dim3(kThreads);
-  np.kernel.sharedMemBytes = 0;
+  np.kernel.blockDim = dim3((unsigned)threads);
+  np.kernel.sharedMemBytes = (unsigned)smem;
   void* args[1] = {argp};
   np.kernel.kernelParams = args;
   RP_TRY_CUDA(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &np));
@@ -543,18 +850,20 @@ rp_status build_solve_graph(rp_handle* h, int mode, const double* vals, const do
   RP_TRY(add_while(obody, &win, &before_inner, hin, &ibody));
   if (mixed) {
     IterArgs<float> ia{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
-                       h->ctl, h->io, h->partials, hin, 1, parts32(h)};
-    RP_TRY(add_kernel(ibody, &n1, nullptr, (void*)k_it_spmv<float>, h->grid, &ia));
-    RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<float>, h->grid, &ia));
-    RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<float>, h->grid, &ia));
+                       h->ctl, h->io, h->partials, hin, 1, parts32(h), sliced32(h)};
+    const IterGrid& gr = h->igrid32;
+    RP_TRY(add_kernel(ibody, &n1, nullptr, k1_kernel(ia), k1_grid(ia, gr), &ia, k1_smem(ia), k1_threads(ia)));
+    RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<float>, gr.k2, &ia));
+    RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<float>, gr.k3, &ia));
     CorrectArgs ca{h->n, h->d32, h->ctl, h->io};
     RP_TRY(add_kernel(obody, &ncor, &win, (void*)k_correct, h->grid, &ca));
   } else {
     IterArgs<double> ia{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
-                        h->ctl, h->io, h->partials, hin, 1, parts64(h)};
-    RP_TRY(add_kernel(ibody, &n1, nullptr, (void*)k_it_spmv<double>, h->grid, &ia));
-    RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<double>, h->grid, &ia));
-    RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<double>, h->grid, &ia));
+                        h->ctl, h->io, h->partials, hin, 1, parts64(h), sliced64(h, vals)};
+    const IterGrid& gr = h->igrid64;
+    RP_TRY(add_kernel(ibody, &n1, nullptr, k1_kernel(ia), k1_grid(ia, gr), &ia, k1_smem(ia), k1_threads(ia)));
+    RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<double>, gr.k2, &ia));
+    RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<double>, gr.k3, &ia));
   }
   RP_TRY_CUDA(cudaGraphInstantiate(exec, top.g, 0));
   return RP_OK;
@@ -575,7 +884,41 @@ rp_status dalloc(T** p, int64_t count) {
 
 }  // namespace
 
+namespace {
+
+// Blocks of one kernel that fit on an SM at once (at most kBlocksPerSm).
+int resident(const void* fn, int smem = 0, int threads = kThreads) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  return nb < kBlocksPerSm ? nb : kBlocksPerSm;
+}
+
+template <typename T>
+IterGrid iter_grid(const rp_handle* h) {
+  const int64_t want = (h->n + kThreads - 1) / kThreads;
+  auto g = [&](int per_sm) {
+    int64_t cap = (int64_t)h->num_sms * per_sm;
+    return (int)(want < 1 ? 1 : want < cap ? want : cap);
+  };
+  const void* sl = (const void*)k_it_spmv_sl<T>;
+  if (cudaFuncSetAttribute(sl, cudaFuncAttributeMaxDynamicSharedMemorySize, SlStage<T>::kSmem) != cudaSuccess)
+    cudaGetLastError();  // the launch reports it
+  IterGrid gr;
+  gr.k1 = g(resident((const void*)k_it_spmv<T>));
+  gr.k1s = g(resident(sl, SlStage<T>::kSmem, kSlThreads));
+  gr.k2 = g(resident((const void*)k_it_resid<T>));
+  gr.k3 = g(resident((const void*)k_it_xp<T>));
+  return gr;
+}
+
+}  // namespace
+
 rp_status ensure_solver_buffers(rp_handle* h) {
+  h->igrid64 = iter_grid<double>(h);
+  h->igrid32 = iter_grid<float>(h);
   const int64_t n = h->n + 64;
   RP_TRY(dalloc(&h->r, n));
   RP_TRY(dalloc(&h->p, n));
@@ -597,7 +940,7 @@ rp_status ensure_solver_buffers(rp_handle* h) {
 
 void free_solver(rp_handle* h) {
   void* ptrs[] = {h->r, h->p, h->q, h->r32, h->p32, h->q32, h->d32, h->b_host_stage, h->x_host_stage,
-                  h->partials, h->ctl, h->io, h->ticket};
+                  h->partials, h->ctl, h->io, h->ticket, h->ctl_spmv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->r = h->p = h->q = nullptr;
@@ -607,6 +950,7 @@ void free_solver(rp_handle* h) {
   h->ctl = nullptr;
   h->io = nullptr;
   h->ticket = nullptr;
+  h->ctl_spmv = nullptr;
   if (h->graphs.fp64) cudaGraphExecDestroy(h->graphs.fp64);
   if (h->graphs.mixed) cudaGraphExecDestroy(h->graphs.mixed);
   if (h->graphs.mixed_ru) cudaGraphExecDestroy(h->graphs.mixed_ru);
@@ -661,9 +1005,9 @@ rp_status host_loop_solve(rp_handle* h, int mode, const double* vals, const doub
   ra.in_graph = 0;
   ra.parts = parts64(h);
   IterArgs<double> a64{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
-                       h->ctl, h->io, h->partials, 0, 0, parts64(h)};
+                       h->ctl, h->io, h->partials, 0, 0, parts64(h), sliced64(h, vals)};
   IterArgs<float> a32{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
-                      h->ctl, h->io, h->partials, 0, 0, parts32(h)};
+                      h->ctl, h->io, h->partials, 0, 0, parts32(h), sliced32(h)};
   CorrectArgs ca{h->n, h->d32, h->ctl, h->io};
   Ctl c;
   auto read = [&]() -> rp_status {
@@ -681,13 +1025,13 @@ rp_status host_loop_solve(rp_handle* h, int mode, const double* vals, const doub
     const bool go = !c.stop;
     while (!c.stop) {
       if (mixed) {
-        k_it_spmv<float><<<h->grid, kThreads, 0, s>>>(a32);
-        k_it_resid<float><<<h->grid, kThreads, 0, s>>>(a32);
-        k_it_xp<float><<<h->grid, kThreads, 0, s>>>(a32);
+        launch_k1(a32, k1_grid(a32, h->igrid32), s);
+        k_it_resid<float><<<h->igrid32.k2, kThreads, 0, s>>>(a32);
+        k_it_xp<float><<<h->igrid32.k3, kThreads, 0, s>>>(a32);
       } else {
-        k_it_spmv<double><<<h->grid, kThreads, 0, s>>>(a64);
-        k_it_resid<double><<<h->grid, kThreads, 0, s>>>(a64);
-        k_it_xp<double><<<h->grid, kThreads, 0, s>>>(a64);
+        launch_k1(a64, k1_grid(a64, h->igrid64), s);
+        k_it_resid<double><<<h->igrid64.k2, kThreads, 0, s>>>(a64);
+        k_it_xp<double><<<h->igrid64.k3, kThreads, 0, s>>>(a64);
       }
       RP_TRY_CUDA(cudaGetLastError());
       RP_TRY(read());
@@ -788,6 +1132,30 @@ extern "C" rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* x
   return RP_OK;
 }
 
+extern "C" rp_status rp_iter_spmv(rp_handle* h, const void* x, void* y, int32_t precision, void* stream) {
+  if (!h || (!x && h->n) || (!y && h->n)) return fail(RP_EINVAL, "null argument");
+  if (precision != RP_FP64 && precision != RP_MIXED && precision != RP_MIXED_RU)
+    return fail(RP_EINVAL, "precision must be RP_FP64, RP_MIXED or RP_MIXED_RU");
+  if (precision != RP_FP64 && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
+  if (h->n == 0) return RP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  RP_TRY(dalloc(&h->ctl_spmv, 1));
+  RP_TRY_CUDA(cudaMemsetAsync(h->ctl_spmv, 0, sizeof(Ctl), s));  // stop = 0, rz = 0
+  if (precision == RP_FP64) {
+    IterArgs<double> a{h->n, h->row_ptr, h->col_idx, h->vals, h->dinv, nullptr,
+                       const_cast<double*>(static_cast<const double*>(x)), static_cast<double*>(y), nullptr,
+                       h->ctl_spmv, h->io, h->partials, 0, 0, parts64(h), sliced64(h, h->vals)};
+    launch_k1(a, k1_grid(a, h->igrid64), s);
+  } else {
+    IterArgs<float> a{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, nullptr,
+                      const_cast<float*>(static_cast<const float*>(x)), static_cast<float*>(y), nullptr,
+                      h->ctl_spmv, h->io, h->partials, 0, 0, parts32(h), sliced32(h)};
+    launch_k1(a, k1_grid(a, h->igrid32), s);
+  }
+  RP_TRY_CUDA(cudaGetLastError());
+  return RP_OK;
+}
+
 extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t precision, int32_t iters,
                                           float* ms_out, void* stream) {
   if (!h || !b || !ms_out || iters < 1) return fail(RP_EINVAL, "invalid argument");
@@ -830,19 +1198,19 @@ extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t
   } evfree{ev};
   for (auto& e : ev) RP_TRY_CUDA(cudaEventCreate(&e));
   IterArgs<double> a64{h->n, h->row_ptr, h->col_idx, h->vals, h->dinv, h->r, h->p, h->q, nullptr,
-                       h->ctl, h->io, h->partials, 0, 0, parts64(h)};
+                       h->ctl, h->io, h->partials, 0, 0, parts64(h), sliced64(h, h->vals)};
   IterArgs<float> a32{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
-                      h->ctl, h->io, h->partials, 0, 0, parts32(h)};
+                      h->ctl, h->io, h->partials, 0, 0, parts32(h), sliced32(h)};
   RP_TRY_CUDA(cudaEventRecord(ev[0], s));
   for (int it = 0; it < iters; ++it) {
-    if (mixed) k_it_spmv<float><<<h->grid, kThreads, 0, s>>>(a32);
-    else k_it_spmv<double><<<h->grid, kThreads, 0, s>>>(a64);
+    if (mixed) launch_k1(a32, k1_grid(a32, h->igrid32), s);
+    else launch_k1(a64, k1_grid(a64, h->igrid64), s);
     RP_TRY_CUDA(cudaEventRecord(ev[3 * it + 1], s));
-    if (mixed) k_it_resid<float><<<h->grid, kThreads, 0, s>>>(a32);
-    else k_it_resid<double><<<h->grid, kThreads, 0, s>>>(a64);
+    if (mixed) k_it_resid<float><<<h->igrid32.k2, kThreads, 0, s>>>(a32);
+    else k_it_resid<double><<<h->igrid64.k2, kThreads, 0, s>>>(a64);
     RP_TRY_CUDA(cudaEventRecord(ev[3 * it + 2], s));
-    if (mixed) k_it_xp<float><<<h->grid, kThreads, 0, s>>>(a32);
-    else k_it_xp<double><<<h->grid, kThreads, 0, s>>>(a64);
+    if (mixed) k_it_xp<float><<<h->igrid32.k3, kThreads, 0, s>>>(a32);
+    else k_it_xp<double><<<h->igrid64.k3, kThreads, 0, s>>>(a64);
     RP_TRY_CUDA(cudaEventRecord(ev[3 * it + 3], s));
   }
   RP_TRY_CUDA(cudaGetLastError());

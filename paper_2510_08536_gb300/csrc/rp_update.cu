@@ -1,6 +1,8 @@
 // Value update (Sec. 3, update procedure): the continuous buffer, ordered by
 // rank and LDU order, is reordered into the row-major device matrix by the
-// permutation P (src_of). The sparsity is never rebuilt.
+// permutation P (src_of). The sparsity is never rebuilt. When the iteration
+// runs on the sliced layout, a second gather refills its values from the
+// CSR values (k_slice_vals: 4 + 8 bytes read, 8 + 4 written per padded entry).
 //
 // Roofline: HBM bound. Per stored entry one 4-byte index read, one 8-byte
 // gathered read and one 8-byte write (+4 bytes for the FP32 copy); the
@@ -85,7 +87,7 @@ static rp_status permute_all(rp_handle* h, const double* buf, cudaStream_t s) {
                                                            nullptr);
   }
   RP_TRY_CUDA(cudaGetLastError());
-  return RP_OK;
+  return fill_sliced(h, s);
 }
 
 }  // namespace rp

@@ -22,6 +22,7 @@ RP_OK, RP_EINVAL, RP_EDUP, RP_ERANGE, RP_EOVERFLOW, RP_ENOMEM, RP_ECUDA = range(
 RP_NOT_CONVERGED, RP_BREAKDOWN, RP_DEVICE_TIMEOUT, RP_EUNSUPPORTED = 7, 8, 9, 10
 RP_MEM_DEVICE, RP_MEM_HOST, RP_MEM_HOST_DIRECT = 0, 1, 2
 RP_FP64, RP_MIXED, RP_MIXED_RU = 0, 1, 2
+RP_LAYOUT_AUTO, RP_LAYOUT_CSR = 0, 1
 PRECISIONS = {"fp64": RP_FP64, "mixed": RP_MIXED, "mixed_ru": RP_MIXED_RU}
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -40,7 +41,7 @@ class Options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("spin_limit", ctypes.c_int64),
-                ("host_loop", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ru_delta", ctypes.c_double)]
+                ("host_loop", ctypes.c_int32), ("layout", ctypes.c_int32), ("ru_delta", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -50,6 +51,11 @@ class SolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SlicedView(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("n_slices", "n_entries", "ibuf_len")] + \
+               [(k, ctypes.c_void_p) for k in ("desc", "ibuf", "pos", "vals", "vals32")]
 
 
 class MapView(ctypes.Structure):
@@ -79,6 +85,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rp_update_values": (i32, [vp, vp, vp, vp, vp, i32, vp]),
         "rp_get_values": (i32, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "rp_spmv": (i32, [vp, vp, vp, vp, vp]),
+        "rp_iter_spmv": (i32, [vp, vp, vp, i32, vp]),
+        "rp_get_sliced_view": (i32, [vp, ctypes.POINTER(SlicedView)]),
         "rp_spmv_noalloc": (i32, [i64, vp, vp, vp, vp, vp, vp, vp]),
         "rp_batch_build": (i32, [ctypes.POINTER(LduDesc), i32, ctypes.POINTER(Options), ctypes.POINTER(vp)]),
         "rp_batch_update_solve": (i32, [vp, vp, i32, vp, vp, dbl, i32, ctypes.POINTER(SolveInfo), vp]),
@@ -255,6 +263,37 @@ def spmv(h: Handle, x, y, xy=None, stream=None):
     _check(load().rp_spmv(h.ptr, _ptr(x), _ptr(y), _ptr(xy), _stream(stream)), "rp_spmv")
 
 
+def iter_spmv(h: Handle, x, y, precision: str = "fp64", stream=None):
+    """rp_iter_spmv: y = A x with the PCG iteration's own kernel (float64 x/y
+    for "fp64", float32 x/y on the FP32 values otherwise)."""
+    _check(load().rp_iter_spmv(h.ptr, _ptr(x), _ptr(y), PRECISIONS[precision], _stream(stream)), "rp_iter_spmv")
+
+
+def sliced_sizes(h: Handle):
+    """(n_slices, n_entries, ibuf_len) of the sliced layout, or None when the
+    iteration runs on the CSR arrays."""
+    v = SlicedView()
+    _check(load().rp_get_sliced_view(h.ptr, ctypes.byref(v)), "rp_get_sliced_view")
+    return (v.n_slices, v.n_entries, v.ibuf_len) if v.n_slices else None
+
+
+def get_sliced_view(h: Handle) -> dict:
+    """rp_get_sliced_view, copied into torch tensors on the device (None when
+    the iteration runs on the CSR arrays)."""
+    v = SlicedView()
+    _check(load().rp_get_sliced_view(h.ptr, ctypes.byref(v)), "rp_get_sliced_view")
+    if v.n_slices == 0:
+        return None
+    import torch
+    torch.cuda.synchronize()
+    return dict(n_slices=v.n_slices, n_entries=v.n_entries, ibuf_len=v.ibuf_len,
+                desc=_view(v.desc, 2 * (v.n_slices + 1), "<i4").clone(),
+                ibuf=_view(v.ibuf, v.ibuf_len, "<i4").clone(),
+                pos=_view(v.pos, v.n_entries, "<i4").clone(),
+                vals=_view(v.vals, v.n_entries, "<f8").clone(),
+                vals32=_view(v.vals32, v.n_entries, "<f4").clone() if v.vals32 else None)
+
+
 def batch_build(systems, want_fp32: bool = True, **opts) -> Handle:
     """rp_batch_build: one handle holding every independent system (one part each)."""
     lib = load()
@@ -365,4 +404,5 @@ class Exports:
                     "rp_update_values_packed", "rp_update_values", "rp_get_values", "rp_spmv", "rp_solve",
                     "rp_solve_adjoint", "rp_profile_iteration", "rp_entry_grad", "rp_face_grad", "rp_destroy", "rp_status_str",
                     "rp_last_error", "rp_spmv_noalloc", "rp_batch_build", "rp_batch_update_solve",
-                    "rp_batch_set_config", "rp_batch_autotune", "rp_set_solver_options")
+                    "rp_batch_set_config", "rp_batch_autotune", "rp_set_solver_options", "rp_iter_spmv",
+                    "rp_get_sliced_view")
