@@ -34,10 +34,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "update+PCG ms/time-step at 256^3 cells, FP64 vs mixed; SpMV HBM GB/s vs peak"
-# DRAM bytes per launch from an ncu capture of the same kernel: 477.4 MB on the 192^3
-# case, scaled to a 256^3 launch by the ratio of algorithmic bytes (one pass per array).
-# Set to None when the kernel changes until it is captured again.
-PROFILED_TRAFFIC = {("mixed_256", "k_it_spmv<float>"): 1132.7e6}
+# DRAM bytes per launch from ncu captures of the same kernels on the 192^3 case, scaled to
+# a 256^3 launch by the ratio of algorithmic bytes (one pass per array): sliced FP32 SpMV
+# 313.8 MB of 319.7 MB algorithmic, sliced FP64 567.9 MB of 573.9 MB, CSR FP32 477.4 MB of
+# 479.5 MB. Remove an entry when its kernel changes, until it is captured again.
+PROFILED_TRAFFIC = {("mixed_256", "k_it_spmv_sl<float>"): 756.3e6,
+                    ("mixed_256", "k_it_spmv_sl<double>"): 1359.0e6,
+                    ("mixed_256", "k_it_spmv<float>"): 1132.7e6}
+# FP64 FMA issue rate of a GB300 SM (2 per clock; 152 SMs x 2 x 2 flop x 2.07 GHz =
+# 1.26 TFLOP/s, the nominal 1.25): the FP64 path is bound by it, not by HBM.
+FP64_FMA_PER_SM_CLK = 2
 WORKLOAD_TEXT = {
     "mixed_256": "256^3 cells (16,777,216), k=128 CPU ranks (8x4x4) merged into 1 CSR, lognormal(0,1.0) face "
                  "coefficients redrawn every step, rhs U[-1,1] seed 0, rel. residual 1e-9 from x=0, inner tol 1e-5",
@@ -477,6 +483,16 @@ def run_ours(args):
     roof["algorithmic_bytes"] = spmv_bytes(head)
     roof["ms_per_launch"] = kern[head]["spmv"]
     other = [p for p in precs if p != head]
+    # FP64 SpMV against the FP64 FMA rate: one FMA per stored (padded) entry and one for p.q
+    fp64_alu = None
+    if "fp64" in kern:
+        fma = (sliced[1] if sliced else nnz) + n
+        sm_mhz = clocks.get("fp64", {}).get("sm_max_mhz") or 2070.0
+        peak_tf = torch.cuda.get_device_properties(dev).multi_processor_count * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+        ach_tf = 2 * fma / (kern["fp64"]["spmv"] * 1e-3) / 1e12
+        fp64_alu = {"bound": "alu", "kernel": f"{k1_name}<double>", "achieved": round(ach_tf, 4), "unit": "TFLOP/s",
+                    "peak": round(peak_tf, 4), "peak_kind": "derived: SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                    "frac": round(ach_tf / peak_tf, 4), "fma_per_launch": fma}
     kernels = {}
     for prec in precs:
         w = 8 if prec == "fp64" else 4
@@ -575,6 +591,7 @@ def run_ours(args):
         "per_precision": results, "kernels": kernels, "roofline": roof,
         "roofline_other_spmv": {o: {"achieved": round(gbs(spmv_bytes(o), kern[o]["spmv"]), 1),
                                     "frac": round(gbs(spmv_bytes(o), kern[o]["spmv"]) / hbm_peak, 4)} for o in other},
+        "roofline_fp64_spmv": fp64_alu,
         "map_build_ms": round(build_ms, 1), "input_setup_s": round(setup_s, 1), "update_paths": update_paths,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": results[head]["gpu_launches"], "batched": batched,
         "clocks": clocks[head], "clocks_other": {o: clocks[o] for o in other},
