@@ -44,6 +44,14 @@ PROFILED_TRAFFIC = {("mixed_256", "k_it_spmv_sl<float>"): 756.3e6,
 # FP64 FMA issue rate of a GB300 SM (2 per clock; 152 SMs x 2 x 2 flop x 2.07 GHz =
 # 1.26 TFLOP/s, the nominal 1.25): the FP64 path is bound by it, not by HBM.
 FP64_FMA_PER_SM_CLK = 2
+MAX_SM_MHZ = 2070.0  # GB300 maximum SM clock (the sampled clocks.max.sm where available)
+
+
+def fp64_peak_tflops(dev, sm_mhz):
+    """Derived FP64 peak: SMs x FP64 FMA per SM clock x 2 flop x SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
 WORKLOAD_TEXT = {
     "mixed_256": "256^3 cells (16,777,216), k=128 CPU ranks (8x4x4) merged into 1 CSR, lognormal(0,1.0) face "
                  "coefficients redrawn every step, rhs U[-1,1] seed 0, rel. residual 1e-9 from x=0, inner tol 1e-5",
@@ -263,6 +271,16 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
                      "iterations_sum_mean": statistics.mean(iters),
                      "algorithmic_GBps": round(gbps, 1), "frac_of_hbm": round(gbps / hbm_peak, 4),
                      "max_rel_residual": max(i["rel_residual"] for infos in infos_all for i in infos)}
+        if prec == "fp64":
+            # FP64 instructions of one step: per iteration one FMA per entry + ~8 per row
+            # (p.q, r update, r.z, r.r, z, x and p updates), per residual pass nz + 8 n
+            ops = sum(inf["iterations"] * (nz + 8 * nn) + inf["passes"] * (nz + 8 * nn)
+                      for infos in infos_all for inf, (nn, nz) in zip(infos, sizes)) / len(infos_all)
+            peak = fp64_peak_tflops(dev, MAX_SM_MHZ)
+            ach = 2 * ops / (ms * 1e-3) / 1e12
+            out[prec]["fp64_alu"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": round(ach, 4),
+                                     "peak": round(peak, 4), "frac": round(ach / peak, 4),
+                                     "fp64_instructions_per_step": int(ops)}
     h.close()
     if args.only_batch:
         return out
@@ -487,8 +505,8 @@ def run_ours(args):
     fp64_alu = None
     if "fp64" in kern:
         fma = (sliced[1] if sliced else nnz) + n
-        sm_mhz = clocks.get("fp64", {}).get("sm_max_mhz") or 2070.0
-        peak_tf = torch.cuda.get_device_properties(dev).multi_processor_count * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+        sm_mhz = clocks.get("fp64", {}).get("sm_max_mhz") or MAX_SM_MHZ
+        peak_tf = fp64_peak_tflops(dev, sm_mhz)
         ach_tf = 2 * fma / (kern["fp64"]["spmv"] * 1e-3) / 1e12
         fp64_alu = {"bound": "alu", "kernel": f"{k1_name}<double>", "achieved": round(ach_tf, 4), "unit": "TFLOP/s",
                     "peak": round(peak_tf, 4), "peak_kind": "derived: SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",

@@ -21,6 +21,8 @@ written for a reader to check against the paper by eye:
   (Sec. 3, update procedure);
 * Jacobi-preconditioned CG for the merged pressure system (the paper solves
   it with CG, Sec. 4; the preconditioner is Jacobi here);
+* Jacobi-preconditioned BiCGStab for the non-symmetric momentum system (the
+  paper's momentum solver, Sec. 4);
 * FP32-inner / FP64-outer iterative refinement, the adjoint solve and the
   gradients with respect to the stored entries (plain definitions).
 
@@ -367,6 +369,86 @@ def pcg(A, dinv, b, tol=1e-9, max_iter=10000, x0=None) -> SolveResult:
         beta = rz_new / rz
         p = z + beta * p
         rz = rz_new
+    tr = b - A @ x
+    return SolveResult(x, it, status, float(np.sqrt(rr / bb)), float(np.sqrt((tr @ tr) / bb)))
+
+
+def bicgstab(A, dinv, b, tol=1e-9, max_iter=10000, x0=None) -> SolveResult:
+    """Jacobi-preconditioned BiCGStab (van der Vorst, 1992) for the non-symmetric
+    momentum system (the paper's momentum solver is BiCGStab, Sec. 4), with the
+    preconditioner applied to the search directions (right preconditioning).
+
+    From r = b - A x (x0 = 0 unless given) and the shadow residual rhat = r, with
+    rho_old = alpha = omega = 1 and p = v = 0, each iteration takes
+    rho = (rhat, r), beta = (rho / rho_old)(alpha / omega), p = r + beta (p - omega v),
+    phat = D^-1 p, v = A phat, alpha = rho / (rhat, v), s = r - alpha v; if
+    ||s|| <= tol ||b|| it ends with x += alpha phat; else shat = D^-1 s, t = A shat,
+    omega = (t, s) / (t, t), x += alpha phat + omega shat, r = s - omega t. Each
+    iteration counts once (two products with A). A recursive residual at the target
+    is confirmed with b - A x; if that fails the run restarts from the true residual
+    (new rhat). rho = 0, (rhat, v) = 0 or omega = 0 end the run with BREAKDOWN."""
+    b = np.asarray(b, np.float64)
+    bb = float(b @ b)
+    if bb == 0.0:
+        return SolveResult(np.zeros_like(b), 0, OK, 0.0, 0.0)
+    thresh = tol * tol * bb
+    x = np.zeros_like(b) if x0 is None else np.array(x0, np.float64)
+    r = b - A @ x if x0 is not None else b.copy()
+    rr = float(r @ r)
+    it = 0
+    status = NOT_CONVERGED
+    restart = True
+    while True:
+        if restart:
+            restart = False
+            if rr <= thresh:
+                tr = b - A @ x
+                trr = float(tr @ tr)
+                if trr <= thresh:
+                    status = OK
+                    break
+                r, rr = tr, trr
+            rhat = r.copy()
+            rho_old = alpha = omega = 1.0
+            p = np.zeros_like(b)
+            v = np.zeros_like(b)
+            rho = float(rhat @ r)
+        if it >= max_iter:
+            break
+        if rho == 0.0:
+            status = BREAKDOWN
+            break
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        phat = dinv * p
+        v = A @ phat
+        rv = float(rhat @ v)
+        if rv == 0.0:
+            status = BREAKDOWN
+            break
+        alpha = rho / rv
+        s = r - alpha * v
+        it += 1
+        ss = float(s @ s)
+        if ss <= thresh:
+            x = x + alpha * phat
+            r, rr = s, ss
+            restart = True
+            continue
+        shat = dinv * s
+        t = A @ shat
+        omega = float(t @ s) / float(t @ t)
+        x = x + alpha * phat + omega * shat
+        r = s - omega * t
+        rr = float(r @ r)
+        if rr <= thresh:
+            restart = True
+            continue
+        if omega == 0.0:
+            status = BREAKDOWN
+            break
+        rho_old = rho
+        rho = float(rhat @ r)
     tr = b - A @ x
     return SolveResult(x, it, status, float(np.sqrt(rr / bb)), float(np.sqrt((tr @ tr) / bb)))
 

@@ -302,6 +302,78 @@ class Assembler:
         return out
 
 
+# ---------------------------------------------------------------- momentum (non-symmetric) systems
+
+MOMENTUM_U0 = 1.0   # velocity scale (cells per unit time)
+MOMENTUM_CT = 0.1   # transient term V / dt on the diagonal
+
+
+def _face_flux(mesh: BoxMesh, u0: float) -> np.ndarray:
+    """Volume flux through every internal face (global face order, owner -> neighbour
+    along +x / +y / +z, unit area) of the velocity field
+    u = u0 (sin(pi X) cos(pi Y), -cos(pi X) sin(pi Y), sin(2 pi Z) / 4) at the face centre,
+    with X, Y, Z the cell-unit coordinates scaled to [0, 1]: a cavity-like vortex."""
+    nx, ny, nz = mesh.nx, mesh.ny, mesh.nz
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx - 1), indexing="ij")
+    X, Y = (i + 1.0) / nx, (j + 0.5) / ny
+    fx = u0 * np.sin(np.pi * X) * np.cos(np.pi * Y)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny - 1), np.arange(nx), indexing="ij")
+    X, Y = (i + 0.5) / nx, (j + 1.0) / ny
+    fy = -u0 * np.cos(np.pi * X) * np.sin(np.pi * Y)
+    k, j, i = np.meshgrid(np.arange(nz - 1), np.arange(ny), np.arange(nx), indexing="ij")
+    Z = (k + 1.0) / nz
+    fz = 0.25 * u0 * np.sin(2.0 * np.pi * Z) + 0.0 * i
+    return np.concatenate([fx.ravel(), fy.ravel(), fz.ravel()])
+
+
+def momentum_staging(mesh: BoxMesh, sigma: float = 0.5, seed: int = 100, u0: float = MOMENTUM_U0,
+                     ct: float = MOMENTUM_CT) -> np.ndarray:
+    """Staging buffer (general storage: [diag | upper | lower | iface] per rank) of an
+    upwind convection-diffusion (momentum) matrix: per internal face, diffusion
+    a_f ~ lognormal(0, sigma) (seeded, global face order) and flux F_f from
+    ``_face_flux``; the owner row couples to the neighbour with -(a_f + max(-F_f, 0)),
+    the neighbour row to the owner with -(a_f + max(F_f, 0)); the diagonal is ct plus
+    the magnitudes of its row's off-diagonals (row sums = ct). Interface entries take
+    the value of the side their row lies on."""
+    n = mesh.n_cells
+    nf = mesh.n_internal_faces
+    a = np.random.default_rng(seed).lognormal(0.0, sigma, size=nf)
+    F = _face_flux(mesh, u0)
+    up = -(a + np.maximum(-F, 0.0))   # row = owner (low side), col = neighbour
+    lo = -(a + np.maximum(F, 0.0))    # row = neighbour (high side), col = owner
+    owner, nbr = _global_face_cells(mesh)
+    diag = np.full(n, ct, np.float64)
+    np.add.at(diag, owner, -up)
+    np.add.at(diag, nbr, -lo)
+    ext = np.concatenate([diag, up, lo])
+    parts = []
+    for r in mesh.ranks:
+        parts.append(r.cell_gid)
+        parts.append(n + r.face_gid)
+        parts.append(n + nf + r.face_gid)
+        if r.n_iface:
+            row_g = r.cell_gid[r.iface_row]
+            col_g = np.concatenate([mesh.ranks[q].cell_gid[c:c + 1] for q, c in
+                                    zip(r.iface_nbr_rank, r.iface_nbr_col)])
+            low_side = row_g < col_g
+            parts.append(np.where(low_side, n + r.iface_face_gid, n + nf + r.iface_face_gid))
+    return ext[np.concatenate(parts)]
+
+
+def _global_face_cells(mesh: BoxMesh):
+    """Global owner (low side) and neighbour cell of every internal face."""
+    nx, ny, nz = mesh.nx, mesh.ny, mesh.nz
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx - 1), indexing="ij")
+    ox = (i + nx * (j + ny * k)).ravel()
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny - 1), np.arange(nx), indexing="ij")
+    oy = (i + nx * (j + ny * k)).ravel()
+    k, j, i = np.meshgrid(np.arange(nz - 1), np.arange(ny), np.arange(nx), indexing="ij")
+    oz = (i + nx * (j + ny * k)).ravel()
+    owner = np.concatenate([ox, oy, oz])
+    nbr = np.concatenate([ox + 1, oy + nx, oz + nx * ny])
+    return owner, nbr
+
+
 def uniform_vector(mesh: BoxMesh, seed: int) -> np.ndarray:
     """U[-1, 1] over global cells (seeded), returned in merged row order."""
     g = np.random.default_rng(seed).uniform(-1.0, 1.0, size=mesh.n_cells)
@@ -335,6 +407,8 @@ WORKLOADS = {
     "adjoint_128": dict(n=(128, 128, 128), p=(4, 4, 4), sigma=0.5),
     # profiling size: every pass larger than L2, a few GB on the device
     "profile_192": dict(n=(192, 192, 192), p=(3, 3, 3), sigma=1.0),
+    # non-symmetric momentum system on the headline mesh (momentum_staging)
+    "momentum_256": dict(n=(256, 256, 256), p=(8, 4, 4), sigma=0.5),
 }
 
 

@@ -412,3 +412,78 @@ def test_gradients_by_central_differences():
         l, u = r0.lower_addr[f], r0.upper_addr[f]
         chain = gs[l] + gs[u] - gs[n0 + f] - gs[n0 + f0 + f]
         assert abs(chain - fg[f]) <= 1e-12 * max(1.0, abs(fg[f]))
+
+
+# ---------------------------------------------------------------- BiCGStab (momentum)
+
+
+def _momentum(dims, parts, seed=100):
+    mesh = synth.box_mesh(*dims, *parts)
+    stg = synth.momentum_staging(mesh, 0.5, seed)
+    (m,) = O.repartition_map(mesh.ranks, 1)
+    vals = O.update_values(m.src_of, stg)
+    A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
+    dinv = O.jacobi_inverse(m.row_ptr, m.col_idx, vals, m.diag_pos)
+    return mesh, stg, m, A, dinv, synth.uniform_vector(mesh, 0)
+
+
+def test_momentum_matrix_rows_and_ldu_product():
+    """The synthetic momentum matrix is non-symmetric with row sums ct, and the merged
+    CSR product equals the per-rank LDU products with distinct lower / upper values."""
+    mesh, stg, m, A, dinv, b = _momentum((9, 7, 6), (3, 1, 2))
+    n = mesh.n_cells
+    np.testing.assert_allclose(A @ np.ones(n), synth.MOMENTUM_CT, rtol=0, atol=1e-12)
+    assert abs(A - A.T).max() > 0.1
+    x = np.random.default_rng(5).standard_normal(n)
+    np.testing.assert_allclose(A @ x, O.ldu_matvec(mesh.ranks, stg, x, False), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("dims,parts", [((7, 6, 5), (2, 2, 1)), ((16, 16, 16), (2, 2, 2)), ((11, 9, 4), (1, 3, 1))])
+def test_bicgstab_matches_scipy(dims, parts):
+    """scipy.sparse.linalg.bicgstab with M = D^-1 is an independent implementation of
+    the same recurrence: same iterate, same count (scipy does not count a final half step)."""
+    import scipy.sparse.linalg as spl
+    mesh, stg, m, A, dinv, b = _momentum(dims, parts)
+    res = O.bicgstab(A, dinv, b, tol=1e-10)
+    calls = []
+    xs, info = spl.bicgstab(A, b, rtol=1e-10, atol=0.0, M=sp.diags(dinv), callback=lambda xk: calls.append(1))
+    assert info == 0 and res.status == O.OK
+    np.testing.assert_allclose(res.x, xs, rtol=1e-12, atol=1e-14)
+    assert res.iterations - len(calls) in (0, 1)
+
+
+def test_bicgstab_matches_dense_solve():
+    mesh, stg, m, A, dinv, b = _momentum((6, 5, 4), (2, 1, 1))
+    res = O.bicgstab(A, dinv, b, tol=1e-12)
+    xe = np.linalg.solve(A.toarray(), b)
+    assert res.status == O.OK and res.true_rel_residual <= 1e-12
+    assert np.linalg.norm(res.x - xe) / np.linalg.norm(xe) <= 1e-10
+
+
+def test_bicgstab_diagonal_system_is_one_step():
+    """A = D: the Jacobi-preconditioned direction is the solution, alpha = 1 up to rounding."""
+    d = np.random.default_rng(3).uniform(1.0, 5.0, 40)
+    A = sp.csr_matrix(sp.diags(d))
+    b = np.random.default_rng(4).uniform(-1.0, 1.0, 40)
+    res = O.bicgstab(A, 1.0 / d, b, tol=1e-9)
+    assert res.status == O.OK and res.iterations == 1
+    np.testing.assert_allclose(res.x, b / d, rtol=1e-15)
+
+
+def test_bicgstab_recursive_residual_tracks_true_residual():
+    """x and r are updated consistently: after k iterations the recursive residual
+    equals b - A x to rounding (a wrong sign or coefficient in either update breaks it)."""
+    mesh, stg, m, A, dinv, b = _momentum((12, 10, 8), (2, 1, 1))
+    for k in (1, 2, 5, 13, 30):
+        res = O.bicgstab(A, dinv, b, tol=1e-14, max_iter=k)
+        assert res.status == O.NOT_CONVERGED and res.iterations == k
+        assert abs(res.rel_residual - res.true_rel_residual) <= 1e-12
+
+
+def test_bicgstab_edge_cases():
+    mesh, stg, m, A, dinv, b = _momentum((5, 4, 3), (1, 1, 1))
+    res = O.bicgstab(A, dinv, np.zeros_like(b))
+    assert res.status == O.OK and res.iterations == 0 and not res.x.any()
+    xe = np.linalg.solve(A.toarray(), b)
+    res = O.bicgstab(A, dinv, b, tol=1e-9, x0=xe)
+    assert res.status == O.OK and res.iterations == 0
