@@ -263,6 +263,21 @@ typedef struct rp_solve_info {
 rp_status rp_solve(rp_handle* h, const double* b, double* x, double tol, int32_t precision,
                    int32_t x_is_guess, int32_t where, rp_solve_info* info, void* stream);
 
+/* Solve a non-symmetric system A x = b (the momentum equation, which the paper
+ * solves with BiCGStab; Sec. 4) to ||b - A x||_2 <= tol ||b||_2 (true
+ * residual, FP64) with Jacobi-preconditioned BiCGStab (van der Vorst, 1992;
+ * D^-1 applied to the search directions) in FP64 on the handle's current
+ * values (general storage: lower and upper coefficients differ). One
+ * iteration = two products with A. A recursive residual at the target is
+ * confirmed with b - A x; if that fails the iteration restarts from the true
+ * residual with a new shadow residual (at most max_restarts times).
+ * (rhat, v) = 0, (rhat, r) = 0 or omega = 0 end with RP_BREAKDOWN; max_iter
+ * caps the iterations (RP_NOT_CONVERGED). Parts, x_is_guess, where, info and
+ * the return value as in rp_solve; info->outer_iterations is 0. Allocates
+ * five n-vectors on first use. */
+rp_status rp_solve_bicgstab(rp_handle* h, const double* b, double* x, double tol, int32_t x_is_guess,
+                            int32_t where, rp_solve_info* info, void* stream);
+
 /* ---- Batched form: many independent systems in one persistent launch ----
  * Each system is one LDU matrix without interfaces (n_iface = 0); system s
  * becomes GPU part s (n_parts = count, alpha = 1, Sec. 3). Rows, buffers and

@@ -1,0 +1,512 @@
+// Jacobi-preconditioned BiCGStab (van der Vorst, 1992) on the merged matrix:
+// the solver of the non-symmetric momentum system (the paper solves momentum
+// with BiCGStab, pressure with CG; Sec. 4). FP64 throughout.
+//
+// One CUDA graph per handle: while (outer) { residual pass; while (inner) {
+// B1; B2; B3; B4; B5 } }, every loop bounded by device counters.
+//   residual pass  r = b - A x, rhat = r, p = v = 0, (r, r) [, (b, b)]; decides
+//   B1             beta = (rho / rho_old)(alpha / omega); p = r + beta (p - omega v); phat = D^-1 p
+//   B2 (SpMV)      v = A phat, (rhat, v) -> alpha = rho / (rhat, v)
+//   B3             s = r - alpha v; shat = D^-1 s; (s, s) -> half step when ||s|| <= tol ||b||
+//   B4 (SpMV)      t = A shat, (t, s), (t, t) -> omega
+//   B5             x += alpha phat + omega shat; r = s - omega t; (r, r), (rhat, r) -> rho, stop
+//                  (half step: x += alpha phat, r = s, stop)
+// A recursive residual at the target ends the inner loop; the residual pass
+// then confirms it with b - A x or restarts from the true residual with a
+// new shadow residual (bounded by max_restarts). Scalars live in device
+// memory and are written only by the last block of a kernel. The SpMVs run
+// over the sliced layout when the handle has it (spmv_sl_body), else CSR.
+//
+// Roofline: FP64-FMA bound on GB300 (one FMA per stored entry per product,
+// two products per iteration, ~14 FP64 instructions per row in B1/B3/B5).
+#include "rp_common.cuh"
+#include "rp_spmv.cuh"
+
+namespace rp {
+
+struct BsCtl {
+  double bb, thresh, tol, rr, ss;
+  double rho, rho_old, alpha, omega;
+  int32_t iter, max_iter, stop, status, pass, restarts, max_restarts, half, x_zero;
+  unsigned int ticket;
+};
+
+struct BsArgs {
+  int64_t n;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* vals;
+  const double* dinv;
+  Parts<double> parts;
+  Sliced<double> sl;
+  double *r, *rhat, *p, *v, *s, *t, *phat, *shat;
+  BsCtl* c;
+  SolveIO* io;
+  double* partials;
+  cudaGraphConditionalHandle inner, outer;
+  int in_graph;
+};
+
+struct BsState {
+  double *rhat = nullptr, *s = nullptr, *t = nullptr, *phat = nullptr, *shat = nullptr;
+  BsCtl* ctl = nullptr;
+  SolveIO* io = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int grid_vec = 1, grid_sl = 1;
+};
+
+namespace {
+
+__global__ void k_bs_setup(BsCtl* c, SolveIO* io, const double* b, double* x, double tol, int x_zero, int max_iter,
+                           int max_restarts) {
+  io->b = b;
+  io->x = x;
+  c->tol = tol;
+  c->x_zero = x_zero;
+  c->max_iter = max_iter;
+  c->max_restarts = max_restarts;
+  c->iter = 0;
+  c->pass = 0;
+  c->restarts = 0;
+  c->status = -1;
+  c->stop = 0;
+  c->half = 0;
+  c->ticket = 0u;
+}
+
+// residual pass: r = b - A x (cold start: r = b, x = 0), rhat = r, p = v = 0
+__global__ void __launch_bounds__(kThreads) k_bs_res(BsArgs a) {
+  BsCtl* c = a.c;
+  const bool first = c->pass == 0;
+  const bool cold = first && c->x_zero;
+  const double* __restrict__ b = a.io->b;
+  double* __restrict__ x = a.io->x;
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    double ri;
+    if (cold) {
+      ri = bi;
+      x[i] = 0.0;
+    } else {
+      ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
+    }
+    a.r[i] = ri;
+    a.rhat[i] = ri;
+    a.p[i] = 0.0;
+    a.v[i] = 0.0;
+    rr += ri * ri;
+    bb += bi * bi;
+  }
+  double v[2] = {rr, bb}, tot[2];
+  if (reduce_last_block<2>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
+    if (first) {
+      c->bb = tot[1];
+      c->thresh = c->tol * c->tol * tot[1];
+    }
+    c->rr = tot[0];
+    c->pass += 1;
+    bool go = false;
+    if (tot[0] <= c->thresh) {
+      c->status = RP_OK;
+    } else if (c->status == RP_BREAKDOWN) {
+    } else if (!isfinite(tot[0])) {
+      c->status = RP_BREAKDOWN;
+    } else if (c->iter >= c->max_iter || (!first && c->restarts >= c->max_restarts)) {
+      c->status = RP_NOT_CONVERGED;
+    } else {
+      if (!first) c->restarts += 1;
+      c->rho = tot[0];  // (rhat, r) with rhat = r
+      c->rho_old = c->alpha = c->omega = 1.0;
+      c->half = 0;
+      go = true;
+    }
+    c->stop = go ? 0 : 1;
+    if (a.in_graph) {
+      cudaGraphSetConditional(a.inner, go ? 1u : 0u);
+      cudaGraphSetConditional(a.outer, go ? 1u : 0u);
+    }
+  }
+}
+
+// B1: p = r + beta (p - omega v); phat = D^-1 p
+__global__ void __launch_bounds__(kThreads) k_bs_p(BsArgs a) {
+  const BsCtl* c = a.c;
+  if (c->stop) return;
+  const double beta = (c->rho / c->rho_old) * (c->alpha / c->omega), omega = c->omega;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double pi = fma(beta, fma(-omega, a.v[i], a.p[i]), a.r[i]);
+    a.p[i] = pi;
+    a.phat[i] = a.dinv[i] * pi;
+  }
+}
+
+// B2 epilogue: (rhat, v) -> alpha
+struct BsEpiV {
+  const double* rhat;
+  BsCtl* c;
+  double* partials;
+  double acc = 0.0;
+  __device__ __forceinline__ void row(int64_t i, double y) { acc = fma(rhat[i], y, acc); }
+  __device__ __forceinline__ void timeout() {
+    c->status = RP_DEVICE_TIMEOUT;
+    c->stop = 1;
+  }
+  __device__ __forceinline__ void finish() {
+    double v[1] = {acc}, tot[1];
+    if (reduce_last_block<1>(v, partials, &c->ticket, tot) && threadIdx.x == 0) {
+      if (c->status == RP_DEVICE_TIMEOUT) {
+        c->stop = 1;
+      } else if (tot[0] == 0.0 || !isfinite(tot[0])) {
+        c->status = RP_BREAKDOWN;
+        c->stop = 1;
+      } else {
+        c->alpha = c->rho / tot[0];
+      }
+    }
+  }
+};
+
+// B4 epilogue: (t, s), (t, t) -> omega
+struct BsEpiT {
+  const double* s;
+  BsCtl* c;
+  double* partials;
+  double ts = 0.0, tt = 0.0;
+  __device__ __forceinline__ void row(int64_t i, double y) {
+    ts = fma(y, s[i], ts);
+    tt = fma(y, y, tt);
+  }
+  __device__ __forceinline__ void timeout() {
+    c->status = RP_DEVICE_TIMEOUT;
+    c->stop = 1;
+  }
+  __device__ __forceinline__ void finish() {
+    double v[2] = {ts, tt}, tot[2];
+    if (reduce_last_block<2>(v, partials, &c->ticket, tot) && threadIdx.x == 0) {
+      const double omega = tot[0] / tot[1];
+      if (c->status == RP_DEVICE_TIMEOUT) {
+        c->stop = 1;
+      } else if (!(tot[1] > 0.0) || !isfinite(omega)) {
+        c->status = RP_BREAKDOWN;
+        c->stop = 1;
+      } else {
+        c->omega = omega;
+      }
+    }
+  }
+};
+
+// B2 / B4 over CSR (any number of parts) or the sliced layout
+template <int WHICH>
+__global__ void __launch_bounds__(kThreads) k_bs_spmv(BsArgs a) {
+  BsCtl* c = a.c;
+  if (c->stop || (WHICH == 2 && c->half)) return;
+  if constexpr (WHICH == 1) {
+    BsEpiV e{a.rhat, c, a.partials};
+    spmv_csr_body<double>(a.n, a.parts, a.row_ptr, a.col, a.vals, a.phat, a.v, e);
+  } else {
+    BsEpiT e{a.s, c, a.partials};
+    spmv_csr_body<double>(a.n, a.parts, a.row_ptr, a.col, a.vals, a.shat, a.t, e);
+  }
+}
+template <int WHICH>
+__global__ void __launch_bounds__(kSlThreads, 5) k_bs_spmv_sl(BsArgs a) {
+  BsCtl* c = a.c;
+  if (c->stop || (WHICH == 2 && c->half)) return;
+  if constexpr (WHICH == 1) {
+    BsEpiV e{a.rhat, c, a.partials};
+    spmv_sl_body<double>(a.sl, a.n, a.phat, a.v, e);
+  } else {
+    BsEpiT e{a.s, c, a.partials};
+    spmv_sl_body<double>(a.sl, a.n, a.shat, a.t, e);
+  }
+}
+
+// B3: s = r - alpha v; shat = D^-1 s; (s, s)
+__global__ void __launch_bounds__(kThreads) k_bs_s(BsArgs a) {
+  BsCtl* c = a.c;
+  if (c->stop) return;
+  const double alpha = c->alpha;
+  double ss = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = fma(-alpha, a.v[i], a.r[i]);
+    a.s[i] = si;
+    a.shat[i] = a.dinv[i] * si;
+    ss = fma(si, si, ss);
+  }
+  double v[1] = {ss}, tot[1];
+  if (reduce_last_block<1>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
+    c->ss = tot[0];
+    c->half = tot[0] <= c->thresh ? 1 : 0;
+  }
+}
+
+// B5: x += alpha phat + omega shat; r = s - omega t; (r, r), (rhat, r)
+// (half step: x += alpha phat; r = s); decides the next iteration
+__global__ void __launch_bounds__(kThreads) k_bs_xr(BsArgs a) {
+  BsCtl* c = a.c;
+  if (c->stop) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.in_graph) cudaGraphSetConditional(a.inner, 0);
+    return;
+  }
+  const bool half = c->half;
+  const double alpha = c->alpha, omega = c->omega;
+  double* __restrict__ x = a.io->x;
+  double rr = 0.0, rhr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (half) {
+      x[i] = fma(alpha, a.phat[i], x[i]);
+      a.r[i] = a.s[i];
+    } else {
+      x[i] = fma(omega, a.shat[i], fma(alpha, a.phat[i], x[i]));
+      const double ri = fma(-omega, a.t[i], a.s[i]);
+      a.r[i] = ri;
+      rr = fma(ri, ri, rr);
+      rhr = fma(a.rhat[i], ri, rhr);
+    }
+  }
+  double v[2] = {rr, rhr}, tot[2];
+  if (reduce_last_block<2>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
+    c->iter += 1;
+    if (half) {
+      c->rr = c->ss;
+      c->stop = 1;  // the residual pass confirms with b - A x
+    } else {
+      c->rr = tot[0];
+      if (tot[0] <= c->thresh) {
+        c->stop = 1;
+      } else if (c->iter >= c->max_iter) {
+        c->stop = 1;
+      } else if (c->omega == 0.0 || tot[1] == 0.0 || !isfinite(tot[1])) {
+        c->status = RP_BREAKDOWN;
+        c->stop = 1;
+      } else {
+        c->rho_old = c->rho;
+        c->rho = tot[1];
+      }
+    }
+    if (a.in_graph) cudaGraphSetConditional(a.inner, c->stop ? 0u : 1u);
+  }
+}
+
+int resident_blocks(const void* fn, int threads, int smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  return nb < kBlocksPerSm ? nb : kBlocksPerSm;
+}
+
+template <typename T>
+rp_status balloc(T** p, int64_t count) {
+  if (*p) return RP_OK;
+  if (count <= 0) count = 1;
+  if (cudaMalloc((void**)p, (size_t)count * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(RP_ENOMEM, "cudaMalloc of %lld bytes failed", (long long)(count * sizeof(T)));
+  }
+  return RP_OK;
+}
+
+rp_status ensure_bs(rp_handle* h) {
+  if (!h->bs) h->bs = new BsState();
+  BsState* b = h->bs;
+  const int64_t n = h->n + 64;
+  RP_TRY(balloc(&b->rhat, n));
+  RP_TRY(balloc(&b->s, n));
+  RP_TRY(balloc(&b->t, n));
+  RP_TRY(balloc(&b->phat, n));
+  RP_TRY(balloc(&b->shat, n));
+  RP_TRY(balloc(&b->ctl, 1));
+  RP_TRY(balloc(&b->io, 1));
+  const int64_t want = (h->n + kThreads - 1) / kThreads;
+  auto grid = [&](int per_sm) {
+    const int64_t cap = (int64_t)h->num_sms * per_sm;
+    return (int)(want < 1 ? 1 : want < cap ? want : cap);
+  };
+  b->grid_vec = grid(resident_blocks((const void*)k_bs_xr, kThreads, 0));
+  b->grid_sl = grid(resident_blocks((const void*)k_bs_spmv_sl<2>, kSlThreads, SlStage<double>::kSmem));
+  return RP_OK;
+}
+
+BsArgs bs_args(rp_handle* h, cudaGraphConditionalHandle inner, cudaGraphConditionalHandle outer, int in_graph) {
+  BsState* b = h->bs;
+  BsArgs a{};
+  a.n = h->n;
+  a.row_ptr = h->row_ptr;
+  a.col = h->col_idx;
+  a.vals = h->vals;
+  a.dinv = h->dinv;
+  a.parts = parts64(h);
+  a.sl = sliced64(h, h->vals);
+  a.r = h->r;
+  a.rhat = b->rhat;
+  a.p = h->p;
+  a.v = h->q;
+  a.s = b->s;
+  a.t = b->t;
+  a.phat = b->phat;
+  a.shat = b->shat;
+  a.c = b->ctl;
+  a.io = b->io;
+  a.partials = h->partials;
+  a.inner = inner;
+  a.outer = outer;
+  a.in_graph = in_graph;
+  return a;
+}
+
+rp_status node(cudaGraph_t g, cudaGraphNode_t* out, const cudaGraphNode_t* dep, void* fn, int grid, int threads,
+               int smem, void* argp) {
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeKernel;
+  np.kernel.func = fn;
+  np.kernel.gridDim = dim3((unsigned)grid);
+  np.kernel.blockDim = dim3((unsigned)threads);
+  np.kernel.sharedMemBytes = (unsigned)smem;
+  void* args[1] = {argp};
+  np.kernel.kernelParams = args;
+  RP_TRY_CUDA(cudaGraphAddNode(out, g, dep, nullptr, dep ? 1 : 0, &np));
+  return RP_OK;
+}
+
+rp_status while_node(cudaGraph_t g, cudaGraphNode_t* out, const cudaGraphNode_t* dep, cudaGraphConditionalHandle hnd,
+                     cudaGraph_t* body) {
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = hnd;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  RP_TRY_CUDA(cudaGraphAddNode(out, g, dep, nullptr, dep ? 1 : 0, &np));
+  *body = np.conditional.phGraph_out[0];
+  return RP_OK;
+}
+
+// the five inner kernels with their launch shapes
+struct BsLaunch {
+  void* fn;
+  int grid, threads, smem;
+};
+void bs_inner(const rp_handle* h, BsLaunch (&k)[5]) {
+  const BsState* b = h->bs;
+  const bool sl = h->sl_slices > 0;
+  const int gs = sl ? b->grid_sl : h->grid, ts = sl ? kSlThreads : kThreads, ms = sl ? SlStage<double>::kSmem : 0;
+  k[0] = {(void*)k_bs_p, b->grid_vec, kThreads, 0};
+  k[1] = {sl ? (void*)k_bs_spmv_sl<1> : (void*)k_bs_spmv<1>, gs, ts, ms};
+  k[2] = {(void*)k_bs_s, b->grid_vec, kThreads, 0};
+  k[3] = {sl ? (void*)k_bs_spmv_sl<2> : (void*)k_bs_spmv<2>, gs, ts, ms};
+  k[4] = {(void*)k_bs_xr, b->grid_vec, kThreads, 0};
+}
+
+rp_status build_bs_graph(rp_handle* h, cudaGraphExec_t* exec) {
+  cudaGraph_t top = nullptr;
+  RP_TRY_CUDA(cudaGraphCreate(&top, 0));
+  struct Guard {
+    cudaGraph_t g;
+    ~Guard() { cudaGraphDestroy(g); }
+  } guard{top};
+  cudaGraphConditionalHandle hout, hin;
+  RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hout, top, 1, cudaGraphCondAssignDefault));
+  cudaGraphNode_t wout, nres, win, nk[5];
+  cudaGraph_t obody, ibody;
+  RP_TRY(while_node(top, &wout, nullptr, hout, &obody));
+  RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hin, obody, 0, 0));
+  BsArgs a = bs_args(h, hin, hout, 1);
+  RP_TRY(node(obody, &nres, nullptr, (void*)k_bs_res, h->grid, kThreads, 0, &a));
+  RP_TRY(while_node(obody, &win, &nres, hin, &ibody));
+  BsLaunch k[5];
+  bs_inner(h, k);
+  for (int j = 0; j < 5; ++j)
+    RP_TRY(node(ibody, &nk[j], j ? &nk[j - 1] : nullptr, k[j].fn, k[j].grid, k[j].threads, k[j].smem, &a));
+  RP_TRY_CUDA(cudaGraphInstantiate(exec, top, 0));
+  return RP_OK;
+}
+
+// the same kernel sequence launched from the host (profilers that cannot see
+// inside conditional graphs); the control block is read after every kernel group
+rp_status bs_host_loop(rp_handle* h, cudaStream_t s) {
+  BsArgs a = bs_args(h, 0, 0, 0);
+  BsLaunch k[5];
+  bs_inner(h, k);
+  BsCtl c;
+  for (;;) {
+    k_bs_res<<<h->grid, kThreads, 0, s>>>(a);
+    RP_TRY_CUDA(cudaGetLastError());
+    RP_TRY_CUDA(cudaMemcpyAsync(&c, h->bs->ctl, sizeof(BsCtl), cudaMemcpyDeviceToHost, s));
+    RP_TRY_CUDA(cudaStreamSynchronize(s));
+    if (c.stop) break;
+    while (!c.stop) {
+      void* args[1] = {&a};
+      for (auto& kk : k)
+        RP_TRY_CUDA(cudaLaunchKernel(kk.fn, dim3((unsigned)kk.grid), dim3((unsigned)kk.threads), args,
+                                     (size_t)kk.smem, s));
+      RP_TRY_CUDA(cudaMemcpyAsync(&c, h->bs->ctl, sizeof(BsCtl), cudaMemcpyDeviceToHost, s));
+      RP_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  return RP_OK;
+}
+
+}  // namespace
+
+void free_bicgstab(rp_handle* h) {
+  BsState* b = h->bs;
+  if (!b) return;
+  void* ptrs[] = {b->rhat, b->s, b->t, b->phat, b->shat, b->ctl, b->io};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  delete b;
+  h->bs = nullptr;
+}
+
+}  // namespace rp
+
+using namespace rp;
+
+extern "C" rp_status rp_solve_bicgstab(rp_handle* h, const double* b, double* x, double tol, int32_t x_is_guess,
+                                       int32_t where, rp_solve_info* info, void* stream) {
+  if (!h || (!b && h->n) || (!x && h->n)) return fail(RP_EINVAL, "null argument");
+  if (!(tol >= 0.0)) return fail(RP_EINVAL, "tol must be >= 0");
+  if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
+  if (h->n == 0) {
+    if (info) *info = rp_solve_info{RP_OK, 0, 0, 0, 0, 0.0};
+    return RP_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  RP_TRY(ensure_bs(h));
+  BsState* bs = h->bs;
+  if (!bs->graph && !h->opts.host_loop) RP_TRY(build_bs_graph(h, &bs->graph));
+  const double* bd = b;
+  double* xd = x;
+  if (where == RP_MEM_HOST) {
+    if (!h->b_host_stage && cudaMalloc((void**)&h->b_host_stage, 8 * (h->n + 64)) != cudaSuccess)
+      return fail(RP_ENOMEM, "cudaMalloc failed");
+    if (!h->x_host_stage && cudaMalloc((void**)&h->x_host_stage, 8 * (h->n + 64)) != cudaSuccess)
+      return fail(RP_ENOMEM, "cudaMalloc failed");
+    RP_TRY_CUDA(cudaMemcpyAsync(h->b_host_stage, b, 8 * h->n, cudaMemcpyHostToDevice, s));
+    if (x_is_guess) RP_TRY_CUDA(cudaMemcpyAsync(h->x_host_stage, x, 8 * h->n, cudaMemcpyHostToDevice, s));
+    bd = h->b_host_stage;
+    xd = h->x_host_stage;
+  }
+  k_bs_setup<<<1, 1, 0, s>>>(bs->ctl, bs->io, bd, xd, tol, x_is_guess ? 0 : 1, h->opts.max_iter,
+                             h->opts.max_restarts);
+  RP_TRY_CUDA(cudaGetLastError());
+  if (h->opts.host_loop) RP_TRY(bs_host_loop(h, s));
+  else RP_TRY_CUDA(cudaGraphLaunch(bs->graph, s));
+  if (where == RP_MEM_HOST) RP_TRY_CUDA(cudaMemcpyAsync(x, h->x_host_stage, 8 * h->n, cudaMemcpyDeviceToHost, s));
+  if (!info) return RP_OK;
+  BsCtl c;
+  RP_TRY_CUDA(cudaMemcpyAsync(&c, bs->ctl, sizeof(BsCtl), cudaMemcpyDeviceToHost, s));
+  RP_TRY_CUDA(cudaStreamSynchronize(s));
+  info->status = c.status < 0 ? RP_NOT_CONVERGED : c.status;
+  info->iterations = c.iter;
+  info->outer_iterations = 0;
+  info->restarts = c.restarts;
+  info->passes = c.pass;
+  info->rel_residual = c.bb > 0.0 ? sqrt(c.rr / c.bb) : 0.0;
+  return (rp_status)info->status;
+}

@@ -132,6 +132,8 @@ struct IterGrid {
   int k1 = 1, k1s = 1, k2 = 1, k3 = 1;  // K1 on CSR, K1 on the sliced layout, K2, K3
 };
 
+struct BsState;  // BiCGStab work space and graph (rp_bicgstab.cu)
+
 // Per-call pointers of the batched solve (read by the captured kernel).
 struct BatchIO {
   const double* buf;
@@ -245,6 +247,9 @@ struct rp_handle {
   rp::Graphs graphs;
   cudaStream_t capture_stream = nullptr;
 
+  // BiCGStab (non-symmetric systems), allocated on first use
+  rp::BsState* bs = nullptr;
+
   // batched form (one system per part)
   bool batch_ready = false;
   int batch_cluster = 8, batch_threads = 512;  // autotuned by rp_batch_autotune
@@ -271,6 +276,7 @@ rp_status ensure_solver_buffers(rp_handle* h);
 rp_status build_sliced(rp_handle* h, cudaStream_t s);  // after the CSR map
 rp_status fill_sliced(rp_handle* h, cudaStream_t s);   // after every value update
 void free_sliced(rp_handle* h);
+void free_bicgstab(rp_handle* h);
 rp_status build_graphs(rp_handle* h);
 void free_solver(rp_handle* h);
 void free_batch(rp_handle* h);

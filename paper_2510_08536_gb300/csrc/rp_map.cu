@@ -469,6 +469,7 @@ static void free_handle_memory(rp_handle* h) {
   free_solver(h);
   free_batch(h);
   free_sliced(h);
+  free_bicgstab(h);
 }
 
 extern "C" void rp_destroy(rp_handle* h) {

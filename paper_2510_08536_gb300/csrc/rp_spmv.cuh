@@ -1,0 +1,376 @@
+// SpMV building blocks shared by the solvers: row products over CSR (and
+// over the local + non-local CSR of GPU parts), the sliced-layout decoders,
+// the TMA / mbarrier helpers and the two SpMV bodies, y = A x over CSR and
+// over the sliced layout, each followed by a solver-specific epilogue.
+#pragma once
+
+#include <type_traits>
+
+#include "rp_common.cuh"
+
+namespace rp {
+
+template <typename T>
+__device__ __forceinline__ T row_dot(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                     const T* __restrict__ vals, const T* __restrict__ x, int64_t i) {
+  const int s = __ldg(row_ptr + i), e = __ldg(row_ptr + i + 1);
+  T sum = T(0);
+  for (int j = s; j < e; ++j) sum = fma(__ldg(vals + j), __ldg(x + __ldg(col + j)), sum);
+  return sum;
+}
+
+// Row i of the matrix split into parts (Sec. 3): the part's local CSR (part-
+// local columns) plus its non-local CSR, whose compressed columns name the
+// halo rows -- on one GPU the halo exchange is this gather from x.
+template <typename T>
+__device__ __forceinline__ T row_dot_parts(const Parts<T>& P, const int32_t* __restrict__ row_ptr,
+                                           const int32_t* __restrict__ col, const T* __restrict__ vals,
+                                           const T* __restrict__ x, int64_t i) {
+  const int p = find_rank(P.row_off, P.n, i);
+  const int64_t r0 = __ldg(P.row_off + p), li = i - r0;
+  const int32_t* rp = row_ptr + r0 + p;
+  const int64_t no = __ldg(P.nnz_off + p);
+  T sum = T(0);
+  for (int j = __ldg(rp + li); j < __ldg(rp + li + 1); ++j)
+    sum = fma(__ldg(vals + no + j), __ldg(x + r0 + __ldg(col + no + j)), sum);
+  const int32_t* nrp = P.nl_row_ptr + r0 + p;
+  const int64_t nlo = __ldg(P.nl_off + p), nco = __ldg(P.nlcol_off + p);
+  for (int j = __ldg(nrp + li); j < __ldg(nrp + li + 1); ++j)
+    sum = fma(__ldg(P.nl_vals + nlo + j), __ldg(x + __ldg(P.nl_cols + nco + __ldg(P.nl_col + nlo + j))), sum);
+  return sum;
+}
+
+inline Parts<double> parts64(const rp_handle* h) {
+  return Parts<double>{h->n_parts, h->d_part_row_off, h->d_part_nnz_off, h->d_part_nl_off, h->d_part_nlcol_off,
+                       h->nl_row_ptr, h->nl_col_idx, h->nl_cols, h->nl_vals};
+}
+inline Parts<float> parts32(const rp_handle* h) {
+  return Parts<float>{h->n_parts, h->d_part_row_off, h->d_part_nnz_off, h->d_part_nl_off, h->d_part_nlcol_off,
+                      h->nl_row_ptr, h->nl_col_idx, h->nl_cols, h->nl_vals32};
+}
+
+template <typename T>
+__device__ __forceinline__ T row_dot_any(const Parts<T>& P, const int32_t* __restrict__ row_ptr,
+                                         const int32_t* __restrict__ col, const T* __restrict__ vals,
+                                         const T* __restrict__ x, int64_t i) {
+  return P.n > 1 ? row_dot_parts<T>(P, row_ptr, col, vals, x, i) : row_dot<T>(row_ptr, col, vals, x, i);
+}
+
+inline Sliced<double> sliced64(const rp_handle* h, const double* vals) {
+  if (h->sl_slices == 0 || vals != h->vals) return Sliced<double>{};  // e.g. transposed values
+  return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_ibuf, h->sl_vals, h->opts.spin_limit};
+}
+inline Sliced<float> sliced32(const rp_handle* h) {
+  if (h->sl_slices == 0 || !h->sl_vals32) return Sliced<float>{};
+  return Sliced<float>{h->sl_slices, h->sl_desc, h->sl_ibuf, h->sl_vals32, h->opts.spin_limit};
+}
+
+// 16-byte vectors of the streaming kernels
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int N = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int N = 2;
+};
+
+template <int E>
+__device__ __forceinline__ float& comp(float4& v) {
+  return E == 0 ? v.x : E == 1 ? v.y : E == 2 ? v.z : v.w;
+}
+template <int E>
+__device__ __forceinline__ double& comp(double2& v) {
+  return E == 0 ? v.x : v.y;
+}
+
+// apply f(element index e, element references...) to every component
+template <int W, typename F, int E = 0>
+__device__ __forceinline__ void for_each_comp(F&& f) {
+  if constexpr (E < W) {
+    f(std::integral_constant<int, E>{});
+    for_each_comp<W, F, E + 1>(static_cast<F&&>(f));
+  }
+}
+
+// ---- SpMV over the sliced layout, staged through shared memory by TMA bulk copies.
+//
+// A block is kChunk consumer warps plus one producer warp. The block owns
+// chunks of kChunk consecutive slices (consumer warp w takes slice w of the
+// chunk: rows 256 c + 32 w + lane, as the CSR body's thread 32 w + lane of
+// block c maps rows). The producer keeps up to kStages chunks in flight:
+// once consumers have released a stage (its "empty" mbarrier), it posts the
+// byte count on the stage's "full" mbarrier and issues three cp.async.bulk
+// copies -- the chunk's values, its offset tables + index words and its run
+// of slice descriptors. Bytes in flight cost no registers, and consumer
+// warps wait only on their own chunk's data, not on each other; a slice
+// then waits on one memory round trip, its gathers of p. Offset tables of
+// up to 32 entries are read with a warp shuffle (source lane = index byte,
+// taken modulo 32 by the shuffle), longer ones from shared memory; rows of
+// up to 8 entries run a body unrolled for their exact width. A chunk larger
+// than a stage (rows over 8 entries, long tables) is read straight from
+// global memory by the same warps. Every barrier wait is bounded: after
+// spin iterations the block waits (bounded) for its own copies and calls the
+// epilogue's timeout (which records RP_DEVICE_TIMEOUT and stops the solve).
+//
+// Epilogue (Epi): row(i, y_i) per computed row (per-thread accumulation),
+// timeout() by one thread of a block whose wait ran out, finish() by every
+// thread at the end (block reduction, last-block scalars).
+
+constexpr int kChunk = kThreads / 32;  // slices per chunk, one per consumer warp
+constexpr int kSlThreads = kThreads + 32;
+constexpr int kStageIdx = 3072;        // table + index word bytes a stage holds
+constexpr int kStageDesc = 128;        // descriptor run (kChunk + 1 entries, padded)
+
+// Stages per block: 3 for FP32 (34 KB), 2 for FP64 (38 KB; 3 would leave
+// room for only 3 blocks an SM).
+template <typename T>
+struct SlStage {
+  static constexpr int kStages = sizeof(T) == 4 ? 3 : 2;
+  static constexpr int kVals = kChunk * kSliceRows * 8 * (int)sizeof(T);  // rows of <= 8 entries
+  static constexpr int kBytes = kVals + kStageIdx + kStageDesc;
+  static constexpr int kSmem = kStages * kBytes;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int64_t limit) {
+  for (int64_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// global -> shared bulk copy completing on bar (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Offset of the entry whose index byte is byte e of wd. SHFL: tables of up to
+// 32 entries held one per lane in tv (warp-uniform choice, all lanes call).
+template <bool SHFL>
+__device__ __forceinline__ int slice_offset(uint32_t wd, int e, int32_t tv, const int32_t* tab) {
+  if (SHFL) return __shfl_sync(0xffffffffu, tv, (int)(wd >> (8 * e)));
+  return tab[(wd >> (8 * e)) & 255u];
+}
+
+// Sum of one row of a slice, L entries: values at v[32 k] (lane applied),
+// index words at iw[32 g]; the same fused multiply-adds in the same order as
+// row_dot over the row's CSR entries. Lanes without a row (valid false) run
+// the shuffles but load nothing.
+template <typename T, bool SHFL, int L>
+__device__ __forceinline__ T slice_row_exact(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab,
+                                             const T* x, bool valid) {
+  const uint32_t w0 = iw[0], w1 = L > 4 ? iw[kSliceRows] : 0u;
+  T vv[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) vv[k] = v[k * kSliceRows];
+  T sum = T(0);
+#pragma unroll
+  for (int k = 0; k < L; ++k) {
+    const int off = slice_offset<SHFL>(k < 4 ? w0 : w1, k & 3, tv, tab);
+    if (valid) sum = fma(vv[k], __ldg(x + off), sum);
+  }
+  return sum;
+}
+
+template <typename T, bool SHFL>
+__device__ __forceinline__ T slice_row(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab, const T* x,
+                                       bool valid, int L) {
+  switch (L) {
+    case 1: return slice_row_exact<T, SHFL, 1>(v, iw, tv, tab, x, valid);
+    case 2: return slice_row_exact<T, SHFL, 2>(v, iw, tv, tab, x, valid);
+    case 3: return slice_row_exact<T, SHFL, 3>(v, iw, tv, tab, x, valid);
+    case 4: return slice_row_exact<T, SHFL, 4>(v, iw, tv, tab, x, valid);
+    case 5: return slice_row_exact<T, SHFL, 5>(v, iw, tv, tab, x, valid);
+    case 6: return slice_row_exact<T, SHFL, 6>(v, iw, tv, tab, x, valid);
+    case 7: return slice_row_exact<T, SHFL, 7>(v, iw, tv, tab, x, valid);
+    case 8: return slice_row_exact<T, SHFL, 8>(v, iw, tv, tab, x, valid);
+    default: break;
+  }
+  T sum = T(0);
+  for (int g = 0; g < ((L + 3) >> 2); ++g) {
+    const uint32_t wd = iw[g * kSliceRows];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * g + e < L) {
+        const int off = slice_offset<SHFL>(wd, e, tv, tab);
+        if (valid) sum = fma(v[(4 * g + e) * kSliceRows], __ldg(x + off), sum);
+      }
+  }
+  return sum;
+}
+
+// One slice: descriptor pair (d0, d1), values v and table tab (shared or
+// global), gathers from x relative to the lane's row.
+template <typename T>
+__device__ __forceinline__ T slice_sum(uint2 d0, uint2 d1, const T* v, const int32_t* tab, const T* x, bool valid,
+                                       int lane) {
+  const int L = (int)((d1.x - d0.x) >> 5);
+  const int D = (int)(d1.y - d0.y) - kSliceRows * ((L + 3) >> 2);
+  const uint32_t* iw = reinterpret_cast<const uint32_t*>(tab + D) + lane;
+  if (D <= 32) {
+    // a slice holds >= 32 words of table + index words: lanes past D read one of them, unused
+    const int32_t tv = tab[lane];
+    return slice_row<T, true>(v, iw, tv, tab, x, valid, L);
+  }
+  return slice_row<T, false>(v, iw, 0, tab, x, valid, L);
+}
+
+template <typename T, class Epi>
+__device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, int64_t n64, const T* xin, T* yout, Epi& epi) {
+  using St = SlStage<T>;
+  constexpr int kStages = St::kStages;
+  extern __shared__ __align__(128) unsigned char sbuf[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ uint32_t chunk_x[kStages], chunk_y[kStages];
+  __shared__ int staged[kStages];
+  __shared__ int timed_out, issued;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int S = (int)sl.n_slices, n = (int)n64;
+  const int NC = (S + kChunk - 1) / kChunk, G = gridDim.x;
+  const uint2* desc = sl.desc;
+
+  if (tid == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kChunk);
+    }
+    timed_out = 0;
+    issued = 0;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (w == kChunk) {
+    // producer warp: one lane posts every chunk of this block
+    if (lane == 0) {
+      uint2 nd0 = make_uint2(0u, 0u), nd1 = nd0;
+      if ((int)blockIdx.x < NC) {
+        nd0 = __ldg(desc + blockIdx.x * kChunk);
+        nd1 = __ldg(desc + min((int)blockIdx.x * kChunk + kChunk, S));
+      }
+      int i = 0;
+      for (int ch = blockIdx.x; ch < NC; ch += G, ++i) {
+        const int st = i % kStages;
+        if (i >= kStages && !mbar_wait(&empty[st], (uint32_t)((i / kStages - 1) & 1), sl.spin)) {
+          atomicExch(&timed_out, 1);
+          break;
+        }
+        const uint2 d0 = nd0, d1 = nd1;
+        if (ch + G < NC) {  // bounds of the next chunk, loaded while this one is posted
+          nd0 = __ldg(desc + (ch + G) * kChunk);
+          nd1 = __ldg(desc + min((ch + G) * kChunk + kChunk, S));
+        }
+        unsigned char* base = sbuf + st * St::kBytes;
+        const uint32_t vb = (d1.x - d0.x) * (uint32_t)sizeof(T), ib = (d1.y - d0.y) * 4u;
+        const bool fit = vb <= (uint32_t)St::kVals && ib <= (uint32_t)kStageIdx;
+        chunk_x[st] = d0.x;
+        chunk_y[st] = d0.y;
+        staged[st] = fit;
+        // consumers' generic-proxy reads of this stage (released through
+        // empty[st]) before the async-proxy writes of the copy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (fit) {
+          const uint32_t db = 16u * (uint32_t)((kChunk + 2) / 2);  // kChunk + 1 descriptors, 16-byte multiple
+          mbar_expect_tx(&full[st], vb + ib + db);
+          bulk_g2s(base, sl.vals + d0.x, vb, &full[st]);
+          bulk_g2s(base + St::kVals, sl.ibuf + d0.y, ib, &full[st]);
+          bulk_g2s(base + St::kVals + kStageIdx, desc + (int64_t)ch * kChunk, db, &full[st]);
+        } else {
+          mbar_arrive(&full[st]);
+        }
+      }
+      issued = i;
+    }
+  } else {
+    int i = 0;
+    for (int ch = blockIdx.x; ch < NC; ch += G, ++i) {
+      const int st = i % kStages;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((i / kStages) & 1), sl.spin));
+      if (!ok) {
+        if (lane == 0) atomicExch(&timed_out, 1);
+        break;
+      }
+      const int s = ch * kChunk + w;
+      if (s < S) {
+        const int row = s * kSliceRows + lane;
+        const bool valid = row < n;
+        const T* x = xin + row;
+        const unsigned char* base = sbuf + st * St::kBytes;
+        T sum;
+        if (staged[st]) {
+          const uint2* sd = reinterpret_cast<const uint2*>(base + St::kVals + kStageIdx);
+          const uint2 d0 = sd[w], d1 = sd[w + 1];
+          sum = slice_sum<T>(d0, d1, reinterpret_cast<const T*>(base) + (d0.x - chunk_x[st]) + lane,
+                             reinterpret_cast<const int32_t*>(base + St::kVals) + (d0.y - chunk_y[st]), x, valid,
+                             lane);
+        } else {
+          const uint2 d0 = __ldg(desc + s), d1 = __ldg(desc + s + 1);
+          sum = slice_sum<T>(d0, d1, sl.vals + d0.x + lane, sl.ibuf + d0.y, x, valid, lane);
+        }
+        if (valid) {
+          yout[row] = sum;
+          epi.row(row, sum);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+  }
+  __syncthreads();
+  if (timed_out) {
+    // wait (bounded) for the copies this block may still have in flight, then report
+    if (tid == kChunk * 32) {
+      for (int j = issued - kStages; j < issued; ++j)
+        if (j >= 0) mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1), sl.spin);
+      epi.timeout();
+    }
+    __syncthreads();
+  }
+  epi.finish();
+}
+
+
+// y = A x over CSR (any number of parts), grid-stride over rows; rows map
+// to threads as in spmv_sl_body.
+template <typename T, class Epi>
+__device__ __forceinline__ void spmv_csr_body(int64_t n, const Parts<T>& parts, const int32_t* __restrict__ row_ptr,
+                                              const int32_t* __restrict__ col, const T* __restrict__ vals,
+                                              const T* xin, T* yout, Epi& epi) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T s = row_dot_any<T>(parts, row_ptr, col, vals, xin, i);
+    yout[i] = s;
+    epi.row(i, s);
+  }
+  epi.finish();
+}
+
+}  // namespace rp

@@ -342,9 +342,7 @@ def momentum_staging(mesh: BoxMesh, sigma: float = 0.5, seed: int = 100, u0: flo
     up = -(a + np.maximum(-F, 0.0))   # row = owner (low side), col = neighbour
     lo = -(a + np.maximum(F, 0.0))    # row = neighbour (high side), col = owner
     owner, nbr = _global_face_cells(mesh)
-    diag = np.full(n, ct, np.float64)
-    np.add.at(diag, owner, -up)
-    np.add.at(diag, nbr, -lo)
+    diag = ct + np.bincount(owner, weights=-up, minlength=n) + np.bincount(nbr, weights=-lo, minlength=n)
     ext = np.concatenate([diag, up, lo])
     parts = []
     for r in mesh.ranks:
@@ -353,8 +351,10 @@ def momentum_staging(mesh: BoxMesh, sigma: float = 0.5, seed: int = 100, u0: flo
         parts.append(n + nf + r.face_gid)
         if r.n_iface:
             row_g = r.cell_gid[r.iface_row]
-            col_g = np.concatenate([mesh.ranks[q].cell_gid[c:c + 1] for q, c in
-                                    zip(r.iface_nbr_rank, r.iface_nbr_col)])
+            col_g = np.empty(r.n_iface, np.int64)
+            for q in np.unique(r.iface_nbr_rank):
+                m = r.iface_nbr_rank == q
+                col_g[m] = mesh.ranks[q].cell_gid[r.iface_nbr_col[m]]
             low_side = row_g < col_g
             parts.append(np.where(low_side, n + r.iface_face_gid, n + nf + r.iface_face_gid))
     return ext[np.concatenate(parts)]
