@@ -270,10 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nv = a.n / W;
-  for (int64_t k = tid; k < nv; k += stride) {
-    V qv = reinterpret_cast<const V*>(a.q)[k];
-    V rv = reinterpret_cast<const V*>(a.r)[k];
-    V dv = reinterpret_cast<const V*>(a.dinv)[k];
+  auto step = [&](V& rv, V qv, V dv) {
     for_each_comp<W>([&](auto e) {
       constexpr int E = decltype(e)::value;
       T ri = fma(-alpha, comp<E>(qv), comp<E>(rv));
@@ -281,6 +278,23 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
       rz = fma(ri, comp<E>(dv) * ri, rz);
       rr = fma(ri, ri, rr);
     });
+  };
+  int64_t k = tid;
+  // two vectors of each stream in flight per thread
+  for (; k + stride < nv; k += 2 * stride) {
+    V q0 = reinterpret_cast<const V*>(a.q)[k], q1 = reinterpret_cast<const V*>(a.q)[k + stride];
+    V r0 = reinterpret_cast<const V*>(a.r)[k], r1 = reinterpret_cast<const V*>(a.r)[k + stride];
+    V d0 = reinterpret_cast<const V*>(a.dinv)[k], d1 = reinterpret_cast<const V*>(a.dinv)[k + stride];
+    step(r0, q0, d0);
+    step(r1, q1, d1);
+    reinterpret_cast<V*>(a.r)[k] = r0;
+    reinterpret_cast<V*>(a.r)[k + stride] = r1;
+  }
+  for (; k < nv; k += stride) {
+    V qv = reinterpret_cast<const V*>(a.q)[k];
+    V rv = reinterpret_cast<const V*>(a.r)[k];
+    V dv = reinterpret_cast<const V*>(a.dinv)[k];
+    step(rv, qv, dv);
     reinterpret_cast<V*>(a.r)[k] = rv;
   }
   for (int64_t i = nv * W + tid; i < a.n; i += stride) {
