@@ -312,6 +312,48 @@ def jacobi_inverse(row_ptr, col_idx, vals, diag_pos=None):
     return one / diag
 
 
+def _operator(prec):
+    """A preconditioner as z = prec(r): an array is the Jacobi inverse diagonal."""
+    if callable(prec):
+        return prec
+    return lambda r: prec * r
+
+
+def line_part(row_ptr, col_idx, vals, block=32):
+    """The line (block-tridiagonal) part M of a matrix: per row i its diagonal and
+    the couplings (i, i-1) and (i, i+1) that stay inside i's block of ``block``
+    consecutive rows (blocks start at multiples of ``block``). Returns
+    (sub, diag, sup): sub[i] = A[i, i-1] (0 at a block start), sup[i] = A[i, i+1]
+    (0 at a block end). On a line-ordered mesh (rows x-fastest, x-lines of
+    ``block`` cells) M is the x-line part of A: block-Jacobi over the lines."""
+    n = row_ptr.shape[0] - 1
+    row = np.repeat(np.arange(n), np.diff(row_ptr))
+    col = np.asarray(col_idx, np.int64)
+    sub = np.zeros(n, vals.dtype)
+    diag = np.zeros(n, vals.dtype)
+    sup = np.zeros(n, vals.dtype)
+    m = col == row
+    diag[row[m]] = vals[m]
+    m = (col == row - 1) & (row % block != 0)
+    sub[row[m]] = vals[m]
+    m = (col == row + 1) & (row % block != block - 1)
+    sup[row[m]] = vals[m]
+    return sub, diag, sup
+
+
+def line_operator(sub, diag, sup, dtype=np.float64):
+    """z = M^-1 r for M = tridiag(sub, diag, sup), by one banded LU solve
+    (scipy.linalg.solve_banded) in ``dtype``; the zero couplings at block
+    boundaries make it independent solves per block."""
+    import scipy.linalg as sla
+    n = diag.shape[0]
+    ab = np.zeros((3, n), dtype)
+    ab[0, 1:] = sup[:-1]
+    ab[1] = diag
+    ab[2, :-1] = sub[1:]
+    return lambda r: sla.solve_banded((1, 1), ab, np.asarray(r, dtype))
+
+
 def pcg(A, dinv, b, tol=1e-9, max_iter=10000, x0=None) -> SolveResult:
     """Preconditioned CG with z = D^-1 r.
 
@@ -319,7 +361,9 @@ def pcg(A, dinv, b, tol=1e-9, max_iter=10000, x0=None) -> SolveResult:
     alpha = (r.z)/(p.Ap), x += alpha p, r -= alpha Ap; stop when
     ||r|| <= tol ||b||, after confirming with the true residual b - A x (if
     that fails, r is replaced by it and the iteration restarts from p = z);
-    otherwise z = D^-1 r, beta = (r.z)_new/(r.z)_old, p = z + beta p."""
+    otherwise z = D^-1 r, beta = (r.z)_new/(r.z)_old, p = z + beta p.
+    ``dinv`` is the Jacobi inverse diagonal, or any preconditioner z = dinv(r)."""
+    prec = _operator(dinv)
     b = np.asarray(b, np.float64)
     bb = float(b @ b)
     if bb == 0.0:
@@ -333,7 +377,7 @@ def pcg(A, dinv, b, tol=1e-9, max_iter=10000, x0=None) -> SolveResult:
     restart = True
     while True:
         if restart:
-            z = dinv * r
+            z = prec(r)
             p = z.copy()
             rz = float(r @ z)
             restart = False
@@ -364,7 +408,7 @@ def pcg(A, dinv, b, tol=1e-9, max_iter=10000, x0=None) -> SolveResult:
             rr = trr
             restart = True
             continue
-        z = dinv * r
+        z = prec(r)
         rz_new = float(r @ z)
         beta = rz_new / rz
         p = z + beta * p
@@ -460,6 +504,7 @@ def pcg_fp32(A32, dinv32, rhs32, rel_tol=1e-5, max_iter=10000):
     in FP64 and alpha / beta are rounded to FP32 before use. Stops on the
     recursive residual ||r|| <= rel_tol ||rhs||. Returns (d, iterations,
     status)."""
+    prec = _operator(dinv32)
     f32 = np.float32
     x = np.zeros_like(rhs32)
     r = rhs32.copy()
@@ -467,7 +512,7 @@ def pcg_fp32(A32, dinv32, rhs32, rel_tol=1e-5, max_iter=10000):
     thresh = rel_tol * rel_tol * float(r64 @ r64)
     if thresh == 0.0:
         return x, 0, OK
-    z = dinv32 * r
+    z = prec(r)
     p = z.copy()
     rz = float(r64 @ z.astype(np.float64))
     it = 0
@@ -483,7 +528,7 @@ def pcg_fp32(A32, dinv32, rhs32, rel_tol=1e-5, max_iter=10000):
         r64 = r.astype(np.float64)
         if float(r64 @ r64) <= thresh:
             return x, it, OK
-        z = dinv32 * r
+        z = prec(r)
         rz_new = float(r64 @ z.astype(np.float64))
         beta = f32(rz_new / rz)
         p = z + beta * p
@@ -536,6 +581,7 @@ def mixed_reliable(A64, A_in, dinv_in, b, tol=1e-9, delta=1e-5, max_iter=20000, 
     convergence test ||r|| <= tol ||b|| is taken on it; otherwise r replaces
     the inner residual and the iteration CONTINUES with p = z + beta p,
     beta = (r.z)_new / (r.z)_old (no restart of the search direction)."""
+    prec = _operator(dinv_in)
     f = dtype
     b = np.asarray(b, np.float64)
     bb = float(b @ b)
@@ -553,7 +599,7 @@ def mixed_reliable(A64, A_in, dinv_in, b, tol=1e-9, delta=1e-5, max_iter=20000, 
         return max(delta * delta * start_rr, 0.25 * thresh)
 
     inner = phase_end(float(r64 @ r64))
-    z = dinv_in * r
+    z = prec(r)
     p = z.copy()
     rz = float(r64 @ z.astype(np.float64))
     d = np.zeros_like(r)
@@ -585,7 +631,7 @@ def mixed_reliable(A64, A_in, dinv_in, b, tol=1e-9, delta=1e-5, max_iter=20000, 
             r = res.astype(f)
             r64 = r.astype(np.float64)
             inner = phase_end(float(r64 @ r64))
-        z = dinv_in * r
+        z = prec(r)
         rz_new = float(r64 @ z.astype(np.float64))
         beta = f(rz_new / rz)
         p = z + beta * p
