@@ -81,6 +81,7 @@ def parse():
                     help="run only the batched form (default launch shape, no loop baseline): profiling runs")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--no-bicgstab", action="store_true", help="skip the non-symmetric (momentum) solve")
+    ap.add_argument("--no-line", action="store_true", help="skip the line-preconditioner measurement")
     ap.add_argument("--alpha-sweep", action="store_true",
                     help="repartitioning-ratio study at 128^3: GPU parts and CPU ranks merged")
     ap.add_argument("--host-loop", action="store_true",
@@ -512,6 +513,34 @@ def run_ours(args):
             "gpu_launches": sum(launches(prec, i) for i in infos),
         }
 
+    # the same steps with the line (block-tridiagonal, 32-row blocks) preconditioner
+    line = None
+    if not args.no_line and world == 1:
+        repart.set_solver_options(h, precond=repart.RP_PRECOND_LINE)
+        line = {"precond": "block-Jacobi over 32-row blocks (tridiagonal part): x-lines of the 256^3 ranks"}
+        ln_steps = max(1, min(args.steps, 5))
+        for prec in precs:
+            for t in range(2):
+                assert step(t, prec, stg_dev, b, x)["status"] == 0
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            infos = []
+            e0.record(stream)
+            for t in range(ln_steps):
+                infos.append(step(t, prec, stg_dev, b, x))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            line[prec] = {"ms_per_step": round(e0.elapsed_time(e1) / ln_steps, 3),
+                          "iterations_mean": statistics.mean(i["iterations"] for i in infos),
+                          "max_rel_residual": max(i["rel_residual"] for i in infos),
+                          "statuses": sorted({i["status"] for i in infos})}
+        for prec in ("fp64", "mixed"):
+            if prec in precs:
+                kk = [repart.profile_iteration(h, b, prec, iters=20) for _ in range(2)]
+                line[prec]["kernel_ms"] = {k2: round(v, 5) for k2, v in kk[-1].items()}
+        repart.set_solver_options(h, precond=repart.RP_PRECOND_JACOBI)
+        repart.update_values_packed(h, stg_dev[0])
+
     # kernel durations (CUDA events on the launching stream, same kernels as the graph runs)
     kern = {}
     for prec in precs:
@@ -665,7 +694,7 @@ def run_ours(args):
         "roofline_fp64_spmv": fp64_alu,
         "map_build_ms": round(build_ms, 1), "input_setup_s": round(setup_s, 1), "update_paths": update_paths,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": results[head]["gpu_launches"], "batched": batched,
-        "bicgstab": bicg,
+        "bicgstab": bicg, "line_precond": line,
         "clocks": clocks[head], "clocks_other": {o: clocks[o] for o in other},
     }
     return line

@@ -72,6 +72,14 @@ enum { RP_FP64 = 0, RP_MIXED = 1, RP_MIXED_RU = 2 };
  * distinct column offsets; else CSR. RP_LAYOUT_CSR: always CSR. Both give
  * the same products row by row (same entries, same order). */
 enum { RP_LAYOUT_AUTO = 0, RP_LAYOUT_CSR = 1 };
+/* Preconditioner of the PCG solves (rp_options.precond). RP_PRECOND_JACOBI:
+ * z = D^-1 r. RP_PRECOND_LINE: block-Jacobi over blocks of 32 consecutive
+ * rows (blocks start at multiples of 32) with each block's tridiagonal part:
+ * the diagonal and the couplings (i, i-1), (i, i+1) inside the block, solved
+ * exactly (LU factors built at every value update). On a line-ordered mesh
+ * (rows x-fastest, x-lines of 32 cells per rank) this is line-Jacobi along x.
+ * Needs n_parts = 1; the adjoint solve and BiCGStab keep Jacobi. */
+enum { RP_PRECOND_JACOBI = 0, RP_PRECOND_LINE = 1 };
 
 typedef struct rp_handle rp_handle;
 
@@ -112,17 +120,21 @@ typedef struct rp_options {
   int32_t layout;         /* RP_LAYOUT_AUTO or RP_LAYOUT_CSR                      */
   double ru_delta;        /* RP_MIXED_RU: residual reduction between two FP64
                              refinements (default 0.1; 0: use inner_tol)          */
+  int32_t precond;        /* RP_PRECOND_JACOBI or RP_PRECOND_LINE                 */
+  int32_t spare;          /* must be 0                                            */
 } rp_options;
 
 /* Replace the solver settings of a handle (max_iter, max_outer, max_restarts,
- * inner_tol, ru_delta, host_loop); structural fields are ignored. Takes
- * effect at the next solve. */
+ * inner_tol, ru_delta, host_loop, precond); structural fields are ignored.
+ * Takes effect at the next solve. Switching to RP_PRECOND_LINE builds its
+ * factors from the current values (blocks the host); RP_EUNSUPPORTED for
+ * n_parts > 1. */
 rp_status rp_set_solver_options(rp_handle* h, const rp_options* opts);
 
 /* Defaults: n_parts 1, general (non-symmetric) storage, FP32 copy on,
  * transpose off, max_iter 20000, max_outer 30, max_restarts 8, current
  * device, inner_tol 1e-5, spin_limit 1<<26, host_loop 0, layout
- * RP_LAYOUT_AUTO, ru_delta 0.1. */
+ * RP_LAYOUT_AUTO, ru_delta 0.1, precond RP_PRECOND_JACOBI. */
 void rp_default_options(rp_options* opts);
 
 /* Sec. 3 steps 1-3 and the three outputs (sparsity pattern, update pattern,

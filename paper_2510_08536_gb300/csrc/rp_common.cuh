@@ -130,9 +130,22 @@ constexpr int kSliceDescPad = 8;  // bulk copies of descriptor runs may read pas
 // fit on the SMs at once (by each kernel's register use), capped by the rows.
 struct IterGrid {
   int k1 = 1, k1s = 1, k2 = 1, k3 = 1;  // K1 on CSR, K1 on the sliced layout, K2, K3
+  int k2l = 1, k3l = 1;                 // K2, K3 with the line preconditioner
 };
 
 struct BsState;  // BiCGStab work space and graph (rp_bicgstab.cu)
+
+// Line (block-tridiagonal) preconditioner over 32-row blocks: per row the LU
+// factors of its block's tridiagonal part, l = a_i / u_{i-1}, w = 1 / u_i,
+// g = c_i / u_i (a, c: couplings to rows i-1, i+1 inside the block), and the
+// buffer z that receives M^-1 r. l == nullptr: Jacobi.
+template <typename T>
+struct Line {
+  const T* l;
+  const T* w;
+  const T* g;
+  T* z;
+};
 
 // Per-call pointers of the batched solve (read by the captured kernel).
 struct BatchIO {
@@ -247,6 +260,11 @@ struct rp_handle {
   rp::Graphs graphs;
   cudaStream_t capture_stream = nullptr;
 
+  // line preconditioner (precond == RP_PRECOND_LINE)
+  int precond = RP_PRECOND_JACOBI;
+  double *ln_l = nullptr, *ln_w = nullptr, *ln_g = nullptr, *ln_z = nullptr;
+  float *ln_l32 = nullptr, *ln_w32 = nullptr, *ln_g32 = nullptr, *ln_z32 = nullptr;
+
   // BiCGStab (non-symmetric systems), allocated on first use
   rp::BsState* bs = nullptr;
 
@@ -277,6 +295,8 @@ rp_status build_sliced(rp_handle* h, cudaStream_t s);  // after the CSR map
 rp_status fill_sliced(rp_handle* h, cudaStream_t s);   // after every value update
 void free_sliced(rp_handle* h);
 void free_bicgstab(rp_handle* h);
+rp_status line_factors(rp_handle* h, cudaStream_t s);  // after every value update (precond LINE)
+void free_line(rp_handle* h);
 rp_status build_graphs(rp_handle* h);
 void free_solver(rp_handle* h);
 void free_batch(rp_handle* h);

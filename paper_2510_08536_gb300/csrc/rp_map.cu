@@ -368,6 +368,11 @@ rp_status validate(const rp_ldu_desc* ranks, int32_t k, const rp_options& o) {
     return fail(RP_EINVAL, "invalid solver options");
   if (o.layout != RP_LAYOUT_AUTO && o.layout != RP_LAYOUT_CSR)
     return fail(RP_EINVAL, "layout must be RP_LAYOUT_AUTO or RP_LAYOUT_CSR");
+  if (o.precond != RP_PRECOND_JACOBI && o.precond != RP_PRECOND_LINE)
+    return fail(RP_EINVAL, "precond must be RP_PRECOND_JACOBI or RP_PRECOND_LINE");
+  if (o.spare != 0) return fail(RP_EINVAL, "spare must be 0");
+  if (o.precond == RP_PRECOND_LINE && o.n_parts != 1)
+    return fail(RP_EUNSUPPORTED, "the line preconditioner needs n_parts = 1");
   int64_t n = 0, nnz = 0, slots = 0;
   for (int r = 0; r < k; ++r) {
     const rp_ldu_desc& d = ranks[r];
@@ -470,6 +475,7 @@ static void free_handle_memory(rp_handle* h) {
   free_batch(h);
   free_sliced(h);
   free_bicgstab(h);
+  free_line(h);
 }
 
 extern "C" void rp_destroy(rp_handle* h) {
@@ -498,6 +504,7 @@ extern "C" rp_status rp_build_repartition(const rp_ldu_desc* ranks, int32_t k, c
   h->symmetric = o.symmetric != 0;
   h->want_fp32 = o.want_fp32 != 0;
   h->want_transpose = o.want_transpose != 0;
+  h->precond = o.precond;
   const int alpha = k / o.n_parts;
 
   // rank tables

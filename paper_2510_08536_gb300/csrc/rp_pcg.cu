@@ -41,6 +41,7 @@ struct IterArgs {
   int in_graph;  // 0: launched on a stream (kernel timing), no condition to set
   Parts<T> parts;
   Sliced<T> sl;  // K1 runs k_it_spmv_sl when built (n_slices > 0)
+  Line<T> line;  // line preconditioner (K2 writes z, K3 reads it); l == nullptr: Jacobi
 };
 
 struct ResArgs {
@@ -63,7 +64,71 @@ struct ResArgs {
   int in_graph;
   int ru;  // mixed: continued (not restarted) inner PCG across refinements
   Parts<double> parts;
+  Line<double> line;   // FP64 path, line preconditioner
+  Line<float> line32;  // mixed path, line preconditioner
 };
+
+// z = M^-1 r for the 32-row block this warp holds (lane j: row 32 s + j) of
+// the line preconditioner: forward substitution y_j = r_j - l_j y_{j-1}, then
+// back substitution z_j = w_j y_j - g_j z_{j+1}, each as a 5-step parallel
+// scan of affine maps over the warp (l = 0 at the block start, g = 0 at its
+// end). All 32 lanes must call it; lanes without a row pass zeros.
+template <typename T>
+__device__ __forceinline__ T line_solve(T r, T l, T w, T g, int lane) {
+  T m = -l, k = r;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T mp = __shfl_up_sync(0xffffffffu, m, d), kp = __shfl_up_sync(0xffffffffu, k, d);
+    if (lane >= d) {
+      k = fma(m, kp, k);
+      m *= mp;
+    }
+  }
+  T M = -g, K = w * k;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T Mn = __shfl_down_sync(0xffffffffu, M, d), Kn = __shfl_down_sync(0xffffffffu, K, d);
+    if (lane + d < 32) {
+      K = fma(M, Kn, K);
+      M *= Mn;
+    }
+  }
+  return K;
+}
+
+// LU factors of the line preconditioner, one thread per 32-row block
+// (Thomas algorithm in FP64 from the FP64 values; FP32 copies rounded to
+// nearest). Columns are sorted, so a row's in-block neighbours i-1 and i+1,
+// if stored, sit right before and after its diagonal entry.
+__global__ void __launch_bounds__(kThreads)
+    k_line_factors(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                   const double* __restrict__ vals, const int32_t* __restrict__ diag_pos, double* __restrict__ l,
+                   double* __restrict__ w, double* __restrict__ g, float* __restrict__ l32, float* __restrict__ w32,
+                   float* __restrict__ g32) {
+  const int64_t nb = (n + 31) / 32;
+  for (int64_t blk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; blk < nb; blk += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = blk * 32, i1 = i0 + 32 < n ? i0 + 32 : n;
+    double w_prev = 0.0, c_prev = 0.0;
+    for (int64_t i = i0; i < i1; ++i) {
+      const int dp = diag_pos[i], rs = row_ptr[i], re = row_ptr[i + 1];
+      const double a = (i > i0 && dp > rs && col[dp - 1] == i - 1) ? vals[dp - 1] : 0.0;
+      const double c = (i + 1 < i1 && dp + 1 < re && col[dp + 1] == i + 1) ? vals[dp + 1] : 0.0;
+      const double li = a * w_prev;             // a_i / u_{i-1}
+      const double wi = 1.0 / (vals[dp] - li * c_prev);  // 1 / u_i
+      const double gi = wi * c;
+      l[i] = li;
+      w[i] = wi;
+      g[i] = gi;
+      if (l32) {
+        l32[i] = (float)li;
+        w32[i] = (float)wi;
+        g32[i] = (float)gi;
+      }
+      w_prev = wi;
+      c_prev = c;
+    }
+  }
+}
 
 // K1: q = A p and (p, q); the last block forms alpha.
 // Per-thread partial sums are kept in T: the FP32 path does no per-element
@@ -255,8 +320,8 @@ void launch_k1(const IterArgs<T>& a, int grid, cudaStream_t s) {
   else k_it_spmv<T><<<grid, kThreads, 0, s>>>(a);
 }
 
-// K2: r -= alpha q; z = D^-1 r; (r, z), (r, r); stop test; beta.
-template <typename T>
+// K2: r -= alpha q; z = D^-1 r (LINE: z = M^-1 r, stored); (r, z), (r, r); stop test; beta.
+template <typename T, bool LINE>
 __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
   Ctl* c = a.ctl;
   if (c->stop) {
@@ -280,6 +345,29 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
     });
   };
   int64_t k = tid;
+  if constexpr (LINE) {
+    // one 32-row block per warp per step (rows as in the Jacobi loop)
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = tid - lane; base < a.n; base += stride) {
+      const int64_t i = base + lane;
+      const bool valid = i < a.n;
+      T ri = T(0), li = T(0), wi = T(0), gi = T(0);
+      if (valid) {
+        ri = fma(-alpha, a.q[i], a.r[i]);
+        li = a.line.l[i];
+        wi = a.line.w[i];
+        gi = a.line.g[i];
+      }
+      const T zi = line_solve<T>(ri, li, wi, gi, lane);
+      if (valid) {
+        a.r[i] = ri;
+        a.line.z[i] = zi;
+      }
+      rz = fma(ri, zi, rz);
+      rr = fma(ri, ri, rr);
+    }
+    k = nv;  // the Jacobi loops below do nothing
+  }
   // two vectors of each stream in flight per thread
   for (; k + stride < nv; k += 2 * stride) {
     V q0 = reinterpret_cast<const V*>(a.q)[k], q1 = reinterpret_cast<const V*>(a.q)[k + stride];
@@ -297,7 +385,7 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
     step(rv, qv, dv);
     reinterpret_cast<V*>(a.r)[k] = rv;
   }
-  for (int64_t i = nv * W + tid; i < a.n; i += stride) {
+  for (int64_t i = nv * W + tid; !LINE && i < a.n; i += stride) {
     T ri = fma(-alpha, a.q[i], a.r[i]);
     a.r[i] = ri;
     rz = fma(ri, a.dinv[i] * ri, rz);
@@ -324,8 +412,9 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
   }
 }
 
-// K3: x += alpha p; p = z + beta p (the latter only while iterating).
-template <typename T>
+// K3: x += alpha p; p = z + beta p (the latter only while iterating; z = D^-1 r,
+// or LINE: the z K2 stored).
+template <typename T, bool LINE>
 __global__ void __launch_bounds__(kThreads) k_it_xp(IterArgs<T> a) {
   Ctl* c = a.ctl;
   if (c->skip_x) return;
@@ -348,24 +437,33 @@ __global__ void __launch_bounds__(kThreads) k_it_xp(IterArgs<T> a) {
     });
     reinterpret_cast<V*>(x)[k] = xv;
     if (upd_p) {
-      V rv = reinterpret_cast<const V*>(a.r)[k];
-      V dv = reinterpret_cast<const V*>(a.dinv)[k];
-      for_each_comp<W>([&](auto e) {
-        constexpr int E = decltype(e)::value;
-        comp<E>(pv) = fma(beta, comp<E>(pv), comp<E>(dv) * comp<E>(rv));
-      });
+      if constexpr (LINE) {
+        V zv = reinterpret_cast<const V*>(a.line.z)[k];
+        for_each_comp<W>([&](auto e) {
+          constexpr int E = decltype(e)::value;
+          comp<E>(pv) = fma(beta, comp<E>(pv), comp<E>(zv));
+        });
+      } else {
+        V rv = reinterpret_cast<const V*>(a.r)[k];
+        V dv = reinterpret_cast<const V*>(a.dinv)[k];
+        for_each_comp<W>([&](auto e) {
+          constexpr int E = decltype(e)::value;
+          comp<E>(pv) = fma(beta, comp<E>(pv), comp<E>(dv) * comp<E>(rv));
+        });
+      }
       reinterpret_cast<V*>(a.p)[k] = pv;
     }
   }
   for (int64_t i = nv * W + tid; i < a.n; i += stride) {
     T pi = a.p[i];
     x[i] = fma(alpha, pi, x[i]);
-    if (upd_p) a.p[i] = fma(beta, pi, a.dinv[i] * a.r[i]);
+    if (upd_p) a.p[i] = fma(beta, pi, LINE ? a.line.z[i] : a.dinv[i] * a.r[i]);
   }
 }
 
 // Residual pass of the FP64 solve: r = b - A x (or r = b, x = 0 on a cold
-// start), p = z = D^-1 r, (r, z), (r, r) [, (b, b)]; decides the next step.
+// start), p = z = D^-1 r (LINE: M^-1 r), (r, z), (r, r) [, (b, b)]; decides the next step.
+template <bool LINE>
 __global__ void __launch_bounds__(kThreads) k_res64(ResArgs a) {
   Ctl* c = a.ctl;
   const bool cold = c->pass == 0 && c->x_zero;
@@ -373,18 +471,31 @@ __global__ void __launch_bounds__(kThreads) k_res64(ResArgs a) {
   const double* __restrict__ b = a.io->b;
   double* __restrict__ x = a.io->x;
   double rz = 0.0, rr = 0.0, bb = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double bi = b[i];
-    double ri;
-    if (cold) {
-      ri = bi;
-      x[i] = 0.0;
-    } else {
-      ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform loop over 32-row blocks (the line solve needs the whole warp)
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < a.n; base += stride) {
+    const int64_t i = base + lane;
+    const bool valid = i < a.n;
+    double bi = 0.0, ri = 0.0;
+    if (valid) {
+      bi = b[i];
+      if (cold) {
+        ri = bi;
+        x[i] = 0.0;
+      } else {
+        ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
+      }
+      a.r[i] = ri;
     }
-    a.r[i] = ri;
-    const double zi = a.dinv[i] * ri;
-    a.p[i] = zi;
+    double zi;
+    if constexpr (LINE) {
+      zi = line_solve<double>(ri, valid ? a.line.l[i] : 0.0, valid ? a.line.w[i] : 0.0, valid ? a.line.g[i] : 0.0,
+                              lane);
+    } else {
+      zi = valid ? a.dinv[i] * ri : 0.0;
+    }
+    if (valid) a.p[i] = zi;
     rz += ri * zi;
     rr += ri * ri;
     bb += bi * bi;
@@ -420,7 +531,9 @@ __global__ void __launch_bounds__(kThreads) k_res64(ResArgs a) {
 }
 
 // Residual pass of the mixed solve: r = b - A x in FP64 with FP64 values,
-// its FP32 copy as the inner right-hand side, d = 0, p = z = D32^-1 r32.
+// its FP32 copy as the inner right-hand side, d = 0, p = z = D32^-1 r32
+// (LINE: z = M32^-1 r32, also stored for the continued refinement).
+template <bool LINE>
 __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
   Ctl* c = a.ctl;
   const bool cold = c->pass == 0 && c->x_zero;
@@ -428,20 +541,36 @@ __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
   const double* __restrict__ b = a.io->b;
   double* __restrict__ x = a.io->x;
   double rz = 0.0, rr = 0.0, bb = 0.0, rr32 = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double bi = b[i];
-    double ri;
-    if (cold) {
-      ri = bi;
-      x[i] = 0.0;
-    } else {
-      ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform loop over 32-row blocks (the line solve needs the whole warp)
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < a.n; base += stride) {
+    const int64_t i = base + lane;
+    const bool valid = i < a.n;
+    double bi = 0.0, ri = 0.0;
+    if (valid) {
+      bi = b[i];
+      if (cold) {
+        ri = bi;
+        x[i] = 0.0;
+      } else {
+        ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
+      }
     }
     const float r32 = (float)ri;
-    a.r32[i] = r32;
-    a.d32[i] = 0.0f;
-    const float z32 = a.dinv32[i] * r32;
-    if (!a.ru || first) a.p32[i] = z32;  // continued refinement keeps p after the first pass
+    float z32;
+    if constexpr (LINE) {
+      z32 = line_solve<float>(r32, valid ? a.line32.l[i] : 0.0f, valid ? a.line32.w[i] : 0.0f,
+                              valid ? a.line32.g[i] : 0.0f, lane);
+      if (valid) a.line32.z[i] = z32;
+    } else {
+      z32 = valid ? a.dinv32[i] * r32 : 0.0f;
+    }
+    if (valid) {
+      a.r32[i] = r32;
+      a.d32[i] = 0.0f;
+      if (!a.ru || first) a.p32[i] = z32;  // continued refinement keeps p after the first pass
+    }
     rz += (double)r32 * (double)z32;
     rr32 += (double)r32 * (double)r32;
     rr += ri * ri;
@@ -505,14 +634,17 @@ struct RuArgs {
   const float* r32;
   float* p32;
   Ctl* c;
+  const float* z32;  // LINE: M32^-1 r32 stored by the residual pass
 };
 
-// continued refinement: p = D32^-1 r32 + beta p after the residual was replaced
+// continued refinement: p = D32^-1 r32 + beta p (LINE: z32 + beta p) after the
+// residual was replaced
+template <bool LINE>
 __global__ void __launch_bounds__(kThreads) k_ru_p(RuArgs a) {
   if (!a.c->ru_apply) return;
   const float beta = (float)a.c->beta_ru;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
-    a.p32[i] = fmaf(beta, a.p32[i], a.dinv32[i] * a.r32[i]);
+    a.p32[i] = fmaf(beta, a.p32[i], LINE ? a.z32[i] : a.dinv32[i] * a.r32[i]);
 }
 
 // x += d (FP64) after an inner FP32 solve.
@@ -600,21 +732,28 @@ struct GraphGuard {
   }
 };
 
-// while (outer) { residual pass; [p = z + beta p]; while (inner) { K1; K2; K3 }; [x += d] }
-// mode: 0 FP64, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG
-rp_status build_solve_graph(rp_handle* h, int mode, const double* vals, const double* dinv,
-                            cudaGraphExec_t* exec) {
-  const bool mixed = mode != 0;
-  GraphGuard top;
-  RP_TRY_CUDA(cudaGraphCreate(&top.g, 0));
-  cudaGraphConditionalHandle hout, hin;
-  RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hout, top.g, 1, cudaGraphCondAssignDefault));
-  cudaGraphNode_t wout, nres, win, n1, n2, n3, ncor;
-  cudaGraph_t obody, ibody;
-  RP_TRY(add_while(top.g, &wout, nullptr, hout, &obody));
-  RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hin, obody, 0, 0));
+// Arguments and kernels of one solve (graph, host loop and kernel timing use
+// the same set): residual pass, continued-refinement step, iteration kernels
+// of both precisions and the correction, with the Jacobi or line variants.
+struct SolveSet {
+  bool line;
+  ResArgs ra;
+  RuArgs ru;
+  IterArgs<double> a64;
+  IterArgs<float> a32;
+  CorrectArgs ca;
+  void *res, *rup, *k2_64, *k3_64, *k2_32, *k3_32;
+  int g2_64, g3_64, g2_32, g3_32;
+};
 
-  ResArgs ra{};
+SolveSet solve_set(rp_handle* h, int mode, const double* vals, const double* dinv, cudaGraphConditionalHandle hin,
+                   cudaGraphConditionalHandle hout, int in_graph) {
+  SolveSet k{};
+  const bool mixed = mode != 0;
+  k.line = h->precond == RP_PRECOND_LINE && vals == h->vals && h->ln_l != nullptr;
+  const Line<double> l64 = k.line ? Line<double>{h->ln_l, h->ln_w, h->ln_g, h->ln_z} : Line<double>{};
+  const Line<float> l32 = k.line ? Line<float>{h->ln_l32, h->ln_w32, h->ln_g32, h->ln_z32} : Line<float>{};
+  ResArgs& ra = k.ra;
   ra.n = h->n;
   ra.row_ptr = h->row_ptr;
   ra.col = h->col_idx;
@@ -631,33 +770,82 @@ rp_status build_solve_graph(rp_handle* h, int mode, const double* vals, const do
   ra.partials = h->partials;
   ra.inner = hin;
   ra.outer = hout;
-  ra.in_graph = 1;
+  ra.in_graph = in_graph;
   ra.ru = mode == 2;
   ra.parts = parts64(h);
-  RP_TRY(add_kernel(obody, &nres, nullptr, mixed ? (void*)k_res_mixed : (void*)k_res64, h->grid, &ra));
+  ra.line = l64;
+  ra.line32 = l32;
+  k.ru = RuArgs{h->n, h->dinv32, h->r32, h->p32, h->ctl, h->ln_z32};
+  k.a64 = IterArgs<double>{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
+                           h->ctl, h->io, h->partials, hin, in_graph, parts64(h), sliced64(h, vals), l64};
+  k.a32 = IterArgs<float>{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
+                          h->ctl, h->io, h->partials, hin, in_graph, parts32(h), sliced32(h), l32};
+  k.ca = CorrectArgs{h->n, h->d32, h->ctl, h->io};
+  if (k.line) {
+    k.res = mixed ? (void*)k_res_mixed<true> : (void*)k_res64<true>;
+    k.rup = (void*)k_ru_p<true>;
+    k.k2_64 = (void*)k_it_resid<double, true>;
+    k.k3_64 = (void*)k_it_xp<double, true>;
+    k.k2_32 = (void*)k_it_resid<float, true>;
+    k.k3_32 = (void*)k_it_xp<float, true>;
+    k.g2_64 = h->igrid64.k2l;
+    k.g3_64 = h->igrid64.k3l;
+    k.g2_32 = h->igrid32.k2l;
+    k.g3_32 = h->igrid32.k3l;
+  } else {
+    k.res = mixed ? (void*)k_res_mixed<false> : (void*)k_res64<false>;
+    k.rup = (void*)k_ru_p<false>;
+    k.k2_64 = (void*)k_it_resid<double, false>;
+    k.k3_64 = (void*)k_it_xp<double, false>;
+    k.k2_32 = (void*)k_it_resid<float, false>;
+    k.k3_32 = (void*)k_it_xp<float, false>;
+    k.g2_64 = h->igrid64.k2;
+    k.g3_64 = h->igrid64.k3;
+    k.g2_32 = h->igrid32.k2;
+    k.g3_32 = h->igrid32.k3;
+  }
+  return k;
+}
+
+rp_status launch1(void* fn, int grid, int threads, int smem, void* argp, cudaStream_t s) {
+  void* args[1] = {argp};
+  RP_TRY_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)threads), args, (size_t)smem, s));
+  return RP_OK;
+}
+
+// while (outer) { residual pass; [p = z + beta p]; while (inner) { K1; K2; K3 }; [x += d] }
+// mode: 0 FP64, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG
+rp_status build_solve_graph(rp_handle* h, int mode, const double* vals, const double* dinv,
+                            cudaGraphExec_t* exec) {
+  const bool mixed = mode != 0;
+  GraphGuard top;
+  RP_TRY_CUDA(cudaGraphCreate(&top.g, 0));
+  cudaGraphConditionalHandle hout, hin;
+  RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hout, top.g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNode_t wout, nres, win, n1, n2, n3, ncor;
+  cudaGraph_t obody, ibody;
+  RP_TRY(add_while(top.g, &wout, nullptr, hout, &obody));
+  RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hin, obody, 0, 0));
+
+  SolveSet k = solve_set(h, mode, vals, dinv, hin, hout, 1);
+  RP_TRY(add_kernel(obody, &nres, nullptr, k.res, h->grid, &k.ra));
   cudaGraphNode_t before_inner = nres, nru;
   if (mode == 2) {
-    RuArgs ru{h->n, h->dinv32, h->r32, h->p32, h->ctl};
-    RP_TRY(add_kernel(obody, &nru, &nres, (void*)k_ru_p, h->grid, &ru));
+    RP_TRY(add_kernel(obody, &nru, &nres, k.rup, h->grid, &k.ru));
     before_inner = nru;
   }
   RP_TRY(add_while(obody, &win, &before_inner, hin, &ibody));
   if (mixed) {
-    IterArgs<float> ia{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
-                       h->ctl, h->io, h->partials, hin, 1, parts32(h), sliced32(h)};
-    const IterGrid& gr = h->igrid32;
-    RP_TRY(add_kernel(ibody, &n1, nullptr, k1_kernel(ia), k1_grid(ia, gr), &ia, k1_smem(ia), k1_threads(ia)));
-    RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<float>, gr.k2, &ia));
-    RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<float>, gr.k3, &ia));
-    CorrectArgs ca{h->n, h->d32, h->ctl, h->io};
-    RP_TRY(add_kernel(obody, &ncor, &win, (void*)k_correct, h->grid, &ca));
+    IterArgs<float>& ia = k.a32;
+    RP_TRY(add_kernel(ibody, &n1, nullptr, k1_kernel(ia), k1_grid(ia, h->igrid32), &ia, k1_smem(ia), k1_threads(ia)));
+    RP_TRY(add_kernel(ibody, &n2, &n1, k.k2_32, k.g2_32, &ia));
+    RP_TRY(add_kernel(ibody, &n3, &n2, k.k3_32, k.g3_32, &ia));
+    RP_TRY(add_kernel(obody, &ncor, &win, (void*)k_correct, h->grid, &k.ca));
   } else {
-    IterArgs<double> ia{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
-                        h->ctl, h->io, h->partials, hin, 1, parts64(h), sliced64(h, vals)};
-    const IterGrid& gr = h->igrid64;
-    RP_TRY(add_kernel(ibody, &n1, nullptr, k1_kernel(ia), k1_grid(ia, gr), &ia, k1_smem(ia), k1_threads(ia)));
-    RP_TRY(add_kernel(ibody, &n2, &n1, (void*)k_it_resid<double>, gr.k2, &ia));
-    RP_TRY(add_kernel(ibody, &n3, &n2, (void*)k_it_xp<double>, gr.k3, &ia));
+    IterArgs<double>& ia = k.a64;
+    RP_TRY(add_kernel(ibody, &n1, nullptr, k1_kernel(ia), k1_grid(ia, h->igrid64), &ia, k1_smem(ia), k1_threads(ia)));
+    RP_TRY(add_kernel(ibody, &n2, &n1, k.k2_64, k.g2_64, &ia));
+    RP_TRY(add_kernel(ibody, &n3, &n2, k.k3_64, k.g3_64, &ia));
   }
   RP_TRY_CUDA(cudaGraphInstantiate(exec, top.g, 0));
   return RP_OK;
@@ -703,16 +891,52 @@ IterGrid iter_grid(const rp_handle* h) {
   IterGrid gr;
   gr.k1 = g(resident((const void*)k_it_spmv<T>));
   gr.k1s = g(resident(sl, SlStage<T>::kSmem, kSlThreads));
-  gr.k2 = g(resident((const void*)k_it_resid<T>));
-  gr.k3 = g(resident((const void*)k_it_xp<T>));
+  gr.k2 = g(resident((const void*)k_it_resid<T, false>));
+  gr.k3 = g(resident((const void*)k_it_xp<T, false>));
+  gr.k2l = g(resident((const void*)k_it_resid<T, true>));
+  gr.k3l = g(resident((const void*)k_it_xp<T, true>));
   return gr;
 }
 
 }  // namespace
 
+rp_status ensure_line_buffers(rp_handle* h) {
+  const int64_t n = h->n + 64;
+  RP_TRY(dalloc(&h->ln_l, n));
+  RP_TRY(dalloc(&h->ln_w, n));
+  RP_TRY(dalloc(&h->ln_g, n));
+  RP_TRY(dalloc(&h->ln_z, n));
+  if (h->want_fp32) {
+    RP_TRY(dalloc(&h->ln_l32, n));
+    RP_TRY(dalloc(&h->ln_w32, n));
+    RP_TRY(dalloc(&h->ln_g32, n));
+    RP_TRY(dalloc(&h->ln_z32, n));
+  }
+  return RP_OK;
+}
+
+rp_status line_factors(rp_handle* h, cudaStream_t s) {
+  if (h->precond != RP_PRECOND_LINE || h->n == 0) return RP_OK;
+  RP_TRY(ensure_line_buffers(h));
+  const int g = grid_for(h, (h->n + 31) / 32);
+  k_line_factors<<<g, kThreads, 0, s>>>(h->n, h->row_ptr, h->col_idx, h->vals, h->diag_pos, h->ln_l, h->ln_w,
+                                        h->ln_g, h->ln_l32, h->ln_w32, h->ln_g32);
+  RP_TRY_CUDA(cudaGetLastError());
+  return RP_OK;
+}
+
+void free_line(rp_handle* h) {
+  void* ptrs[] = {h->ln_l, h->ln_w, h->ln_g, h->ln_z, h->ln_l32, h->ln_w32, h->ln_g32, h->ln_z32};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h->ln_l = h->ln_w = h->ln_g = h->ln_z = nullptr;
+  h->ln_l32 = h->ln_w32 = h->ln_g32 = h->ln_z32 = nullptr;
+}
+
 rp_status ensure_solver_buffers(rp_handle* h) {
   h->igrid64 = iter_grid<double>(h);
   h->igrid32 = iter_grid<float>(h);
+  if (h->precond == RP_PRECOND_LINE) RP_TRY(ensure_line_buffers(h));
   const int64_t n = h->n + 64;
   RP_TRY(dalloc(&h->r, n));
   RP_TRY(dalloc(&h->p, n));
@@ -779,30 +1003,7 @@ rp_status read_info(rp_handle* h, rp_solve_info* info, cudaStream_t s) {
 // control block is read back after every residual pass and every iteration.
 rp_status host_loop_solve(rp_handle* h, int mode, const double* vals, const double* dinv, cudaStream_t s) {
   const bool mixed = mode != 0;
-  ResArgs ra{};
-  ra.ru = mode == 2;
-  RuArgs ru{h->n, h->dinv32, h->r32, h->p32, h->ctl};
-  ra.n = h->n;
-  ra.row_ptr = h->row_ptr;
-  ra.col = h->col_idx;
-  ra.vals = vals;
-  ra.dinv = dinv;
-  ra.r = h->r;
-  ra.p = h->p;
-  ra.dinv32 = h->dinv32;
-  ra.r32 = h->r32;
-  ra.p32 = h->p32;
-  ra.d32 = h->d32;
-  ra.ctl = h->ctl;
-  ra.io = h->io;
-  ra.partials = h->partials;
-  ra.in_graph = 0;
-  ra.parts = parts64(h);
-  IterArgs<double> a64{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
-                       h->ctl, h->io, h->partials, 0, 0, parts64(h), sliced64(h, vals)};
-  IterArgs<float> a32{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
-                      h->ctl, h->io, h->partials, 0, 0, parts32(h), sliced32(h)};
-  CorrectArgs ca{h->n, h->d32, h->ctl, h->io};
+  SolveSet k = solve_set(h, mode, vals, dinv, 0, 0, 0);
   Ctl c;
   auto read = [&]() -> rp_status {
     RP_TRY_CUDA(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -811,26 +1012,24 @@ rp_status host_loop_solve(rp_handle* h, int mode, const double* vals, const doub
   };
   // same bounds as the graph: passes and iterations are capped on the device
   for (;;) {
-    if (mixed) k_res_mixed<<<h->grid, kThreads, 0, s>>>(ra);
-    else k_res64<<<h->grid, kThreads, 0, s>>>(ra);
-    if (mode == 2) k_ru_p<<<h->grid, kThreads, 0, s>>>(ru);
-    RP_TRY_CUDA(cudaGetLastError());
+    RP_TRY(launch1(k.res, h->grid, kThreads, 0, &k.ra, s));
+    if (mode == 2) RP_TRY(launch1(k.rup, h->grid, kThreads, 0, &k.ru, s));
     RP_TRY(read());
     const bool go = !c.stop;
     while (!c.stop) {
       if (mixed) {
-        launch_k1(a32, k1_grid(a32, h->igrid32), s);
-        k_it_resid<float><<<h->igrid32.k2, kThreads, 0, s>>>(a32);
-        k_it_xp<float><<<h->igrid32.k3, kThreads, 0, s>>>(a32);
+        launch_k1(k.a32, k1_grid(k.a32, h->igrid32), s);
+        RP_TRY(launch1(k.k2_32, k.g2_32, kThreads, 0, &k.a32, s));
+        RP_TRY(launch1(k.k3_32, k.g3_32, kThreads, 0, &k.a32, s));
       } else {
-        launch_k1(a64, k1_grid(a64, h->igrid64), s);
-        k_it_resid<double><<<h->igrid64.k2, kThreads, 0, s>>>(a64);
-        k_it_xp<double><<<h->igrid64.k3, kThreads, 0, s>>>(a64);
+        launch_k1(k.a64, k1_grid(k.a64, h->igrid64), s);
+        RP_TRY(launch1(k.k2_64, k.g2_64, kThreads, 0, &k.a64, s));
+        RP_TRY(launch1(k.k3_64, k.g3_64, kThreads, 0, &k.a64, s));
       }
       RP_TRY_CUDA(cudaGetLastError());
       RP_TRY(read());
     }
-    if (mixed) k_correct<<<h->grid, kThreads, 0, s>>>(ca);
+    if (mixed) RP_TRY(launch1((void*)k_correct, h->grid, kThreads, 0, &k.ca, s));
     if (!go) break;
   }
   RP_TRY_CUDA(cudaGetLastError());
@@ -901,6 +1100,21 @@ extern "C" rp_status rp_set_solver_options(rp_handle* h, const rp_options* o) {
   h->opts.inner_tol = o->inner_tol;
   h->opts.ru_delta = o->ru_delta;
   h->opts.host_loop = o->host_loop;
+  if (o->precond != RP_PRECOND_JACOBI && o->precond != RP_PRECOND_LINE)
+    return fail(RP_EINVAL, "precond must be RP_PRECOND_JACOBI or RP_PRECOND_LINE");
+  if (o->precond == RP_PRECOND_LINE && h->n_parts != 1)
+    return fail(RP_EUNSUPPORTED, "the line preconditioner needs n_parts = 1");
+  if (o->precond != h->precond) {
+    h->precond = o->precond;
+    h->opts.precond = o->precond;
+    for (cudaGraphExec_t* g : {&h->graphs.fp64, &h->graphs.mixed, &h->graphs.mixed_ru})
+      if (*g) {
+        cudaGraphExecDestroy(*g);
+        *g = nullptr;
+      }
+    RP_TRY(line_factors(h, 0));  // from the current values
+    RP_TRY_CUDA(cudaStreamSynchronize(0));
+  }
   if (h->batch_ready) {  // the batched kernel's arguments are part of its graphs
     h->batch_args.max_iter = o->max_iter;
     h->batch_args.max_outer = o->max_outer;
@@ -962,26 +1176,8 @@ extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t
   RP_TRY(dalloc(&h->x_host_stage, h->n + 64));
   // a fresh CG run from x = 0 that never meets its tolerance (tol = 0)
   k_setup<<<1, 1, 0, s>>>(h->ctl, h->io, b, h->x_host_stage, 0.0, 0.0, 1, iters + 2, 0, 1);
-  ResArgs ra{};
-  ra.n = h->n;
-  ra.row_ptr = h->row_ptr;
-  ra.col = h->col_idx;
-  ra.vals = h->vals;
-  ra.dinv = h->dinv;
-  ra.r = h->r;
-  ra.p = h->p;
-  ra.dinv32 = h->dinv32;
-  ra.r32 = h->r32;
-  ra.p32 = h->p32;
-  ra.d32 = h->d32;
-  ra.ctl = h->ctl;
-  ra.io = h->io;
-  ra.partials = h->partials;
-  ra.in_graph = 0;
-  ra.parts = parts64(h);
-  if (mixed) k_res_mixed<<<h->grid, kThreads, 0, s>>>(ra);
-  else k_res64<<<h->grid, kThreads, 0, s>>>(ra);
-  RP_TRY_CUDA(cudaGetLastError());
+  SolveSet k = solve_set(h, mixed ? 1 : 0, h->vals, h->dinv, 0, 0, 0);
+  RP_TRY(launch1(k.res, h->grid, kThreads, 0, &k.ra, s));
   std::vector<cudaEvent_t> ev(3 * iters + 1, nullptr);
   struct EvFree {
     std::vector<cudaEvent_t>& v;
@@ -991,20 +1187,16 @@ extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t
     }
   } evfree{ev};
   for (auto& e : ev) RP_TRY_CUDA(cudaEventCreate(&e));
-  IterArgs<double> a64{h->n, h->row_ptr, h->col_idx, h->vals, h->dinv, h->r, h->p, h->q, nullptr,
-                       h->ctl, h->io, h->partials, 0, 0, parts64(h), sliced64(h, h->vals)};
-  IterArgs<float> a32{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
-                      h->ctl, h->io, h->partials, 0, 0, parts32(h), sliced32(h)};
   RP_TRY_CUDA(cudaEventRecord(ev[0], s));
   for (int it = 0; it < iters; ++it) {
-    if (mixed) launch_k1(a32, k1_grid(a32, h->igrid32), s);
-    else launch_k1(a64, k1_grid(a64, h->igrid64), s);
+    if (mixed) launch_k1(k.a32, k1_grid(k.a32, h->igrid32), s);
+    else launch_k1(k.a64, k1_grid(k.a64, h->igrid64), s);
     RP_TRY_CUDA(cudaEventRecord(ev[3 * it + 1], s));
-    if (mixed) k_it_resid<float><<<h->igrid32.k2, kThreads, 0, s>>>(a32);
-    else k_it_resid<double><<<h->igrid64.k2, kThreads, 0, s>>>(a64);
+    if (mixed) RP_TRY(launch1(k.k2_32, k.g2_32, kThreads, 0, &k.a32, s));
+    else RP_TRY(launch1(k.k2_64, k.g2_64, kThreads, 0, &k.a64, s));
     RP_TRY_CUDA(cudaEventRecord(ev[3 * it + 2], s));
-    if (mixed) k_it_xp<float><<<h->igrid32.k3, kThreads, 0, s>>>(a32);
-    else k_it_xp<double><<<h->igrid64.k3, kThreads, 0, s>>>(a64);
+    if (mixed) RP_TRY(launch1(k.k3_32, k.g3_32, kThreads, 0, &k.a32, s));
+    else RP_TRY(launch1(k.k3_64, k.g3_64, kThreads, 0, &k.a64, s));
     RP_TRY_CUDA(cudaEventRecord(ev[3 * it + 3], s));
   }
   RP_TRY_CUDA(cudaGetLastError());

@@ -87,6 +87,7 @@ static rp_status permute_all(rp_handle* h, const double* buf, cudaStream_t s) {
                                                            nullptr);
   }
   RP_TRY_CUDA(cudaGetLastError());
+  RP_TRY(line_factors(h, s));
   return fill_sliced(h, s);
 }
 

@@ -23,6 +23,7 @@ RP_NOT_CONVERGED, RP_BREAKDOWN, RP_DEVICE_TIMEOUT, RP_EUNSUPPORTED = 7, 8, 9, 10
 RP_MEM_DEVICE, RP_MEM_HOST, RP_MEM_HOST_DIRECT = 0, 1, 2
 RP_FP64, RP_MIXED, RP_MIXED_RU = 0, 1, 2
 RP_LAYOUT_AUTO, RP_LAYOUT_CSR = 0, 1
+RP_PRECOND_JACOBI, RP_PRECOND_LINE = 0, 1
 PRECISIONS = {"fp64": RP_FP64, "mixed": RP_MIXED, "mixed_ru": RP_MIXED_RU}
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -41,7 +42,8 @@ class Options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("spin_limit", ctypes.c_int64),
-                ("host_loop", ctypes.c_int32), ("layout", ctypes.c_int32), ("ru_delta", ctypes.c_double)]
+                ("host_loop", ctypes.c_int32), ("layout", ctypes.c_int32), ("ru_delta", ctypes.c_double),
+                ("precond", ctypes.c_int32), ("spare", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):

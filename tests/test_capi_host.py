@@ -118,3 +118,12 @@ def test_batch_rejects_coupled_systems(lib):
     assert e.value.status == repart.RP_EINVAL
     assert b"interface" in lib.rp_last_error()
     assert lib.rp_batch_set_config(None, 8, 256) == repart.RP_EINVAL
+
+
+def test_rejects_bad_solver_choices(lib):
+    assert _status(_ranks(), layout=2) == repart.RP_EINVAL
+    assert _status(_ranks(), precond=2) == repart.RP_EINVAL
+    assert _status(_ranks(), spare=1) == repart.RP_EINVAL
+    assert _status(_ranks(), n_parts=2, precond=repart.RP_PRECOND_LINE) == repart.RP_EUNSUPPORTED
+    o = repart.default_options()
+    assert o.precond == repart.RP_PRECOND_JACOBI and o.layout == repart.RP_LAYOUT_AUTO and o.spare == 0
