@@ -36,9 +36,9 @@ sys.path.insert(0, ROOT)
 METRIC = "update+PCG ms/time-step at 256^3 cells, FP64 vs mixed; SpMV HBM GB/s vs peak"
 # DRAM bytes per launch from ncu captures of the same kernels on the 192^3 case, scaled to
 # a 256^3 launch by the ratio of algorithmic bytes (one pass per array): sliced FP32 SpMV
-# 313.8 MB of 319.7 MB algorithmic, sliced FP64 567.9 MB of 573.9 MB, CSR FP32 477.4 MB of
+# 314.0 MB of 319.7 MB algorithmic, sliced FP64 567.9 MB of 573.9 MB, CSR FP32 477.4 MB of
 # 479.5 MB. Remove an entry when its kernel changes, until it is captured again.
-PROFILED_TRAFFIC = {("mixed_256", "k_it_spmv_sl<float>"): 756.3e6,
+PROFILED_TRAFFIC = {("mixed_256", "k_it_spmv_sl<float>"): 756.9e6,
                     ("mixed_256", "k_it_spmv_sl<double>"): 1359.0e6,
                     ("mixed_256", "k_it_spmv<float>"): 1132.7e6}
 # FP64 FMA issue rate of a GB300 SM (2 per clock; 152 SMs x 2 x 2 flop x 2.07 GHz =

@@ -126,11 +126,13 @@ constexpr int kSlThreads = kThreads + 32;
 constexpr int kStageIdx = 3072;        // table + index word bytes a stage holds
 constexpr int kStageDesc = 128;        // descriptor run (kChunk + 1 entries, padded)
 
-// Stages per block: 3 for FP32 (34 KB), 2 for FP64 (38 KB; 3 would leave
-// room for only 3 blocks an SM).
+// Two stages per block (FP32 23 KB, FP64 39 KB): warps beat depth -- at
+// 256^3 the FP32 SpMV takes 0.138 ms with 2 stages (7 blocks of 9 warps an
+// SM, register-limited), 0.145 ms with 3 (6 blocks, shared-memory-limited),
+// 0.171 ms with 4.
 template <typename T>
 struct SlStage {
-  static constexpr int kStages = sizeof(T) == 4 ? 3 : 2;
+  static constexpr int kStages = 2;
   static constexpr int kVals = kChunk * kSliceRows * 8 * (int)sizeof(T);  // rows of <= 8 entries
   static constexpr int kBytes = kVals + kStageIdx + kStageDesc;
   static constexpr int kSmem = kStages * kBytes;
