@@ -112,7 +112,10 @@ typedef struct rp_options {
   int32_t max_restarts;   /* residual-replacement restarts allowed per solve      */
   int32_t device;         /* CUDA device ordinal (-1: current device)             */
   double inner_tol;       /* relative tolerance of the FP32 inner solve           */
-  int64_t spin_limit;     /* iteration limit of every device-side wait            */
+  int64_t spin_limit;     /* probe limit of every device-side wait; a wait that
+                             runs out ends the solve with RP_DEVICE_TIMEOUT after
+                             its block's own copies have landed (0: every wait
+                             gives up at once -- tests the timeout path)         */
   int32_t host_loop;      /* 1: rp_solve launches the same kernels from the host,
                              reading the control block after every iteration
                              (slow; for profilers that cannot look inside
@@ -125,7 +128,7 @@ typedef struct rp_options {
 } rp_options;
 
 /* Replace the solver settings of a handle (max_iter, max_outer, max_restarts,
- * inner_tol, ru_delta, host_loop, precond); structural fields are ignored.
+ * inner_tol, ru_delta, host_loop, precond, spin_limit); structural fields are ignored.
  * Takes effect at the next solve. Switching to RP_PRECOND_LINE builds its
  * factors from the current values (blocks the host); RP_EUNSUPPORTED for
  * n_parts > 1. */

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_bs_res(BsArgs a) {
     bool go = false;
     if (tot[0] <= c->thresh) {
       c->status = RP_OK;
-    } else if (c->status == RP_BREAKDOWN) {
+    } else if (c->status == RP_BREAKDOWN || c->status == RP_DEVICE_TIMEOUT) {
     } else if (!isfinite(tot[0])) {
       c->status = RP_BREAKDOWN;
     } else if (c->iter >= c->max_iter || (!first && c->restarts >= c->max_restarts)) {
@@ -451,6 +451,13 @@ rp_status bs_host_loop(rp_handle* h, cudaStream_t s) {
 }
 
 }  // namespace
+
+void drop_bicgstab_graph(rp_handle* h) {
+  if (h->bs && h->bs->graph) {
+    cudaGraphExecDestroy(h->bs->graph);
+    h->bs->graph = nullptr;
+  }
+}
 
 void free_bicgstab(rp_handle* h) {
   BsState* b = h->bs;

@@ -125,6 +125,10 @@ struct Sliced {
   int64_t spin;      // iteration limit of every shared-memory barrier wait
 };
 constexpr int kSliceDescPad = 8;  // bulk copies of descriptor runs may read past the end
+// Probe bound of the wait for a block's own bulk copies after another wait
+// ran out: copies land within microseconds, so it is met unless the GPU
+// itself stalls, and it keeps the drain bounded whatever spin_limit is.
+constexpr int64_t kDrainProbes = int64_t(1) << 22;
 
 // Grids of the three PCG iteration kernels of one precision: blocks that
 // fit on the SMs at once (by each kernel's register use), capped by the rows.
@@ -295,6 +299,7 @@ rp_status build_sliced(rp_handle* h, cudaStream_t s);  // after the CSR map
 rp_status fill_sliced(rp_handle* h, cudaStream_t s);   // after every value update
 void free_sliced(rp_handle* h);
 void free_bicgstab(rp_handle* h);
+void drop_bicgstab_graph(rp_handle* h);  // after a change of captured arguments
 rp_status line_factors(rp_handle* h, cudaStream_t s);  // after every value update (precond LINE)
 void free_line(rp_handle* h);
 rp_status build_graphs(rp_handle* h);

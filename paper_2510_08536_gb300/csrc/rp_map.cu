@@ -364,7 +364,7 @@ rp_status validate(const rp_ldu_desc* ranks, int32_t k, const rp_options& o) {
   if (!ranks || k < 1) return fail(RP_EINVAL, "need k >= 1 rank descriptors");
   if (o.n_parts < 1 || k % o.n_parts) return fail(RP_EINVAL, "n_parts=%d must divide k=%d", o.n_parts, k);
   if (o.max_iter < 0 || o.max_outer < 0 || o.max_restarts < 0 || !(o.inner_tol > 0.0) ||
-      o.spin_limit < 1 || !(o.ru_delta >= 0.0 && o.ru_delta < 1.0))
+      o.spin_limit < 0 || !(o.ru_delta >= 0.0 && o.ru_delta < 1.0))
     return fail(RP_EINVAL, "invalid solver options");
   if (o.layout != RP_LAYOUT_AUTO && o.layout != RP_LAYOUT_CSR)
     return fail(RP_EINVAL, "layout must be RP_LAYOUT_AUTO or RP_LAYOUT_CSR");

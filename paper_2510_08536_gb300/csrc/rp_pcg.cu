@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
     // wait (bounded) for the copies this block may still have in flight, then stop the solve
     if (tid == kChunk * 32) {
       for (int j = issued - kStages; j < issued; ++j)
-        if (j >= 0) mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1), a.sl.spin);
+        if (j >= 0) mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1), kDrainProbes);
       c->status = RP_DEVICE_TIMEOUT;
       c->stop = 1;
       c->skip_x = 1;
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) k_res64(ResArgs a) {
     bool go = false;
     if (tot[1] <= c->thresh) {
       c->status = RP_OK;
-    } else if (c->status == RP_BREAKDOWN) {
+    } else if (c->status == RP_BREAKDOWN || c->status == RP_DEVICE_TIMEOUT) {
     } else if (!isfinite(tot[1])) {
       c->status = RP_BREAKDOWN;
     } else if (c->iter_total >= c->max_iter || (!first && c->restarts >= c->max_restarts)) {
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
     bool go = false;
     if (tot[1] <= c->thresh) {
       c->status = RP_OK;
-    } else if (c->status == RP_BREAKDOWN) {
+    } else if (c->status == RP_BREAKDOWN || c->status == RP_DEVICE_TIMEOUT) {
     } else if (!isfinite(tot[1])) {
       c->status = RP_BREAKDOWN;
     } else if (c->outer >= c->max_outer) {
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_ru_p(RuArgs a) {
 
 // x += d (FP64) after an inner FP32 solve.
 __global__ void __launch_bounds__(kThreads) k_correct(CorrectArgs a) {
-  if (a.c->skip_correct || a.c->status == RP_BREAKDOWN) return;
+  if (a.c->skip_correct || a.c->status == RP_BREAKDOWN || a.c->status == RP_DEVICE_TIMEOUT) return;
   double* __restrict__ x = a.io->x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] += (double)a.d[i];
@@ -1092,28 +1092,33 @@ extern "C" rp_status rp_solve(rp_handle* h, const double* b, double* x, double t
 extern "C" rp_status rp_set_solver_options(rp_handle* h, const rp_options* o) {
   if (!h || !o) return fail(RP_EINVAL, "null argument");
   if (o->max_iter < 0 || o->max_outer < 0 || o->max_restarts < 0 || !(o->inner_tol > 0.0) ||
-      !(o->ru_delta >= 0.0 && o->ru_delta < 1.0))
+      !(o->ru_delta >= 0.0 && o->ru_delta < 1.0) || o->spin_limit < 0)
     return fail(RP_EINVAL, "invalid solver options");
+  if (o->precond != RP_PRECOND_JACOBI && o->precond != RP_PRECOND_LINE)
+    return fail(RP_EINVAL, "precond must be RP_PRECOND_JACOBI or RP_PRECOND_LINE");
+  if (o->precond == RP_PRECOND_LINE && h->n_parts != 1)
+    return fail(RP_EUNSUPPORTED, "the line preconditioner needs n_parts = 1");
   h->opts.max_iter = o->max_iter;
   h->opts.max_outer = o->max_outer;
   h->opts.max_restarts = o->max_restarts;
   h->opts.inner_tol = o->inner_tol;
   h->opts.ru_delta = o->ru_delta;
   h->opts.host_loop = o->host_loop;
-  if (o->precond != RP_PRECOND_JACOBI && o->precond != RP_PRECOND_LINE)
-    return fail(RP_EINVAL, "precond must be RP_PRECOND_JACOBI or RP_PRECOND_LINE");
-  if (o->precond == RP_PRECOND_LINE && h->n_parts != 1)
-    return fail(RP_EUNSUPPORTED, "the line preconditioner needs n_parts = 1");
-  if (o->precond != h->precond) {
+  const bool new_precond = o->precond != h->precond, new_spin = o->spin_limit != h->opts.spin_limit;
+  if (new_precond || new_spin) {  // both are part of the captured kernel arguments
     h->precond = o->precond;
     h->opts.precond = o->precond;
-    for (cudaGraphExec_t* g : {&h->graphs.fp64, &h->graphs.mixed, &h->graphs.mixed_ru})
+    h->opts.spin_limit = o->spin_limit;
+    for (cudaGraphExec_t* g : {&h->graphs.fp64, &h->graphs.mixed, &h->graphs.mixed_ru, &h->graphs.adjoint})
       if (*g) {
         cudaGraphExecDestroy(*g);
         *g = nullptr;
       }
-    RP_TRY(line_factors(h, 0));  // from the current values
-    RP_TRY_CUDA(cudaStreamSynchronize(0));
+    drop_bicgstab_graph(h);
+    if (new_precond) {
+      RP_TRY(line_factors(h, 0));  // from the current values
+      RP_TRY_CUDA(cudaStreamSynchronize(0));
+    }
   }
   if (h->batch_ready) {  // the batched kernel's arguments are part of its graphs
     h->batch_args.max_iter = o->max_iter;

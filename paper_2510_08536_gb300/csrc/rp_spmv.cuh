@@ -352,7 +352,7 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, int64_t n64, co
     // wait (bounded) for the copies this block may still have in flight, then report
     if (tid == kChunk * 32) {
       for (int j = issued - kStages; j < issued; ++j)
-        if (j >= 0) mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1), sl.spin);
+        if (j >= 0) mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1), kDrainProbes);
       epi.timeout();
     }
     __syncthreads();

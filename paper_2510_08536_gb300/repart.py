@@ -334,7 +334,7 @@ def batch_update_solve(h: Handle, buffer, b, x, tol: float = 1e-9, precision: st
 
 def set_solver_options(h: Handle, **kw):
     """rp_set_solver_options: change max_iter / max_outer / max_restarts /
-    inner_tol / ru_delta / host_loop of an existing handle."""
+    inner_tol / ru_delta / host_loop / precond / spin_limit of an existing handle."""
     o = h.options if getattr(h, "options", None) is not None else default_options()
     for key, val in kw.items():
         setattr(o, key, val)
