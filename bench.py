@@ -513,6 +513,20 @@ def run_ours(args):
             "gpu_launches": sum(launches(prec, i) for i in infos),
         }
 
+    # error of each mixed result against the FP64 result of the same system (the FP64 path
+    # is checked against the oracle in the tests; the oracle's own 256^3 solve takes minutes)
+    repart.update_values_packed(h, stg_dev[0])
+    sols = {}
+    for prec in precs:
+        xx = torch.zeros(n, dtype=torch.float64, device=dev)
+        repart.solve(h, b, xx, tol=1e-9, precision=prec)
+        sols[prec] = xx
+    if "fp64" in sols:
+        ref_norm = float(torch.linalg.norm(sols["fp64"]))
+        for prec in precs:
+            results[prec]["rel_error_vs_fp64"] = float(torch.linalg.norm(sols[prec] - sols["fp64"])) / ref_norm
+    del sols
+
     # the same steps with the line (block-tridiagonal, 32-row blocks) preconditioner
     line = None
     if not args.no_line and world == 1:
