@@ -423,6 +423,21 @@ def run_alpha_sweep(args, dev):
 # ---------------------------------------------------------------- ours
 
 
+def replica_ms_per_step(ms_local, steps, device=None):
+    """Whole-job ms per time step of N independent replicas: each rank timed `steps`
+    steps in ms_local; the job took the slowest rank's time (max over ranks) for
+    N * steps steps. Works over any initialised process group (NCCL on the GPUs,
+    gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local / steps, ms_local
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max / (steps * dist.get_world_size()), ms_max
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -496,15 +511,10 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         clocks[prec] = sampler.stop()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms_step, ms = replica_ms_per_step(e0.elapsed_time(e1), args.steps, dev)
         bad = [i for i in infos if i["status"] != 0]
         results[prec] = {
-            "ms_per_step": ms / (args.steps * world),
+            "ms_per_step": ms_step,
             "ms_per_step_per_replica": ms / args.steps,
             "iterations_mean": statistics.mean(i["iterations"] for i in infos),
             "outer_mean": statistics.mean(i["outer_iterations"] for i in infos),
@@ -646,13 +656,8 @@ def run_ours(args):
             assert info["status"] == 0, info
         e1.record(stream)
         barrier()
-        ems = e0.elapsed_time(e1)
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([ems], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
-        e2e = {"value": round(ems / (args.steps * world), 3), "unit": "ms/time-step",
+        ems_step, _ = replica_ms_per_step(e0.elapsed_time(e1), args.steps, dev)
+        e2e = {"value": round(ems_step, 3), "unit": "ms/time-step",
                "h2d_bytes_per_step": 8 * n_slots + 8 * n, "d2h_bytes_per_step": 8 * n,
                "path": "rp_update_values_packed + rp_solve with pinned host buffers"}
         del stg_pin
