@@ -36,10 +36,10 @@ sys.path.insert(0, ROOT)
 METRIC = "update+PCG ms/time-step at 256^3 cells, FP64 vs mixed; SpMV HBM GB/s vs peak"
 # DRAM bytes per launch from ncu captures of the same kernels on the 192^3 case, scaled to
 # a 256^3 launch by the ratio of algorithmic bytes (one pass per array): sliced FP32 SpMV
-# 314.0 MB of 319.7 MB algorithmic, sliced FP64 567.9 MB of 573.9 MB, CSR FP32 477.4 MB of
+# 278.2 MB of 285.2 MB algorithmic, sliced FP64 533.2 MB of 539.4 MB, CSR FP32 477.4 MB of
 # 479.5 MB. Remove an entry when its kernel changes, until it is captured again.
-PROFILED_TRAFFIC = {("mixed_256", "k_it_spmv_sl<float>"): 756.9e6,
-                    ("mixed_256", "k_it_spmv_sl<double>"): 1359.0e6,
+PROFILED_TRAFFIC = {("mixed_256", "k_it_spmv_sl<float>"): 659.8e6,
+                    ("mixed_256", "k_it_spmv_sl<double>"): 1264.5e6,
                     ("mixed_256", "k_it_spmv<float>"): 1132.7e6}
 # FP64 FMA issue rate of a GB300 SM (2 per clock; 152 SMs x 2 x 2 flop x 2.07 GHz =
 # 1.26 TFLOP/s, the nominal 1.25): the FP64 path is bound by it, not by HBM.
@@ -584,9 +584,9 @@ def run_ours(args):
 
     def spmv_bytes(prec):
         w = 8 if prec == "fp64" else 4
-        if sliced:  # values + offset tables and index words + slice descriptors + p read + q write
-            slices, entries, ibuf_len = sliced
-            return w * entries + 4 * ibuf_len + 8 * (slices + 1) + 2 * w * n
+        if sliced:  # values + index words + table references + tables + slice descriptors + p read + q write
+            slices, entries, ibuf_len, tabs_len = sliced
+            return w * entries + 4 * ibuf_len + 4 * slices + 4 * tabs_len + 8 * (slices + 1) + 2 * w * n
         return (w + 4) * nnz + 4 * (n + 1) + 2 * w * n
 
     def gbs(bytes_, ms):
@@ -701,7 +701,7 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "headline": head,
                    "n_rows": n, "nnz": nnz, "draws_cycled": draws, "l2": "inputs larger than L2, no flush",
                    "layout": ({"kind": "sliced", "slices": sliced[0], "padded_entries": sliced[1],
-                               "table_and_index_words": sliced[2]} if sliced else {"kind": "csr"}),
+                               "index_words": sliced[2], "table_words": sliced[3]} if sliced else {"kind": "csr"}),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "fp64_ms_per_step": round(results["fp64"]["ms_per_step"], 3) if "fp64" in results else None,
         "mixed_ms_per_step": round(results["mixed"]["ms_per_step"], 3) if "mixed" in results else None,

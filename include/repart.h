@@ -224,19 +224,24 @@ rp_status rp_spmv_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_
  * once next to the CSR map by rp_build_repartition and refilled from the CSR
  * values by every value update). Rows in slices of 32 (n_slices = ceil(n/32),
  * 0 when the layout is not in use), one row per lane. Slice s: desc[2s] = x_s,
- * desc[2s+1] = y_s (uint32 pairs, desc[2 n_slices], desc[2 n_slices + 1]
+ * desc[2s+1] = y_s (uint32 pairs; desc[2 n_slices], desc[2 n_slices + 1]
  * close the last slice); L_s = (x_{s+1} - x_s) / 32 entries per row, the
  * longest row of the slice, shorter rows padded with zero values; values of
  * entry k of lane j at vals[x_s + 32 k + j] (vals32 alike, NULL without
- * want_fp32); ibuf[y_s ...] holds D_s int32 column offsets (col - row, padded
- * with zeros to a multiple of 8), then ceil(L_s / 4) uint32 words per lane
- * (word g of lane j at 32 g + j) whose byte e is the offset index of entry
- * 4 g + e. pos[x_s + 32 k + j] is the CSR position of that entry, -1 for
- * padding. Entry k of a row is its k-th CSR entry. Device views, owned by
- * the handle; n_entries counts padded entries, ibuf_len int32 words. */
+ * want_fp32). tinfo[s] = t | w4 << 31: the slice's table of distinct column
+ * offsets (col - row, first-appearance order over entry k, then lane) is
+ * tabs[t .. t + D), D = tabs[t - 1] (equal tables are stored once); w4 = 1
+ * (D <= 16): 4-bit offset indices, entry 8 g + e of lane j in bits 4e..4e+3
+ * of ibuf[y_s + 32 g + j]; w4 = 0: 8-bit indices, entry 4 g + e in byte e of
+ * ibuf[y_s + 32 g + j]. pos[x_s + 32 k + j] is the CSR position of that entry,
+ * -1 for padding. Entry k of a row is its k-th CSR entry. Device views, owned
+ * by the handle; n_entries counts padded entries, ibuf_len index words,
+ * tabs_len table words. */
 typedef struct rp_sliced_view {
-  int64_t n_slices, n_entries, ibuf_len;
+  int64_t n_slices, n_entries, ibuf_len, tabs_len;
   const uint32_t* desc;
+  const uint32_t* tinfo;
+  const int32_t* tabs;
   const int32_t* ibuf;
   const int32_t* pos;
   const double* vals;

@@ -105,21 +105,27 @@ struct Parts {
 // Sliced layout of the merged matrix (one part): rows in slices of 32, one
 // row per lane. Slice s keeps its values column-major at vals[x_s + 32 k +
 // lane] (k < L_s, the longest row of the slice; shorter rows are padded with
-// zeros) and, at ibuf[y_s ...], a table of D_s distinct column offsets
-// col - row (padded to a multiple of 8) followed by ceil(L_s / 4) words per
-// lane of 8-bit table indices (word g of lane j at 32 g + j, entry 4 g + e in
-// byte e). desc[s] = (x_s, y_s), desc[n_slices] closes the last slice, so
-// L_s = (x_{s+1} - x_s) / 32 and D_s = y_{s+1} - y_s - 32 ceil(L_s / 4).
-// Entries keep the CSR order of their row, so a row's products are summed
-// exactly as over the CSR arrays.
+// zeros) and, instead of column indices, per entry a 4- or 8-bit index into a
+// table of the slice's distinct column offsets col - row. Distinct tables are
+// stored once in tabs ([D, offset_0 .. offset_{D-1}] each, 32 spare words at
+// the end); tinfo[s] = t_s | w4 << 31 names the slice's table (tabs[t_s - 1]
+// = D_s) and its index width: w4 = 1 (D_s <= 16) packs 8 indices a word
+// (entry 8 g + e in bits 4e..4e+3 of word g), else 4 (entry 4 g + e in byte
+// e). The index words of lane j are at ibuf[y_s + 32 g + j]. desc[s] =
+// (x_s, y_s), desc[n_slices] closes the last slice, so L_s = (x_{s+1} - x_s)
+// / 32. Entries keep the CSR order of their row, so a row's products are
+// summed exactly as over the CSR arrays.
 constexpr int kSliceRows = 32;
 constexpr int kSliceMaxDict = 256;   // 8-bit indices
 constexpr int kSliceMaxWidth = 32;   // longest row the layout takes
+constexpr uint32_t kSliceW4 = 0x80000000u;  // tinfo flag: 4-bit indices
 
 template <typename T>
 struct Sliced {
   int64_t n_slices;  // 0: not built (CSR only)
   const uint2* desc; // n_slices + 1 entries, then kSliceDescPad zero entries
+  const uint32_t* tinfo;  // n_slices entries, then kSliceDescPad
+  const int32_t* tabs;
   const int32_t* ibuf;
   const T* vals;
   int64_t spin;      // iteration limit of every shared-memory barrier wait
@@ -242,8 +248,11 @@ struct rp_handle {
   // sliced layout (n_parts == 1, built when every slice fits; see Sliced)
   int64_t sl_slices = 0;     // 0: the iteration runs on the CSR arrays
   int64_t sl_entries = 0;    // padded entries (32 per slice and width unit)
-  int64_t sl_ibuf_len = 0;   // int32 words of tables and index words
+  int64_t sl_ibuf_len = 0;   // index words
+  int64_t sl_tabs_len = 0;   // int32 words of the distinct tables
   uint2* sl_desc = nullptr;  // [sl_slices + 1]
+  uint32_t* sl_tinfo = nullptr;  // [sl_slices]
+  int32_t* sl_tabs = nullptr;
   int32_t* sl_ibuf = nullptr;
   int32_t* sl_pos = nullptr;  // CSR position of each padded entry, -1 = padding
   double* sl_vals = nullptr;

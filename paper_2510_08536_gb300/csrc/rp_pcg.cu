@@ -237,10 +237,11 @@ __global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (fit) {
           const uint32_t db = 16u * (uint32_t)((kChunk + 2) / 2);  // kChunk + 1 descriptors, 16-byte multiple
-          mbar_expect_tx(&full[st], vb + ib + db);
+          mbar_expect_tx(&full[st], vb + ib + db + kStageInfo);
           bulk_g2s(base, a.sl.vals + d0.x, vb, &full[st]);
           bulk_g2s(base + St::kVals, a.sl.ibuf + d0.y, ib, &full[st]);
           bulk_g2s(base + St::kVals + kStageIdx, desc + (int64_t)ch * kChunk, db, &full[st]);
+          bulk_g2s(base + St::kVals + kStageIdx + kStageDesc, a.sl.tinfo + (int64_t)ch * kChunk, kStageInfo, &full[st]);
         } else {
           mbar_arrive(&full[st]);
         }
@@ -265,13 +266,15 @@ __global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
         T sum;
         if (staged[st]) {
           const uint2* sd = reinterpret_cast<const uint2*>(base + St::kVals + kStageIdx);
+          const uint32_t* si = reinterpret_cast<const uint32_t*>(base + St::kVals + kStageIdx + kStageDesc);
           const uint2 d0 = sd[w], d1 = sd[w + 1];
-          sum = slice_sum<T>(d0, d1, reinterpret_cast<const T*>(base) + (d0.x - chunk_x[st]) + lane,
-                             reinterpret_cast<const int32_t*>(base + St::kVals) + (d0.y - chunk_y[st]), x, valid,
-                             lane);
+          sum = slice_sum<T>(d0, d1, si[w], reinterpret_cast<const T*>(base) + (d0.x - chunk_x[st]) + lane,
+                             reinterpret_cast<const uint32_t*>(base + St::kVals) + (d0.y - chunk_y[st]) + lane,
+                             a.sl.tabs, x, valid, lane);
         } else {
           const uint2 d0 = __ldg(desc + s), d1 = __ldg(desc + s + 1);
-          sum = slice_sum<T>(d0, d1, a.sl.vals + d0.x + lane, a.sl.ibuf + d0.y, x, valid, lane);
+          sum = slice_sum<T>(d0, d1, __ldg(a.sl.tinfo + s), a.sl.vals + d0.x + lane,
+                             reinterpret_cast<const uint32_t*>(a.sl.ibuf + d0.y) + lane, a.sl.tabs, x, valid, lane);
         }
         if (valid) {
           a.q[row] = sum;
@@ -296,7 +299,6 @@ __global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
   }
   pcg_k1_finish<T>(a.ctl, a.partials, acc);
 }
-
 
 template <typename T>
 void* k1_kernel(const IterArgs<T>& a) {

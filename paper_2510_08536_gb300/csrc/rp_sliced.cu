@@ -5,20 +5,26 @@
 // update, residual passes, adjoint and gradients use them). For the
 // iteration the same entries are re-laid in slices of 32 rows, one row per
 // lane, values column-major inside the slice, and every column index is
-// replaced by an 8-bit index into a per-slice table of column offsets
-// col - row. Finite-volume rows touch a handful of neighbours at a few
-// distinct offsets, so a slice's table is short (9-13 entries on a
-// decomposed box mesh) and an entry costs 4 + 1 bytes in FP32 (8 + 1 in
-// FP64) instead of 4 + 4 (8 + 4) plus the row pointer: the SpMV, which
-// bounds every PCG iteration, moves ~35% fewer bytes in FP32.
+// replaced by a 4- or 8-bit index into a table of the slice's distinct
+// column offsets col - row. Finite-volume rows touch a handful of
+// neighbours at a few distinct offsets (9-13 per slice on a decomposed box
+// mesh), and slices repeat the same few tables, so distinct tables are kept
+// once and a slice with at most 16 offsets packs 8 indices a word: an entry
+// costs 4 + 1/2 bytes in FP32 (8 + 1/2 in FP64) instead of 4 + 4 (8 + 4)
+// plus the row pointer -- the SpMV, which bounds every PCG iteration, moves
+// ~40% fewer bytes in FP32.
 //
-// Built once, next to the CSR map, on the device: one warp per slice finds
-// the distinct offsets of its rows in first-appearance order (entry k, then
-// lane), a host scan sizes the slices, a second warp pass writes tables,
-// index words and the CSR position of every padded entry. The layout is not
-// built (the iteration keeps the CSR kernels) when a row has more than 32
-// entries or a slice more than 256 distinct offsets.
+// Built once, next to the CSR map: one warp per slice finds the distinct
+// offsets of its rows in first-appearance order (entry k, then lane) and its
+// longest row; a second warp pass writes the tables to a scratch array; the
+// host removes duplicate tables and sizes the slices; a third warp pass
+// writes index words and the CSR position of every padded entry. The layout
+// is not built (the iteration keeps the CSR kernels) when a row has more than
+// 32 entries or a slice more than 256 distinct offsets.
+#include <cstring>
 #include <memory>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "rp_common.cuh"
@@ -78,7 +84,7 @@ __device__ int slice_table(const int32_t* __restrict__ row_ptr, const int32_t* _
   return cnt;
 }
 
-// pass 1: width L_s and padded table length of every slice; err bit 1: a
+// pass 1: width L_s and table length D_s of every slice; err bit 1: a
 // row longer than kSliceMaxWidth, bit 2: a table longer than kSliceMaxDict
 __global__ void __launch_bounds__(kThreads)
     k_slice_count(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n, int64_t S,
@@ -100,28 +106,47 @@ __global__ void __launch_bounds__(kThreads)
     }
     if (lane == 0) {
       width[s] = (uint8_t)L;
-      tlen[s] = (uint16_t)((D + 7) & ~7);
+      tlen[s] = (uint16_t)D;
     }
   }
 }
 
-// pass 2: tables, index words and CSR positions; err bit 4: a table length
-// differs from pass 1 (cannot happen: both passes are deterministic)
+// pass 2: every slice's table into the scratch array at toff[s]
+__global__ void __launch_bounds__(kThreads)
+    k_slice_tables(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n, int64_t S,
+                   const uint8_t* __restrict__ width, const int64_t* __restrict__ toff, int32_t* __restrict__ tab) {
+  __shared__ int32_t sdict[kWarpsPerBlock][kSliceMaxDict];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + w; s < S; s += (int64_t)gridDim.x * kWarpsPerBlock) {
+    const int D = slice_table(row_ptr, col, n, s, width[s], sdict[w], [](int, bool, int, int) {});
+    __syncwarp();
+    for (int j = lane; j < D; j += 32) tab[toff[s] + j] = sdict[w][j];
+  }
+}
+
+// pass 3: index words (4- or 8-bit as tinfo says) and CSR positions; err
+// bit 4: a slice's size differs from the earlier passes (cannot happen: all
+// passes are deterministic)
 __global__ void __launch_bounds__(kThreads)
     k_slice_fill(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n, int64_t S,
-                 const uint2* __restrict__ desc, int32_t* __restrict__ ibuf, int32_t* __restrict__ pos,
-                 int32_t* err) {
+                 const uint2* __restrict__ desc, const uint32_t* __restrict__ tinfo, int32_t* __restrict__ ibuf,
+                 int32_t* __restrict__ pos, int32_t* err) {
   __shared__ int32_t sdict[kWarpsPerBlock][kSliceMaxDict];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int32_t* dict = sdict[w];
   for (int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + w; s < S; s += (int64_t)gridDim.x * kWarpsPerBlock) {
     const uint2 d0 = desc[s], d1 = desc[s + 1];
     const int L = (int)((d1.x - d0.x) >> 5);
-    const int nw = (L + 3) >> 2;
-    const int Dp = (int)(d1.y - d0.y) - kSliceRows * nw;
+    const bool w4 = (tinfo[s] & kSliceW4) != 0;
+    const int per = w4 ? 8 : 4, bits = w4 ? 4 : 8;
+    const int nw = (L + per - 1) / per;
+    if ((int64_t)(d1.y - d0.y) != (int64_t)kSliceRows * nw) {
+      if (lane == 0) atomicOr(err, 4);
+      continue;
+    }
     const int64_t row = s * kSliceRows + lane;
     const int64_t rs = row < n ? row_ptr[row] : 0;
-    uint32_t* iw = reinterpret_cast<uint32_t*>(ibuf + d0.y + Dp);
+    uint32_t* iw = reinterpret_cast<uint32_t*>(ibuf + d0.y);
     int32_t* ps = pos + d0.x;
     uint32_t word = 0;
     const int D = slice_table(row_ptr, col, n, s, L, dict, [&](int k, bool has, int id, int cnt) {
@@ -136,19 +161,14 @@ __global__ void __launch_bounds__(kThreads)
               break;
             }
       }
-      word |= (uint32_t)id << (8 * (k & 3));
-      if ((k & 3) == 3 || k == L - 1) {
-        iw[(k >> 2) * kSliceRows + lane] = word;
+      word |= (uint32_t)id << (bits * (k % per));
+      if (k % per == per - 1 || k == L - 1) {
+        iw[(k / per) * kSliceRows + lane] = word;
         word = 0;
       }
       ps[k * kSliceRows + lane] = has ? (int32_t)(rs + k) : -1;
     });
-    if (((D + 7) & ~7) != Dp) {
-      if (lane == 0) atomicOr(err, 4);
-      continue;
-    }
-    __syncwarp();
-    for (int j = lane; j < Dp; j += 32) ibuf[d0.y + j] = j < D ? dict[j] : 0;
+    if ((D <= 16) != w4 && lane == 0) atomicOr(err, 4);
   }
 }
 
@@ -195,15 +215,17 @@ struct Tmp {
 }  // namespace
 
 void free_sliced(rp_handle* h) {
-  void* ptrs[] = {h->sl_desc, h->sl_ibuf, h->sl_pos, h->sl_vals, h->sl_vals32};
+  void* ptrs[] = {h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_pos, h->sl_vals, h->sl_vals32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->sl_desc = nullptr;
+  h->sl_tinfo = nullptr;
+  h->sl_tabs = nullptr;
   h->sl_ibuf = nullptr;
   h->sl_pos = nullptr;
   h->sl_vals = nullptr;
   h->sl_vals32 = nullptr;
-  h->sl_slices = h->sl_entries = h->sl_ibuf_len = 0;
+  h->sl_slices = h->sl_entries = h->sl_ibuf_len = h->sl_tabs_len = 0;
 }
 
 rp_status build_sliced(rp_handle* h, cudaStream_t st) {
@@ -228,15 +250,48 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
   RP_TRY_CUDA(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
   RP_TRY_CUDA(cudaStreamSynchronize(st));
   if (herr) return RP_OK;  // a row or a slice does not fit: CSR iteration
+
+  // every slice's table into one scratch array, then distinct tables kept once
+  std::vector<int64_t> toff(S + 1, 0);
+  for (int64_t s = 0; s < S; ++s) toff[s + 1] = toff[s] + ht[s];
+  int64_t* dtoff;
+  int32_t* dtab;
+  RP_TRY(tmp.alloc(&dtoff, S + 1));
+  RP_TRY(tmp.alloc(&dtab, toff[S] + 1));
+  RP_TRY_CUDA(cudaMemcpyAsync(dtoff, toff.data(), 8 * (S + 1), cudaMemcpyHostToDevice, st));
+  k_slice_tables<<<g, kThreads, 0, st>>>(h->row_ptr, h->col_idx, n, S, width, dtoff, dtab);
+  RP_TRY_CUDA(cudaGetLastError());
+  std::vector<int32_t> htab(toff[S]);
+  RP_TRY_CUDA(cudaMemcpyAsync(htab.data(), dtab, 4 * toff[S], cudaMemcpyDeviceToHost, st));
+  RP_TRY_CUDA(cudaStreamSynchronize(st));
+  std::vector<int32_t> tabs;
+  std::vector<uint32_t> tinfo(S + kSliceDescPad, 0u);
+  std::unordered_map<std::string, uint32_t> seen;
   std::vector<uint2> desc(S + 1 + kSliceDescPad, make_uint2(0u, 0u));
   uint64_t x = 0, y = 0;
   for (int64_t s = 0; s < S; ++s) {
+    const int D = ht[s];
+    std::string key(reinterpret_cast<const char*>(htab.data() + toff[s]), 4 * (size_t)D);
+    auto it = seen.find(key);
+    uint32_t t;
+    if (it == seen.end()) {
+      tabs.push_back(D);
+      t = (uint32_t)tabs.size();
+      tabs.insert(tabs.end(), htab.begin() + toff[s], htab.begin() + toff[s + 1]);
+      seen.emplace(std::move(key), t);
+    } else {
+      t = it->second;
+    }
+    const bool w4 = D <= 16;
+    tinfo[s] = t | (w4 ? kSliceW4 : 0u);
     desc[s] = make_uint2((uint32_t)x, (uint32_t)y);
+    const int per = w4 ? 8 : 4;
     x += (uint64_t)kSliceRows * hw[s];
-    y += (uint64_t)ht[s] + (uint64_t)kSliceRows * ((hw[s] + 3) / 4);
-    if (x > 0xffffff00ull || y > 0xffffff00ull) return RP_OK;  // offsets past 32 bits: CSR iteration
+    y += (uint64_t)kSliceRows * ((hw[s] + per - 1) / per);
+    if (x > 0xffffff00ull || y > 0xffffff00ull || tabs.size() > 0x7fffff00ull) return RP_OK;  // CSR iteration
   }
   desc[S] = make_uint2((uint32_t)x, (uint32_t)y);
+  tabs.insert(tabs.end(), 32, 0);  // lanes past a table read these
   free_sliced(h);
   auto undo = [&](rp_status s) {
     free_sliced(h);
@@ -248,6 +303,8 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
     if (s_ != RP_OK) return undo(s_); \
   } while (0)
   SL_TRY(salloc(&h->sl_desc, S + 1 + kSliceDescPad));
+  SL_TRY(salloc(&h->sl_tinfo, S + kSliceDescPad));
+  SL_TRY(salloc(&h->sl_tabs, (int64_t)tabs.size()));
   SL_TRY(salloc(&h->sl_ibuf, (int64_t)y));
   SL_TRY(salloc(&h->sl_pos, (int64_t)x));
   SL_TRY(salloc(&h->sl_vals, (int64_t)x));
@@ -259,16 +316,22 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
   };
   RP_TRY(cu(cudaMemcpyAsync(h->sl_desc, desc.data(), sizeof(uint2) * desc.size(), cudaMemcpyHostToDevice, st),
             "sliced descriptor upload"));
+  RP_TRY(cu(cudaMemcpyAsync(h->sl_tinfo, tinfo.data(), 4 * tinfo.size(), cudaMemcpyHostToDevice, st),
+            "sliced table reference upload"));
+  RP_TRY(cu(cudaMemcpyAsync(h->sl_tabs, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, st),
+            "sliced table upload"));
   RP_TRY(cu(cudaMemsetAsync(h->sl_vals, 0, 8 * x, st), "sliced value clear"));
   if (h->sl_vals32) RP_TRY(cu(cudaMemsetAsync(h->sl_vals32, 0, 4 * x, st), "sliced value clear"));
-  k_slice_fill<<<g, kThreads, 0, st>>>(h->row_ptr, h->col_idx, n, S, h->sl_desc, h->sl_ibuf, h->sl_pos, err);
+  k_slice_fill<<<g, kThreads, 0, st>>>(h->row_ptr, h->col_idx, n, S, h->sl_desc, h->sl_tinfo, h->sl_ibuf,
+                                       h->sl_pos, err);
   RP_TRY(cu(cudaGetLastError(), "k_slice_fill"));
   RP_TRY(cu(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st), "error readback"));
   RP_TRY(cu(cudaStreamSynchronize(st), "sliced layout build"));
-  if (herr) return undo(fail(RP_ECUDA, "sliced layout: table lengths differ between passes"));
+  if (herr) return undo(fail(RP_ECUDA, "sliced layout: slice sizes differ between passes"));
   h->sl_slices = S;
   h->sl_entries = (int64_t)x;
   h->sl_ibuf_len = (int64_t)y;
+  h->sl_tabs_len = (int64_t)tabs.size();
   return RP_OK;
 }
 
@@ -295,7 +358,10 @@ extern "C" rp_status rp_get_sliced_view(const rp_handle* h, rp_sliced_view* out)
   out->n_slices = h->sl_slices;
   out->n_entries = h->sl_entries;
   out->ibuf_len = h->sl_ibuf_len;
+  out->tabs_len = h->sl_tabs_len;
   out->desc = reinterpret_cast<const uint32_t*>(h->sl_desc);
+  out->tinfo = h->sl_tinfo;
+  out->tabs = h->sl_tabs;
   out->ibuf = h->sl_ibuf;
   out->pos = h->sl_pos;
   out->vals = h->sl_vals;

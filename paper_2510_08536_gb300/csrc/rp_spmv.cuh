@@ -58,11 +58,13 @@ __device__ __forceinline__ T row_dot_any(const Parts<T>& P, const int32_t* __res
 
 inline Sliced<double> sliced64(const rp_handle* h, const double* vals) {
   if (h->sl_slices == 0 || vals != h->vals) return Sliced<double>{};  // e.g. transposed values
-  return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_ibuf, h->sl_vals, h->opts.spin_limit};
+  return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_vals,
+                        h->opts.spin_limit};
 }
 inline Sliced<float> sliced32(const rp_handle* h) {
   if (h->sl_slices == 0 || !h->sl_vals32) return Sliced<float>{};
-  return Sliced<float>{h->sl_slices, h->sl_desc, h->sl_ibuf, h->sl_vals32, h->opts.spin_limit};
+  return Sliced<float>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_vals32,
+                       h->opts.spin_limit};
 }
 
 // 16-byte vectors of the streaming kernels
@@ -104,16 +106,15 @@ __device__ __forceinline__ void for_each_comp(F&& f) {
 // chunk: rows 256 c + 32 w + lane, as the CSR body's thread 32 w + lane of
 // block c maps rows). The producer keeps up to kStages chunks in flight:
 // once consumers have released a stage (its "empty" mbarrier), it posts the
-// byte count on the stage's "full" mbarrier and issues three cp.async.bulk
-// copies -- the chunk's values, its offset tables + index words and its run
-// of slice descriptors. Bytes in flight cost no registers, and consumer
-// warps wait only on their own chunk's data, not on each other; a slice
-// then waits on one memory round trip, its gathers of p. Offset tables of
-// up to 32 entries are read with a warp shuffle (source lane = index byte,
-// taken modulo 32 by the shuffle), longer ones from shared memory; rows of
-// up to 8 entries run a body unrolled for their exact width. A chunk larger
-// than a stage (rows over 8 entries, long tables) is read straight from
-// global memory by the same warps. Every barrier wait is bounded: after
+// byte count on the stage's "full" mbarrier and issues four cp.async.bulk
+// copies -- the chunk's values, its index words, its run of slice
+// descriptors and its table references. Bytes in flight cost no registers,
+// and consumer warps wait only on their own chunk's data, not on each other;
+// a slice then waits on one memory round trip, its gathers of p. The offset
+// tables (few, shared by many slices) are read through L1 and looked up with
+// warp shuffles (slice_offset); rows of up to 8 entries run a body unrolled
+// for their exact width. A chunk larger than a stage (long rows) is read
+// straight from global memory by the same warps. Every barrier wait is bounded: after
 // spin iterations the block waits (bounded) for its own copies and calls the
 // epilogue's timeout (which records RP_DEVICE_TIMEOUT and stops the solve).
 //
@@ -123,8 +124,9 @@ __device__ __forceinline__ void for_each_comp(F&& f) {
 
 constexpr int kChunk = kThreads / 32;  // slices per chunk, one per consumer warp
 constexpr int kSlThreads = kThreads + 32;
-constexpr int kStageIdx = 3072;        // table + index word bytes a stage holds
+constexpr int kStageIdx = 3072;        // index word bytes a stage holds
 constexpr int kStageDesc = 128;        // descriptor run (kChunk + 1 entries, padded)
+constexpr int kStageInfo = 32;         // table references of the chunk's kChunk slices
 
 // Two stages per block (FP32 23 KB, FP64 39 KB): warps beat depth -- at
 // 256^3 the FP32 SpMV takes 0.138 ms with 2 stages (7 blocks of 9 warps an
@@ -134,7 +136,7 @@ template <typename T>
 struct SlStage {
   static constexpr int kStages = 2;
   static constexpr int kVals = kChunk * kSliceRows * 8 * (int)sizeof(T);  // rows of <= 8 entries
-  static constexpr int kBytes = kVals + kStageIdx + kStageDesc;
+  static constexpr int kBytes = kVals + kStageIdx + kStageDesc + kStageInfo;
   static constexpr int kSmem = kStages * kBytes;
 };
 
@@ -175,75 +177,81 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-// Offset of the entry whose index byte is byte e of wd. SHFL: tables of up to
-// 32 entries held one per lane in tv (warp-uniform choice, all lanes call).
-template <bool SHFL>
+// How a slice's offset indices are read: 4-bit indices into a table of at
+// most 16 offsets held in tv by both half-warps (lane & 15), looked up by a
+// shuffle of width 16 (the source lane is taken modulo 16, so a shifted word
+// needs no mask); 8-bit indices into a table of at most 32 offsets held in tv,
+// shuffle of width 32; 8-bit indices into a longer table, read from global
+// memory (tables are few and stay in L1). All lanes call the shuffles.
+enum : int { kIdx4 = 0, kIdx8Shfl = 1, kIdx8Glob = 2 };
+
+template <int MODE>
 __device__ __forceinline__ int slice_offset(uint32_t wd, int e, int32_t tv, const int32_t* tab) {
-  if (SHFL) return __shfl_sync(0xffffffffu, tv, (int)(wd >> (8 * e)));
-  return tab[(wd >> (8 * e)) & 255u];
+  if (MODE == kIdx4) return __shfl_sync(0xffffffffu, tv, (int)(wd >> (4 * e)), 16);
+  if (MODE == kIdx8Shfl) return __shfl_sync(0xffffffffu, tv, (int)(wd >> (8 * e)));
+  return __ldg(tab + ((wd >> (8 * e)) & 255u));
 }
 
 // Sum of one row of a slice, L entries: values at v[32 k] (lane applied),
-// index words at iw[32 g]; the same fused multiply-adds in the same order as
-// row_dot over the row's CSR entries. Lanes without a row (valid false) run
-// the shuffles but load nothing.
-template <typename T, bool SHFL, int L>
+// index words at iw[32 g] (lane applied); the same fused multiply-adds in the
+// same order as row_dot over the row's CSR entries. Lanes without a row
+// (valid false) run the shuffles but load nothing.
+template <typename T, int MODE, int L>
 __device__ __forceinline__ T slice_row_exact(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab,
                                              const T* x, bool valid) {
-  const uint32_t w0 = iw[0], w1 = L > 4 ? iw[kSliceRows] : 0u;
+  constexpr int PER = MODE == kIdx4 ? 8 : 4;
+  const uint32_t w0 = iw[0], w1 = L > PER ? iw[kSliceRows] : 0u;
   T vv[L];
 #pragma unroll
   for (int k = 0; k < L; ++k) vv[k] = v[k * kSliceRows];
   T sum = T(0);
 #pragma unroll
   for (int k = 0; k < L; ++k) {
-    const int off = slice_offset<SHFL>(k < 4 ? w0 : w1, k & 3, tv, tab);
+    const int off = slice_offset<MODE>(k < PER ? w0 : w1, k % PER, tv, tab);
     if (valid) sum = fma(vv[k], __ldg(x + off), sum);
   }
   return sum;
 }
 
-template <typename T, bool SHFL>
+template <typename T, int MODE>
 __device__ __forceinline__ T slice_row(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab, const T* x,
                                        bool valid, int L) {
   switch (L) {
-    case 1: return slice_row_exact<T, SHFL, 1>(v, iw, tv, tab, x, valid);
-    case 2: return slice_row_exact<T, SHFL, 2>(v, iw, tv, tab, x, valid);
-    case 3: return slice_row_exact<T, SHFL, 3>(v, iw, tv, tab, x, valid);
-    case 4: return slice_row_exact<T, SHFL, 4>(v, iw, tv, tab, x, valid);
-    case 5: return slice_row_exact<T, SHFL, 5>(v, iw, tv, tab, x, valid);
-    case 6: return slice_row_exact<T, SHFL, 6>(v, iw, tv, tab, x, valid);
-    case 7: return slice_row_exact<T, SHFL, 7>(v, iw, tv, tab, x, valid);
-    case 8: return slice_row_exact<T, SHFL, 8>(v, iw, tv, tab, x, valid);
+    case 1: return slice_row_exact<T, MODE, 1>(v, iw, tv, tab, x, valid);
+    case 2: return slice_row_exact<T, MODE, 2>(v, iw, tv, tab, x, valid);
+    case 3: return slice_row_exact<T, MODE, 3>(v, iw, tv, tab, x, valid);
+    case 4: return slice_row_exact<T, MODE, 4>(v, iw, tv, tab, x, valid);
+    case 5: return slice_row_exact<T, MODE, 5>(v, iw, tv, tab, x, valid);
+    case 6: return slice_row_exact<T, MODE, 6>(v, iw, tv, tab, x, valid);
+    case 7: return slice_row_exact<T, MODE, 7>(v, iw, tv, tab, x, valid);
+    case 8: return slice_row_exact<T, MODE, 8>(v, iw, tv, tab, x, valid);
     default: break;
   }
+  constexpr int PER = MODE == kIdx4 ? 8 : 4;
   T sum = T(0);
-  for (int g = 0; g < ((L + 3) >> 2); ++g) {
+  for (int g = 0; g < (L + PER - 1) / PER; ++g) {
     const uint32_t wd = iw[g * kSliceRows];
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (4 * g + e < L) {
-        const int off = slice_offset<SHFL>(wd, e, tv, tab);
-        if (valid) sum = fma(v[(4 * g + e) * kSliceRows], __ldg(x + off), sum);
+    for (int e = 0; e < PER; ++e)
+      if (PER * g + e < L) {
+        const int off = slice_offset<MODE>(wd, e, tv, tab);
+        if (valid) sum = fma(v[(PER * g + e) * kSliceRows], __ldg(x + off), sum);
       }
   }
   return sum;
 }
 
-// One slice: descriptor pair (d0, d1), values v and table tab (shared or
-// global), gathers from x relative to the lane's row.
+// One slice: descriptor pair (d0, d1), table reference info, values v and
+// index words iw (shared memory or global, lane applied), tables tabs (global),
+// gathers from x relative to the lane's row.
 template <typename T>
-__device__ __forceinline__ T slice_sum(uint2 d0, uint2 d1, const T* v, const int32_t* tab, const T* x, bool valid,
-                                       int lane) {
+__device__ __forceinline__ T slice_sum(uint2 d0, uint2 d1, uint32_t info, const T* v, const uint32_t* iw,
+                                       const int32_t* __restrict__ tabs, const T* x, bool valid, int lane) {
   const int L = (int)((d1.x - d0.x) >> 5);
-  const int D = (int)(d1.y - d0.y) - kSliceRows * ((L + 3) >> 2);
-  const uint32_t* iw = reinterpret_cast<const uint32_t*>(tab + D) + lane;
-  if (D <= 32) {
-    // a slice holds >= 32 words of table + index words: lanes past D read one of them, unused
-    const int32_t tv = tab[lane];
-    return slice_row<T, true>(v, iw, tv, tab, x, valid, L);
-  }
-  return slice_row<T, false>(v, iw, 0, tab, x, valid, L);
+  const int32_t* tab = tabs + (info & ~kSliceW4);
+  if (info & kSliceW4) return slice_row<T, kIdx4>(v, iw, __ldg(tab + (lane & 15)), tab, x, valid, L);
+  if (__ldg(tab - 1) <= 32) return slice_row<T, kIdx8Shfl>(v, iw, __ldg(tab + lane), tab, x, valid, L);
+  return slice_row<T, kIdx8Glob>(v, iw, 0, tab, x, valid, L);
 }
 
 template <typename T, class Epi>
@@ -302,10 +310,11 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, int64_t n64, co
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (fit) {
           const uint32_t db = 16u * (uint32_t)((kChunk + 2) / 2);  // kChunk + 1 descriptors, 16-byte multiple
-          mbar_expect_tx(&full[st], vb + ib + db);
+          mbar_expect_tx(&full[st], vb + ib + db + kStageInfo);
           bulk_g2s(base, sl.vals + d0.x, vb, &full[st]);
           bulk_g2s(base + St::kVals, sl.ibuf + d0.y, ib, &full[st]);
           bulk_g2s(base + St::kVals + kStageIdx, desc + (int64_t)ch * kChunk, db, &full[st]);
+          bulk_g2s(base + St::kVals + kStageIdx + kStageDesc, sl.tinfo + (int64_t)ch * kChunk, kStageInfo, &full[st]);
         } else {
           mbar_arrive(&full[st]);
         }
@@ -330,13 +339,15 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, int64_t n64, co
         T sum;
         if (staged[st]) {
           const uint2* sd = reinterpret_cast<const uint2*>(base + St::kVals + kStageIdx);
+          const uint32_t* si = reinterpret_cast<const uint32_t*>(base + St::kVals + kStageIdx + kStageDesc);
           const uint2 d0 = sd[w], d1 = sd[w + 1];
-          sum = slice_sum<T>(d0, d1, reinterpret_cast<const T*>(base) + (d0.x - chunk_x[st]) + lane,
-                             reinterpret_cast<const int32_t*>(base + St::kVals) + (d0.y - chunk_y[st]), x, valid,
-                             lane);
+          sum = slice_sum<T>(d0, d1, si[w], reinterpret_cast<const T*>(base) + (d0.x - chunk_x[st]) + lane,
+                             reinterpret_cast<const uint32_t*>(base + St::kVals) + (d0.y - chunk_y[st]) + lane,
+                             sl.tabs, x, valid, lane);
         } else {
           const uint2 d0 = __ldg(desc + s), d1 = __ldg(desc + s + 1);
-          sum = slice_sum<T>(d0, d1, sl.vals + d0.x + lane, sl.ibuf + d0.y, x, valid, lane);
+          sum = slice_sum<T>(d0, d1, __ldg(sl.tinfo + s), sl.vals + d0.x + lane,
+                             reinterpret_cast<const uint32_t*>(sl.ibuf + d0.y) + lane, sl.tabs, x, valid, lane);
         }
         if (valid) {
           yout[row] = sum;

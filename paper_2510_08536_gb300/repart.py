@@ -56,8 +56,8 @@ class SolveInfo(ctypes.Structure):
 
 
 class SlicedView(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_int64) for k in ("n_slices", "n_entries", "ibuf_len")] + \
-               [(k, ctypes.c_void_p) for k in ("desc", "ibuf", "pos", "vals", "vals32")]
+    _fields_ = [(k, ctypes.c_int64) for k in ("n_slices", "n_entries", "ibuf_len", "tabs_len")] + \
+               [(k, ctypes.c_void_p) for k in ("desc", "tinfo", "tabs", "ibuf", "pos", "vals", "vals32")]
 
 
 class MapView(ctypes.Structure):
@@ -273,11 +273,11 @@ def iter_spmv(h: Handle, x, y, precision: str = "fp64", stream=None):
 
 
 def sliced_sizes(h: Handle):
-    """(n_slices, n_entries, ibuf_len) of the sliced layout, or None when the
-    iteration runs on the CSR arrays."""
+    """(n_slices, n_entries, ibuf_len, tabs_len) of the sliced layout, or None
+    when the iteration runs on the CSR arrays."""
     v = SlicedView()
     _check(load().rp_get_sliced_view(h.ptr, ctypes.byref(v)), "rp_get_sliced_view")
-    return (v.n_slices, v.n_entries, v.ibuf_len) if v.n_slices else None
+    return (v.n_slices, v.n_entries, v.ibuf_len, v.tabs_len) if v.n_slices else None
 
 
 def get_sliced_view(h: Handle) -> dict:
@@ -289,8 +289,10 @@ def get_sliced_view(h: Handle) -> dict:
         return None
     import torch
     torch.cuda.synchronize()
-    return dict(n_slices=v.n_slices, n_entries=v.n_entries, ibuf_len=v.ibuf_len,
+    return dict(n_slices=v.n_slices, n_entries=v.n_entries, ibuf_len=v.ibuf_len, tabs_len=v.tabs_len,
                 desc=_view(v.desc, 2 * (v.n_slices + 1), "<i4").clone(),
+                tinfo=_view(v.tinfo, v.n_slices, "<i4").clone(),
+                tabs=_view(v.tabs, v.tabs_len, "<i4").clone(),
                 ibuf=_view(v.ibuf, v.ibuf_len, "<i4").clone(),
                 pos=_view(v.pos, v.n_entries, "<i4").clone(),
                 vals=_view(v.vals, v.n_entries, "<f8").clone(),
