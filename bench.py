@@ -80,7 +80,8 @@ def parse():
     ap.add_argument("--only-batch", action="store_true",
                     help="run only the batched form (default launch shape, no loop baseline): profiling runs")
     ap.add_argument("--batch-systems", type=int, default=256)
-    ap.add_argument("--no-bicgstab", action="store_true", help="skip the non-symmetric (momentum) solve")
+    ap.add_argument("--no-bicgstab", action="store_true",
+                    help="skip the non-symmetric (momentum) solve and the adjoint measurement")
     ap.add_argument("--no-line", action="store_true", help="skip the line-preconditioner measurement")
     ap.add_argument("--alpha-sweep", action="store_true",
                     help="repartitioning-ratio study at 128^3: GPU parts and CPU ranks merged")
@@ -214,6 +215,56 @@ def oracle_counts(workload, seeds):
         fill = int(round(statistics.mean(known))) if known else None
         got = [fill if c is None else c for c in got]
     return got
+
+
+# ---------------------------------------------------------------- adjoint (gradients)
+
+
+def run_adjoint(dev, reps=3):
+    """128^3, k = 64: forward FP64 solve, adjoint solve A^T lambda = x - x_t, entry and
+    face gradients (all faces), each timed with CUDA events (mean of reps)."""
+    import torch
+
+    from paper_2510_08536_gb300 import repart, synth
+    mesh = synth.workload_mesh("adjoint_128")
+    stg = torch.from_numpy(synth.Assembler(mesh).staging(synth.face_coeffs(mesh, 0.5, 100))).to(dev)
+    b = torch.from_numpy(synth.uniform_vector(mesh, 0)).to(dev)
+    xt = torch.from_numpy(synth.uniform_vector(mesh, 1)).to(dev)
+    t0 = time.perf_counter()
+    h = repart.build_repartition(mesh.ranks, want_transpose=True, want_fp32=False)
+    build_ms = 1e3 * (time.perf_counter() - t0)
+    n, nf = mesh.n_cells, sum(r.n_faces + r.n_iface for r in mesh.ranks)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    lam = torch.zeros_like(x)
+    gbuf = torch.zeros(h.n_slots, dtype=torch.float64, device=dev)
+    gface = torch.zeros(nf, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def timed(name, fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [fn() for _ in range(reps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_ms"] = round(e0.elapsed_time(e1) / reps, 3)
+        return res[-1]
+
+    timed("update", lambda: repart.update_values_packed(h, stg))
+    info = timed("forward_solve", lambda: repart.solve(h, b, x, tol=1e-9))
+    g = x - xt
+    ainfo = timed("adjoint_solve", lambda: repart.solve_adjoint(h, g, lam, tol=1e-9))
+    timed("entry_grad", lambda: repart.entry_grad(h, lam, x, gbuf))
+    timed("face_grad", lambda: repart.face_grad(h, lam, x, gface))
+    h.close()
+    out.update({"workload": "adjoint_128: 128^3 cells, k=64 (4x4x4), lognormal(0,0.5) faces, rhs U[-1,1] seed 0, "
+                            "x_target U[-1,1] seed 1, FP64, rel. residual 1e-9",
+                "map_build_with_transpose_ms": round(build_ms, 1), "faces": nf,
+                "forward_iterations": info["iterations"], "adjoint_iterations": ainfo["iterations"],
+                "statuses": [info["status"], ainfo["status"]]})
+    return out
 
 
 # ---------------------------------------------------------------- momentum (BiCGStab)
@@ -670,6 +721,9 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = run_batch(args, dev, steps=max(1, min(args.steps, 5)), warmup=max(1, min(args.warmup, 2)))
+    adj = None
+    if not args.no_bicgstab and args.workload == "mixed_256":
+        adj = run_adjoint(dev)
     bicg = None
     if not args.no_bicgstab and args.workload == "mixed_256":
         bicg = run_bicgstab(dev, steps=max(1, min(args.steps, 3)), warmup=max(1, min(args.warmup, 2)))
@@ -713,7 +767,7 @@ def run_ours(args):
         "roofline_fp64_spmv": fp64_alu,
         "map_build_ms": round(build_ms, 1), "input_setup_s": round(setup_s, 1), "update_paths": update_paths,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": results[head]["gpu_launches"], "batched": batched,
-        "bicgstab": bicg, "line_precond": line,
+        "bicgstab": bicg, "line_precond": line, "adjoint": adj,
         "clocks": clocks[head], "clocks_other": {o: clocks[o] for o in other},
     }
     return line
