@@ -323,6 +323,7 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
     """256 uneven independent systems (8k-300k cells, aspect 1-4, lognormal(0, 0.5)):
     update + solve of all of them in one persistent launch per step, FP64 and mixed,
     launch shape autotuned; compared with a loop of single-system rp_solve calls."""
+    import numpy as np
     import torch
 
     from paper_2510_08536_gb300 import repart, synth
@@ -339,6 +340,16 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
                        "from x=0",
            "systems": len(B.systems), "rows": B.n_rows, "nnz": h.nnz, "input_setup_s": round(setup_s, 1)}
     sizes = [(m.n_cells, m.nnz()) for m in B.meshes]
+    # per system (padded entries E, index words I, slices S) of the sliced layout, when built
+    view = repart.get_sliced_view(h)
+    sl_sizes = None
+    if view is not None:
+        d = view["desc"].cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+        so = np.cumsum([0] + [(m.n_cells + 31) // 32 for m in B.meshes])
+        sl_sizes = [(int(d[so[i + 1], 0] - d[so[i], 0]), int(d[so[i + 1], 1] - d[so[i], 1]), int(so[i + 1] - so[i]))
+                    for i in range(len(B.meshes))]
+        del view
+    out["layout"] = "sliced" if sl_sizes else "csr"
     hbm_peak, _ = load_peaks()
     if not args.only_batch:
         c, t, ms = repart.batch_autotune(h, stg[0], b, x, tol=1e-9, precision="fp64")
@@ -358,16 +369,26 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
         ms = e0.elapsed_time(e1) / steps
         bad = sum(1 for infos in infos_all for i in infos if i["status"] != 0)
         iters = [sum(i["iterations"] for i in infos) for infos in infos_all]
-        # algorithmic bytes of one step: update (24 B/entry + 20 B/row), every iteration
-        # (FP64: SpMV + 80 B/row; FP32: SpMV + 40 B/row), every FP64 residual pass
+        # algorithmic bytes of one step: update (24 B/entry + 20 B/row, plus the sliced
+        # values: position, source index, buffer value, FP64 (and FP32) value per padded
+        # entry), every iteration (FP64: SpMV + 80 B/row; FP32: SpMV + 40 B/row), every
+        # FP64 residual pass; SpMV on CSR: values, columns, row pointers, x, y; sliced:
+        # padded values, index words, descriptors and table references, x, y
         w = 8 if prec == "fp64" else 4
         moved = 0.0
         for infos in infos_all:
             for s, inf in enumerate(infos):
                 nn, nz = sizes[s]
-                spmv = (w + 4) * nz + 4 * (nn + 1) + 2 * w * nn
-                res = 12 * nz + 4 * (nn + 1) + 40 * nn
-                moved += 24 * nz + 20 * nn + inf["iterations"] * (spmv + 10 * w * nn) + inf["passes"] * res
+                if sl_sizes:
+                    E, I, S = sl_sizes[s]
+                    spmv = w * E + 4 * I + 12 * S + 2 * w * nn
+                    res = 8 * E + 4 * I + 12 * S + 40 * nn
+                    upd = 24 * nz + 20 * nn + (24 + (w == 4) * 4) * E
+                else:
+                    spmv = (w + 4) * nz + 4 * (nn + 1) + 2 * w * nn
+                    res = 12 * nz + 4 * (nn + 1) + 40 * nn
+                    upd = 24 * nz + 20 * nn
+                moved += upd + inf["iterations"] * (spmv + 10 * w * nn) + inf["passes"] * res
         gbps = moved / len(infos_all) / (ms * 1e-3) / 1e9
         out[prec] = {"ms_per_step": round(ms, 3), "not_converged_systems": bad,
                      "iterations_sum_mean": statistics.mean(iters),

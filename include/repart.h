@@ -67,10 +67,11 @@ enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1, RP_MEM_HOST_DIRECT = 2 };
  * the search direction continues (p = z + beta p). */
 enum { RP_FP64 = 0, RP_MIXED = 1, RP_MIXED_RU = 2 };
 /* Matrix layout of the PCG iteration (rp_options.layout). RP_LAYOUT_AUTO:
- * the sliced layout (see rp_get_sliced_view) when the matrix is one part,
- * no row has more than 32 entries and no 32-row slice more than 256
- * distinct column offsets; else CSR. RP_LAYOUT_CSR: always CSR. Both give
- * the same products row by row (same entries, same order). */
+ * the sliced layout (see rp_get_sliced_view) when the matrix is one part
+ * (or, for the batched solve, every system is one), no row has more than 32
+ * entries and no 32-row slice more than 256 distinct column offsets; else
+ * CSR. RP_LAYOUT_CSR: always CSR. Both give the same products row by row
+ * (same entries, same order). */
 enum { RP_LAYOUT_AUTO = 0, RP_LAYOUT_CSR = 1 };
 /* Preconditioner of the PCG solves (rp_options.precond). RP_PRECOND_JACOBI:
  * z = D^-1 r. RP_PRECOND_LINE: block-Jacobi over blocks of 32 consecutive
@@ -234,9 +235,15 @@ rp_status rp_spmv_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_
  * (D <= 16): 4-bit offset indices, entry 8 g + e of lane j in bits 4e..4e+3
  * of ibuf[y_s + 32 g + j]; w4 = 0: 8-bit indices, entry 4 g + e in byte e of
  * ibuf[y_s + 32 g + j]. pos[x_s + 32 k + j] is the CSR position of that entry,
- * -1 for padding. Entry k of a row is its k-th CSR entry. Device views, owned
- * by the handle; n_entries counts padded entries, ibuf_len index words,
- * tabs_len table words. */
+ * -1 for padding. Entry k of a row is its k-th CSR entry. A batched handle
+ * (rp_batch_build, several parts) holds the slices of every system one after
+ * the other, system p's ceil(n_p / 32) slices after those of systems < p:
+ * there rows and column offsets are those of the system's own CSR matrix
+ * (rp_get_part_map) and pos holds positions in the handle's value array
+ * (rp_get_values); the batched kernel writes these values, the value update
+ * of the merged handle's solve refills them too. Device views, owned by the
+ * handle; n_entries counts padded entries, ibuf_len index words, tabs_len
+ * table words. */
 typedef struct rp_sliced_view {
   int64_t n_slices, n_entries, ibuf_len, tabs_len;
   const uint32_t* desc;

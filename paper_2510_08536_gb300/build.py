@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librepart.so")
 SOURCES = ["rp_map.cu", "rp_update.cu", "rp_pcg.cu", "rp_adjoint.cu", "rp_batch.cu", "rp_noalloc.cu", "rp_sliced.cu", "rp_bicgstab.cu"]
-HEADERS = [os.path.join(CSRC, "rp_common.cuh"), os.path.join(ROOT, "include", "repart.h")]
+HEADERS = [os.path.join(CSRC, h) for h in sorted(os.listdir(CSRC)) if h.endswith(".cuh")] + [
+    os.path.join(ROOT, "include", "repart.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

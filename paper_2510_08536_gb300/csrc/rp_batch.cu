@@ -7,7 +7,9 @@
 // (FP64, or FP32-inner / FP64-outer refinement) of that system, writes the
 // system's status, and takes the next one. Teams never wait on each other.
 //
-// Inside a team the rows of the system are split into T contiguous blocks.
+// Inside a team the rows of the system are split into T contiguous blocks
+// (whole 32-row slices when the sliced layout is built: each CTA then writes
+// its own slices' values in the update and its SpMV runs one warp per slice).
 // The two reductions of each CG iteration go through distributed shared
 // memory: every CTA publishes its partial sums in its own shared memory and,
 // after a hardware cluster barrier, every CTA reads all T partials in rank
@@ -24,6 +26,7 @@
 #include <numeric>
 
 #include "rp_common.cuh"
+#include "rp_spmv.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -101,6 +104,108 @@ __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const 
   for (; i < i1; i += nth) f(i, row_dot_coherent<T>(rp, col, vals, x, i));
 }
 
+// Per-warp staging of one slice's values and index words (slices of up to
+// kStageL entries per row): two buffers per warp in dynamic shared memory.
+constexpr int kStageL = 8;
+constexpr int kStageValBytes = kStageL * 32 * 8;      // FP64 values
+constexpr int kStageIdxBytes = 2 * 32 * 4;            // 8-bit indices: 2 words per row
+constexpr int kStageBuf = kStageValBytes + kStageIdxBytes;
+constexpr int kWarpStage = 2 * kStageBuf;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The warp copies slice (d0, d1) into buf: values (a multiple of 32 entries,
+// 128-byte aligned) at buf, index words (a multiple of 32) at buf + kStageValBytes.
+template <typename T>
+__device__ __forceinline__ void stage_slice(unsigned char* buf, const T* vals, const uint32_t* ibuf, uint2 d0,
+                                            uint2 d1, int lane) {
+  const uint32_t vb = (d1.x - d0.x) * (uint32_t)sizeof(T), ib = (d1.y - d0.y) * 4u;
+  const unsigned char* vs = reinterpret_cast<const unsigned char*>(vals + d0.x);
+  const unsigned char* is = reinterpret_cast<const unsigned char*>(ibuf + d0.y);
+  for (uint32_t o = 16u * lane; o < vb; o += 512u) cp_async16(buf + o, vs + o);
+  for (uint32_t o = 16u * lane; o < ib; o += 512u) cp_async16(buf + kStageValBytes + o, is + o);
+}
+
+__device__ __forceinline__ bool stageable(uint2 d0, uint2 d1) { return d1.x - d0.x <= 32u * kStageL; }
+
+// y_i = (A x)_i for rows [i0, i1) (i0 a multiple of 32) on the sliced layout:
+// one warp per slice, lanes on rows, the same fused multiply-adds in the same
+// order as the CSR row sums. The warp's next slice is copied (cp.async, L2
+// only) into its other staging buffer while the current one is summed, so the
+// value and index loads of one slice overlap the gathers of the previous one;
+// descriptors are loaded two slices ahead. Values and x are written inside the
+// kernel (the values before a block barrier, read back through L2; x with
+// plain loads); descriptors, tables and index words are read-only.
+template <typename T, typename F>
+__device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, int64_t s0, const T* x, int64_t i0,
+                                            int64_t i1, unsigned char* stage, F&& f) {
+  if (i0 >= i1) return;  // i0 = n need not be a multiple of 32
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t nw = blockDim.x >> 5, end = (i1 + 31) >> 5;
+  int64_t ls = (i0 >> 5) + wid;
+  if (ls >= end) return;
+  unsigned char* wbuf = stage + wid * kWarpStage;
+  const uint2* desc = a.sl_desc + s0;
+  const uint32_t* tinfo = a.sl_tinfo + s0;
+  uint2 d0 = __ldg(desc + ls), d1 = __ldg(desc + ls + 1);
+  uint32_t info = __ldg(tinfo + ls);
+  uint2 n0 = d1, n1 = d1;
+  uint32_t ninfo = 0u;
+  if (ls + nw < end) {
+    n0 = __ldg(desc + ls + nw);
+    n1 = __ldg(desc + ls + nw + 1);
+    ninfo = __ldg(tinfo + ls + nw);
+  }
+  if (stageable(d0, d1)) stage_slice<T>(wbuf, vals, a.sl_ibuf, d0, d1, lane);
+  cp_async_commit();
+  int b = 0;
+  for (;;) {
+    const bool more = ls + nw < end;
+    // the next slice's copy goes out before this one is summed
+    if (more && stageable(n0, n1)) stage_slice<T>(wbuf + (b ^ 1) * kStageBuf, vals, a.sl_ibuf, n0, n1, lane);
+    cp_async_commit();
+    const int64_t lm = ls + 2 * nw;
+    uint2 m0 = n1, m1 = n1;
+    uint32_t minfo = 0u;
+    if (lm < end) {
+      m0 = __ldg(desc + lm);
+      m1 = __ldg(desc + lm + 1);
+      minfo = __ldg(tinfo + lm);
+    }
+    cp_async_wait<1>();  // this slice's copies (all but the group just issued)
+    __syncwarp();
+    const int64_t row = (ls << 5) + lane;
+    const bool valid = row < i1;
+    T sum;
+    if (stageable(d0, d1)) {
+      const unsigned char* cur = wbuf + b * kStageBuf;
+      sum = slice_sum<T, true>(d0, d1, info, reinterpret_cast<const T*>(cur) + lane,
+                               reinterpret_cast<const uint32_t*>(cur + kStageValBytes) + lane, a.sl_tabs, x + row,
+                               valid, lane);
+    } else {
+      sum = slice_sum<T, true>(d0, d1, info, vals + d0.x + lane, a.sl_ibuf + d0.y + lane, a.sl_tabs, x + row, valid,
+                               lane);
+    }
+    if (valid) f(row, sum);
+    __syncwarp();  // buffer b is read by every lane before it is refilled
+    if (!more) break;
+    ls += nw;
+    b ^= 1;
+    d0 = n0;
+    d1 = n1;
+    info = ninfo;
+    n0 = m0;
+    n1 = m1;
+    ninfo = minfo;
+  }
+  cp_async_wait<0>();
+}
+
 // Visit rows [i0, i1) of a system whose first row has global index ro: fv(v)
 // for every W-wide vector v (global vector index, 16-byte aligned) inside the
 // range, fs(i) for the ragged rows at either end.
@@ -120,8 +225,9 @@ __device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, FS&
 
 }  // namespace
 
-// MODE: 0 FP64 PCG, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG
-template <int MODE>
+// MODE: 0 FP64 PCG, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG;
+// SL: the SpMV and residual passes run on the sliced layout
+template <int MODE, bool SL>
 #ifndef RP_BATCH_MIN_BLOCKS
 #define RP_BATCH_MIN_BLOCKS 2  // CTAs of kBatchMaxThreads per SM the register budget must allow
 #endif
@@ -133,6 +239,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
   __shared__ double spart[2][kMaxPartials];
   __shared__ double swarp[kMaxPartials][32];
   __shared__ int s_next;
+  extern __shared__ __align__(128) unsigned char stage[];  // SL: kWarpStage per warp
   int parity = 0;
   const double tol = a.io->tol;
   const double* __restrict__ bufall = a.io->buf;
@@ -160,9 +267,18 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
     float* dinv32 = MIXED ? a.dinv32 + ro : nullptr;
     const double* b = ball + ro;
     double* x = xall + ro;
-    const int64_t chunk = (n + T - 1) / T;
+    constexpr bool sl = SL;
+    const int64_t s0 = sl ? a.sl_soff[s] : 0;
+    int64_t chunk = (n + T - 1) / T;
+    if (sl) chunk = (chunk + 31) & ~int64_t(31);
     const int64_t i0 = min((int64_t)me * chunk, n), i1 = min(i0 + chunk, n);
     const int tid = threadIdx.x, nth = blockDim.x;
+    // A x for rows [i0, i1) of this CTA, f(i, (A x)_i) for each
+    auto spmv64 = [&](const double* xv, auto&& f) {
+      if (sl) spmv_slices<double>(a, a.sl_vals, s0, xv, i0, i1, stage, f);
+      else
+        for (int64_t i = i0 + tid; i < i1; i += nth) f(i, row_dot_coherent<double>(rp, col, vals, xv, i));
+    };
 
     // value update of this CTA's rows (Sec. 3 update procedure) and the Jacobi diagonal
     for (int64_t pp = rp[i0] + tid; pp < rp[i1]; pp += nth) {
@@ -174,6 +290,16 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
       const double d = buf[i];  // diagonal block leads the system's buffer
       dinv[i] = 1.0 / d;
       if (MIXED) dinv32[i] = 1.0f / (float)d;
+    }
+    if (sl && i0 < i1) {
+      // this CTA's slices, padding included (zero values)
+      const int64_t e0 = __ldg(a.sl_desc + s0 + (i0 >> 5)).x, e1 = __ldg(a.sl_desc + s0 + ((i1 + 31) >> 5)).x;
+      for (int64_t e = e0 + tid; e < e1; e += nth) {
+        const int32_t pp = __ldg(a.sl_pos + e);
+        const double v = pp >= 0 ? buf[__ldg(a.src_of + pp)] : 0.0;
+        a.sl_vals[e] = v;
+        if (MIXED) a.sl_vals32[e] = (float)v;
+      }
     }
     __syncthreads();
 
@@ -188,20 +314,22 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
       for (;;) {
         // residual pass: r = b - A x (x = 0 on the first pass), p = z = D^-1 r
         double v3[3] = {0.0, 0.0, 0.0}, t3[3];
-        for (int64_t i = i0 + tid; i < i1; i += nth) {
-          double ri;
-          if (passes == 0) {
-            ri = b[i];
-            x[i] = 0.0;
-            v3[2] = fma(ri, ri, v3[2]);
-          } else {
-            ri = b[i] - row_dot_coherent<double>(rp, col, vals, x, i);
-          }
+        auto res_row = [&](int64_t i, double ri) {
           r[i] = ri;
           const double zi = dinv[i] * ri;
           p[i] = zi;
           v3[0] = fma(ri, zi, v3[0]);
           v3[1] = fma(ri, ri, v3[1]);
+        };
+        if (passes == 0) {
+          for (int64_t i = i0 + tid; i < i1; i += nth) {
+            const double ri = b[i];
+            x[i] = 0.0;
+            v3[2] = fma(ri, ri, v3[2]);
+            res_row(i, ri);
+          }
+        } else {
+          spmv64(x, [&](int64_t i, double axi) { res_row(i, b[i] - axi); });
         }
         team_sum<3>(v3, t3, cl, spart, swarp, parity);
         if (passes == 0) {
@@ -221,10 +349,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
         for (;;) {
           cl.sync();  // p of every row visible to the team
           double v1[1] = {0.0}, t1[1];
-          spmv_rows<double>(rp, col, vals, p, i0, i1, [&](int64_t i, double qi) {
+          auto qrow = [&](int64_t i, double qi) {
             q[i] = qi;
             v1[0] = fma(p[i], qi, v1[0]);
-          });
+          };
+          if (sl) spmv_slices<double>(a, a.sl_vals, s0, p, i0, i1, stage, qrow);
+          else spmv_rows<double>(rp, col, vals, p, i0, i1, qrow);
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; break; }
           const double alpha = rz / t1[0];
@@ -295,15 +425,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
         // FP64 residual pass with FP64 values; FP32 copy starts the inner solve
         double v4[4] = {0.0, 0.0, 0.0, 0.0}, t4[4];
         float rzf = 0.f, rr32f = 0.f;
-        for (int64_t i = i0 + tid; i < i1; i += nth) {
-          double ri;
-          if (passes == 0) {
-            ri = b[i];
-            x[i] = 0.0;
-            v4[2] = fma(ri, ri, v4[2]);
-          } else {
-            ri = b[i] - row_dot_coherent<double>(rp, col, vals, x, i);
-          }
+        auto res_row = [&](int64_t i, double ri) {
           const float r32 = (float)ri;
           r[i] = r32;
           d[i] = 0.f;
@@ -312,6 +434,16 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
           rzf = fmaf(r32, z32, rzf);
           rr32f = fmaf(r32, r32, rr32f);
           v4[1] = fma(ri, ri, v4[1]);
+        };
+        if (passes == 0) {
+          for (int64_t i = i0 + tid; i < i1; i += nth) {
+            const double ri = b[i];
+            x[i] = 0.0;
+            v4[2] = fma(ri, ri, v4[2]);
+            res_row(i, ri);
+          }
+        } else {
+          spmv64(x, [&](int64_t i, double axi) { res_row(i, b[i] - axi); });
         }
         v4[0] = rzf;
         v4[3] = rr32f;
@@ -341,10 +473,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
         for (;;) {
           cl.sync();
           float acc = 0.f;
-          spmv_rows<float>(rp, col, vals32, p, i0, i1, [&](int64_t i, float qi) {
+          auto qrow = [&](int64_t i, float qi) {
             q[i] = qi;
             acc = fmaf(p[i], qi, acc);
-          });
+          };
+          if (sl) spmv_slices<float>(a, a.sl_vals32, s0, p, i0, i1, stage, qrow);
+          else spmv_rows<float>(rp, col, vals32, p, i0, i1, qrow);
           double v1[1] = {(double)acc}, t1[1];
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; broke = true; break; }
@@ -453,18 +587,22 @@ rp_status balloc(T** p, int64_t count) {
   return RP_OK;
 }
 
-void* batch_kernel(int mode) {
-  return mode == 2 ? (void*)k_batch<2> : mode == 1 ? (void*)k_batch<1> : (void*)k_batch<0>;
+void* batch_kernel(int mode, bool sl) {
+  if (sl) return mode == 2 ? (void*)k_batch<2, true> : mode == 1 ? (void*)k_batch<1, true> : (void*)k_batch<0, true>;
+  return mode == 2 ? (void*)k_batch<2, false> : mode == 1 ? (void*)k_batch<1, false> : (void*)k_batch<0, false>;
 }
 
 rp_status launch_config(rp_handle* h, int mode, int cluster, int threads, cudaLaunchConfig_t* cfg,
                         cudaLaunchAttribute* attr, int* n_clusters) {
-  void* fn = batch_kernel(mode);
+  const bool sl = h->batch_args.sl_desc != nullptr;
+  void* fn = batch_kernel(mode, sl);
   if (cluster > 8) RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  const int smem = sl ? (threads / 32) * kWarpStage : 0;
+  RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   *cfg = cudaLaunchConfig_t{};
   cfg->blockDim = dim3((unsigned)threads);
   cfg->gridDim = dim3((unsigned)cluster);
-  cfg->dynamicSmemBytes = 0;
+  cfg->dynamicSmemBytes = (size_t)smem;
   attr->id = cudaLaunchAttributeClusterDimension;
   attr->val.clusterDim.x = (unsigned)cluster;
   attr->val.clusterDim.y = 1;
@@ -492,9 +630,8 @@ rp_status build_batch_graph(rp_handle* h, int mode, int cluster, int threads, cu
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(h->batch_queue, 0, sizeof(unsigned int), cs);
-    if (mode == 2) cudaLaunchKernelEx(&cfg, k_batch<2>, ba);
-    else if (mode == 1) cudaLaunchKernelEx(&cfg, k_batch<1>, ba);
-    else cudaLaunchKernelEx(&cfg, k_batch<0>, ba);
+    void* args[] = {&ba};
+    cudaLaunchKernelExC(&cfg, batch_kernel(mode, ba.sl_desc != nullptr), args);
     e = cudaStreamEndCapture(cs, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
@@ -514,6 +651,7 @@ rp_status batch_prepare(rp_handle* h) {
   if (h->n_parts != h->k) return fail(RP_EINVAL, "batched solves need one system per part (n_parts == k)");
   if (h->nl_nnz != 0) return fail(RP_EINVAL, "batched systems must be independent (no processor interfaces)");
   const int ns = h->n_parts;
+  if (h->sl_slices == 0) RP_TRY(build_sliced(h, 0, true));  // every system sliced (when all fit)
   std::vector<int32_t> order(ns);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -564,6 +702,15 @@ rp_status batch_prepare(rp_handle* h) {
   a.max_outer = h->opts.max_outer;
   a.inner_tol = h->opts.inner_tol;
   a.ru_delta = h->opts.ru_delta > 0.0 ? h->opts.ru_delta : h->opts.inner_tol;
+  const bool sl = h->sl_slices > 0;
+  a.sl_soff = sl ? h->sl_part_soff : nullptr;
+  a.sl_desc = sl ? h->sl_desc : nullptr;
+  a.sl_tinfo = sl ? h->sl_tinfo : nullptr;
+  a.sl_tabs = sl ? h->sl_tabs : nullptr;
+  a.sl_ibuf = sl ? reinterpret_cast<const uint32_t*>(h->sl_ibuf) : nullptr;
+  a.sl_pos = sl ? h->sl_pos : nullptr;
+  a.sl_vals = sl ? h->sl_vals : nullptr;
+  a.sl_vals32 = sl ? h->sl_vals32 : nullptr;
   h->batch_ready = true;
   return RP_OK;
 }

@@ -392,7 +392,7 @@ struct BsLaunch {
 };
 void bs_inner(const rp_handle* h, BsLaunch (&k)[5]) {
   const BsState* b = h->bs;
-  const bool sl = h->sl_slices > 0;
+  const bool sl = h->sl_slices > 0 && h->n_parts == 1;  // as sliced64
   const int gs = sl ? b->grid_sl : h->grid, ts = sl ? kSlThreads : kThreads, ms = sl ? SlStage<double>::kSmem : 0;
   k[0] = {(void*)k_bs_p, b->grid_vec, kThreads, 0};
   k[1] = {sl ? (void*)k_bs_spmv_sl<1> : (void*)k_bs_spmv<1>, gs, ts, ms};

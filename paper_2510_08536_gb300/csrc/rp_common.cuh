@@ -187,6 +187,16 @@ struct BatchArgs {
   int32_t max_iter, max_restarts, max_outer;
   double inner_tol;
   double ru_delta;
+  // sliced layout of every system (sl_desc null: the SpMV runs on CSR); the
+  // kernel writes each system's sliced values from the buffer
+  const int64_t* sl_soff;  // [n_sys+1] first slice of each system
+  const uint2* sl_desc;
+  const uint32_t* sl_tinfo;
+  const int32_t* sl_tabs;
+  const uint32_t* sl_ibuf;
+  const int32_t* sl_pos;
+  double* sl_vals;
+  float* sl_vals32;
 };
 
 }  // namespace rp
@@ -245,11 +255,13 @@ struct rp_handle {
   float* dinv32 = nullptr;    // n
   double* dinvT = nullptr;
 
-  // sliced layout (n_parts == 1, built when every slice fits; see Sliced)
+  // sliced layout (n_parts == 1, or every system of a batch handle; built when
+  // every slice fits; see Sliced)
   int64_t sl_slices = 0;     // 0: the iteration runs on the CSR arrays
   int64_t sl_entries = 0;    // padded entries (32 per slice and width unit)
   int64_t sl_ibuf_len = 0;   // index words
   int64_t sl_tabs_len = 0;   // int32 words of the distinct tables
+  int64_t* sl_part_soff = nullptr;  // [n_parts + 1] first slice of each part (device)
   uint2* sl_desc = nullptr;  // [sl_slices + 1]
   uint32_t* sl_tinfo = nullptr;  // [sl_slices]
   int32_t* sl_tabs = nullptr;
@@ -304,7 +316,7 @@ inline int grid_for(const rp_handle* h, int64_t n) {
 }
 
 rp_status ensure_solver_buffers(rp_handle* h);
-rp_status build_sliced(rp_handle* h, cudaStream_t s);  // after the CSR map
+rp_status build_sliced(rp_handle* h, cudaStream_t s, bool parts = false);  // after the CSR map; parts: every part sliced (batch handles)
 rp_status fill_sliced(rp_handle* h, cudaStream_t s);   // after every value update
 void free_sliced(rp_handle* h);
 void free_bicgstab(rp_handle* h);

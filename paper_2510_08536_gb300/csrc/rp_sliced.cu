@@ -34,6 +34,31 @@ namespace {
 
 constexpr int kWarpsPerBlock = kThreads / 32;
 
+// The parts whose rows are sliced (one part: the merged matrix; a batch
+// handle: every system): slices, rows and CSR entries of part p start at
+// soff[p], roff[p], noff[p]; its CSR rows at row_ptr + roff[p] + p count from
+// 0 and its columns are part-local.
+struct SlParts {
+  int32_t P;
+  const int64_t* soff;
+  const int64_t* roff;
+  const int64_t* noff;
+  const int32_t* row_ptr;
+  const int32_t* col;
+};
+
+// Slice s seen from its part: that part's CSR arrays, rows and local slice index.
+struct SlSlice {
+  const int32_t* rp;
+  const int32_t* col;
+  int64_t n, s, nnz0;
+};
+__device__ __forceinline__ SlSlice slice_of(const SlParts& q, int64_t s) {
+  const int p = q.P > 1 ? find_rank(q.soff, q.P, s) : 0;
+  const int64_t r0 = q.roff[p], n0 = q.noff[p];
+  return SlSlice{q.row_ptr + r0 + p, q.col + n0, q.roff[p + 1] - r0, s - q.soff[p], n0};
+}
+
 int slice_grid(const rp_handle* h, int64_t slices) {
   int64_t want = (slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
   int64_t cap = (int64_t)h->num_sms * kBlocksPerSm;
@@ -87,19 +112,19 @@ __device__ int slice_table(const int32_t* __restrict__ row_ptr, const int32_t* _
 // pass 1: width L_s and table length D_s of every slice; err bit 1: a
 // row longer than kSliceMaxWidth, bit 2: a table longer than kSliceMaxDict
 __global__ void __launch_bounds__(kThreads)
-    k_slice_count(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n, int64_t S,
-                  uint8_t* __restrict__ width, uint16_t* __restrict__ tlen, int32_t* err) {
+    k_slice_count(SlParts q, int64_t S, uint8_t* __restrict__ width, uint16_t* __restrict__ tlen, int32_t* err) {
   __shared__ int32_t sdict[kWarpsPerBlock][kSliceMaxDict];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + w; s < S; s += (int64_t)gridDim.x * kWarpsPerBlock) {
-    const int64_t row = s * kSliceRows + lane;
-    const int len = row < n ? (int)(row_ptr[row + 1] - row_ptr[row]) : 0;
+    const SlSlice v = slice_of(q, s);
+    const int64_t row = v.s * kSliceRows + lane;
+    const int len = row < v.n ? (int)(v.rp[row + 1] - v.rp[row]) : 0;
     const int L = __reduce_max_sync(0xffffffffu, len);
     if (L > kSliceMaxWidth) {
       if (lane == 0) atomicOr(err, 1);
       continue;
     }
-    const int D = slice_table(row_ptr, col, n, s, L, sdict[w], [](int, bool, int, int) {});
+    const int D = slice_table(v.rp, v.col, v.n, v.s, L, sdict[w], [](int, bool, int, int) {});
     if (D < 0) {
       if (lane == 0) atomicOr(err, 2);
       continue;
@@ -113,12 +138,13 @@ __global__ void __launch_bounds__(kThreads)
 
 // pass 2: every slice's table into the scratch array at toff[s]
 __global__ void __launch_bounds__(kThreads)
-    k_slice_tables(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n, int64_t S,
-                   const uint8_t* __restrict__ width, const int64_t* __restrict__ toff, int32_t* __restrict__ tab) {
+    k_slice_tables(SlParts q, int64_t S, const uint8_t* __restrict__ width, const int64_t* __restrict__ toff,
+                   int32_t* __restrict__ tab) {
   __shared__ int32_t sdict[kWarpsPerBlock][kSliceMaxDict];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + w; s < S; s += (int64_t)gridDim.x * kWarpsPerBlock) {
-    const int D = slice_table(row_ptr, col, n, s, width[s], sdict[w], [](int, bool, int, int) {});
+    const SlSlice v = slice_of(q, s);
+    const int D = slice_table(v.rp, v.col, v.n, v.s, width[s], sdict[w], [](int, bool, int, int) {});
     __syncwarp();
     for (int j = lane; j < D; j += 32) tab[toff[s] + j] = sdict[w][j];
   }
@@ -128,9 +154,8 @@ __global__ void __launch_bounds__(kThreads)
 // bit 4: a slice's size differs from the earlier passes (cannot happen: all
 // passes are deterministic)
 __global__ void __launch_bounds__(kThreads)
-    k_slice_fill(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n, int64_t S,
-                 const uint2* __restrict__ desc, const uint32_t* __restrict__ tinfo, int32_t* __restrict__ ibuf,
-                 int32_t* __restrict__ pos, int32_t* err) {
+    k_slice_fill(SlParts q, int64_t S, const uint2* __restrict__ desc, const uint32_t* __restrict__ tinfo,
+                 int32_t* __restrict__ ibuf, int32_t* __restrict__ pos, int32_t* err) {
   __shared__ int32_t sdict[kWarpsPerBlock][kSliceMaxDict];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int32_t* dict = sdict[w];
@@ -144,17 +169,18 @@ __global__ void __launch_bounds__(kThreads)
       if (lane == 0) atomicOr(err, 4);
       continue;
     }
-    const int64_t row = s * kSliceRows + lane;
-    const int64_t rs = row < n ? row_ptr[row] : 0;
+    const SlSlice v = slice_of(q, s);
+    const int64_t row = v.s * kSliceRows + lane;
+    const int64_t rs = row < v.n ? v.rp[row] : 0;
     uint32_t* iw = reinterpret_cast<uint32_t*>(ibuf + d0.y);
     int32_t* ps = pos + d0.x;
     uint32_t word = 0;
-    const int D = slice_table(row_ptr, col, n, s, L, dict, [&](int k, bool has, int id, int cnt) {
+    const int D = slice_table(v.rp, v.col, v.n, v.s, L, dict, [&](int k, bool has, int id, int cnt) {
       if (!has) {
         // padding: the diagonal's index (a row < n stored its diagonal at an
         // earlier k, so offset 0 is in the table); zero value, in-range column
         id = 0;
-        if (row < n)
+        if (row < v.n)
           for (int j = 0; j < cnt; ++j)
             if (dict[j] == 0) {
               id = j;
@@ -166,7 +192,7 @@ __global__ void __launch_bounds__(kThreads)
         iw[(k / per) * kSliceRows + lane] = word;
         word = 0;
       }
-      ps[k * kSliceRows + lane] = has ? (int32_t)(rs + k) : -1;
+      ps[k * kSliceRows + lane] = has ? (int32_t)(v.nnz0 + rs + k) : -1;
     });
     if ((D <= 16) != w4 && lane == 0) atomicOr(err, 4);
   }
@@ -215,9 +241,11 @@ struct Tmp {
 }  // namespace
 
 void free_sliced(rp_handle* h) {
-  void* ptrs[] = {h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_pos, h->sl_vals, h->sl_vals32};
+  void* ptrs[] = {h->sl_part_soff, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_pos, h->sl_vals,
+                  h->sl_vals32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  h->sl_part_soff = nullptr;
   h->sl_desc = nullptr;
   h->sl_tinfo = nullptr;
   h->sl_tabs = nullptr;
@@ -228,10 +256,19 @@ void free_sliced(rp_handle* h) {
   h->sl_slices = h->sl_entries = h->sl_ibuf_len = h->sl_tabs_len = 0;
 }
 
-rp_status build_sliced(rp_handle* h, cudaStream_t st) {
-  if (h->n_parts != 1 || h->n == 0 || h->opts.layout == RP_LAYOUT_CSR) return RP_OK;
-  const int64_t n = h->n, S = (n + kSliceRows - 1) / kSliceRows;
+rp_status build_sliced(rp_handle* h, cudaStream_t st, bool parts) {
+  if ((h->n_parts != 1 && !parts) || h->n == 0 || h->opts.layout == RP_LAYOUT_CSR) return RP_OK;
+  const int P = h->n_parts;
+  std::vector<int64_t> soff(P + 1, 0);
+  for (int p = 0; p < P; ++p)
+    soff[p + 1] = soff[p] + (h->part_row_off[p + 1] - h->part_row_off[p] + kSliceRows - 1) / kSliceRows;
+  const int64_t S = soff[P];
+  if (S == 0) return RP_OK;
   Tmp tmp;
+  int64_t* dsoff;
+  RP_TRY(tmp.alloc(&dsoff, P + 1));
+  RP_TRY_CUDA(cudaMemcpyAsync(dsoff, soff.data(), 8 * (P + 1), cudaMemcpyHostToDevice, st));
+  const SlParts q{P, dsoff, h->d_part_row_off, h->d_part_nnz_off, h->row_ptr, h->col_idx};
   uint8_t* width;
   uint16_t* tlen;
   int32_t* err;
@@ -240,7 +277,7 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
   RP_TRY(tmp.alloc(&err, 1));
   RP_TRY_CUDA(cudaMemsetAsync(err, 0, 4, st));
   const int g = slice_grid(h, S);
-  k_slice_count<<<g, kThreads, 0, st>>>(h->row_ptr, h->col_idx, n, S, width, tlen, err);
+  k_slice_count<<<g, kThreads, 0, st>>>(q, S, width, tlen, err);
   RP_TRY_CUDA(cudaGetLastError());
   std::vector<uint8_t> hw(S);
   std::vector<uint16_t> ht(S);
@@ -259,7 +296,7 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
   RP_TRY(tmp.alloc(&dtoff, S + 1));
   RP_TRY(tmp.alloc(&dtab, toff[S] + 1));
   RP_TRY_CUDA(cudaMemcpyAsync(dtoff, toff.data(), 8 * (S + 1), cudaMemcpyHostToDevice, st));
-  k_slice_tables<<<g, kThreads, 0, st>>>(h->row_ptr, h->col_idx, n, S, width, dtoff, dtab);
+  k_slice_tables<<<g, kThreads, 0, st>>>(q, S, width, dtoff, dtab);
   RP_TRY_CUDA(cudaGetLastError());
   std::vector<int32_t> htab(toff[S]);
   RP_TRY_CUDA(cudaMemcpyAsync(htab.data(), dtab, 4 * toff[S], cudaMemcpyDeviceToHost, st));
@@ -302,6 +339,7 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
     rp_status s_ = (call);           \
     if (s_ != RP_OK) return undo(s_); \
   } while (0)
+  SL_TRY(salloc(&h->sl_part_soff, P + 1));
   SL_TRY(salloc(&h->sl_desc, S + 1 + kSliceDescPad));
   SL_TRY(salloc(&h->sl_tinfo, S + kSliceDescPad));
   SL_TRY(salloc(&h->sl_tabs, (int64_t)tabs.size()));
@@ -316,14 +354,15 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
   };
   RP_TRY(cu(cudaMemcpyAsync(h->sl_desc, desc.data(), sizeof(uint2) * desc.size(), cudaMemcpyHostToDevice, st),
             "sliced descriptor upload"));
+  RP_TRY(cu(cudaMemcpyAsync(h->sl_part_soff, soff.data(), 8 * (P + 1), cudaMemcpyHostToDevice, st),
+            "sliced part offsets upload"));
   RP_TRY(cu(cudaMemcpyAsync(h->sl_tinfo, tinfo.data(), 4 * tinfo.size(), cudaMemcpyHostToDevice, st),
             "sliced table reference upload"));
   RP_TRY(cu(cudaMemcpyAsync(h->sl_tabs, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, st),
             "sliced table upload"));
   RP_TRY(cu(cudaMemsetAsync(h->sl_vals, 0, 8 * x, st), "sliced value clear"));
   if (h->sl_vals32) RP_TRY(cu(cudaMemsetAsync(h->sl_vals32, 0, 4 * x, st), "sliced value clear"));
-  k_slice_fill<<<g, kThreads, 0, st>>>(h->row_ptr, h->col_idx, n, S, h->sl_desc, h->sl_tinfo, h->sl_ibuf,
-                                       h->sl_pos, err);
+  k_slice_fill<<<g, kThreads, 0, st>>>(q, S, h->sl_desc, h->sl_tinfo, h->sl_ibuf, h->sl_pos, err);
   RP_TRY(cu(cudaGetLastError(), "k_slice_fill"));
   RP_TRY(cu(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st), "error readback"));
   RP_TRY(cu(cudaStreamSynchronize(st), "sliced layout build"));

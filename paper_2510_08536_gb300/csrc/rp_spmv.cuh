@@ -56,13 +56,15 @@ __device__ __forceinline__ T row_dot_any(const Parts<T>& P, const int32_t* __res
   return P.n > 1 ? row_dot_parts<T>(P, row_ptr, col, vals, x, i) : row_dot<T>(row_ptr, col, vals, x, i);
 }
 
+// The sliced layout for the single-matrix iteration (a batch handle's per-system
+// layout is only for the batched kernel; GPU parts iterate over CSR).
 inline Sliced<double> sliced64(const rp_handle* h, const double* vals) {
-  if (h->sl_slices == 0 || vals != h->vals) return Sliced<double>{};  // e.g. transposed values
+  if (h->sl_slices == 0 || h->n_parts != 1 || vals != h->vals) return Sliced<double>{};  // e.g. transposed values
   return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_vals,
                         h->opts.spin_limit};
 }
 inline Sliced<float> sliced32(const rp_handle* h) {
-  if (h->sl_slices == 0 || !h->sl_vals32) return Sliced<float>{};
+  if (h->sl_slices == 0 || h->n_parts != 1 || !h->sl_vals32) return Sliced<float>{};
   return Sliced<float>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_vals32,
                        h->opts.spin_limit};
 }
@@ -177,6 +179,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
+// Asynchronous prefetch of [src, src + bytes) into L2 (no completion to wait
+// for); src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // How a slice's offset indices are read: 4-bit indices into a table of at
 // most 16 offsets held in tv by both half-warps (lane & 15), looked up by a
 // shuffle of width 16 (the source lane is taken modulo 16, so a shifted word
@@ -192,11 +200,19 @@ __device__ __forceinline__ int slice_offset(uint32_t wd, int e, int32_t tv, cons
   return __ldg(tab + ((wd >> (8 * e)) & 255u));
 }
 
+// A gather from x: read-only path, or (COH) a plain load for a vector that the
+// same kernel writes.
+template <bool COH, typename T>
+__device__ __forceinline__ T xload(const T* p) {
+  if (COH) return *p;
+  return __ldg(p);
+}
+
 // Sum of one row of a slice, L entries: values at v[32 k] (lane applied),
 // index words at iw[32 g] (lane applied); the same fused multiply-adds in the
 // same order as row_dot over the row's CSR entries. Lanes without a row
 // (valid false) run the shuffles but load nothing.
-template <typename T, int MODE, int L>
+template <typename T, int MODE, int L, bool COH = false>
 __device__ __forceinline__ T slice_row_exact(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab,
                                              const T* x, bool valid) {
   constexpr int PER = MODE == kIdx4 ? 8 : 4;
@@ -208,23 +224,23 @@ __device__ __forceinline__ T slice_row_exact(const T* v, const uint32_t* iw, int
 #pragma unroll
   for (int k = 0; k < L; ++k) {
     const int off = slice_offset<MODE>(k < PER ? w0 : w1, k % PER, tv, tab);
-    if (valid) sum = fma(vv[k], __ldg(x + off), sum);
+    if (valid) sum = fma(vv[k], xload<COH>(x + off), sum);
   }
   return sum;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool COH = false>
 __device__ __forceinline__ T slice_row(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab, const T* x,
                                        bool valid, int L) {
   switch (L) {
-    case 1: return slice_row_exact<T, MODE, 1>(v, iw, tv, tab, x, valid);
-    case 2: return slice_row_exact<T, MODE, 2>(v, iw, tv, tab, x, valid);
-    case 3: return slice_row_exact<T, MODE, 3>(v, iw, tv, tab, x, valid);
-    case 4: return slice_row_exact<T, MODE, 4>(v, iw, tv, tab, x, valid);
-    case 5: return slice_row_exact<T, MODE, 5>(v, iw, tv, tab, x, valid);
-    case 6: return slice_row_exact<T, MODE, 6>(v, iw, tv, tab, x, valid);
-    case 7: return slice_row_exact<T, MODE, 7>(v, iw, tv, tab, x, valid);
-    case 8: return slice_row_exact<T, MODE, 8>(v, iw, tv, tab, x, valid);
+    case 1: return slice_row_exact<T, MODE, 1, COH>(v, iw, tv, tab, x, valid);
+    case 2: return slice_row_exact<T, MODE, 2, COH>(v, iw, tv, tab, x, valid);
+    case 3: return slice_row_exact<T, MODE, 3, COH>(v, iw, tv, tab, x, valid);
+    case 4: return slice_row_exact<T, MODE, 4, COH>(v, iw, tv, tab, x, valid);
+    case 5: return slice_row_exact<T, MODE, 5, COH>(v, iw, tv, tab, x, valid);
+    case 6: return slice_row_exact<T, MODE, 6, COH>(v, iw, tv, tab, x, valid);
+    case 7: return slice_row_exact<T, MODE, 7, COH>(v, iw, tv, tab, x, valid);
+    case 8: return slice_row_exact<T, MODE, 8, COH>(v, iw, tv, tab, x, valid);
     default: break;
   }
   constexpr int PER = MODE == kIdx4 ? 8 : 4;
@@ -235,7 +251,7 @@ __device__ __forceinline__ T slice_row(const T* v, const uint32_t* iw, int32_t t
     for (int e = 0; e < PER; ++e)
       if (PER * g + e < L) {
         const int off = slice_offset<MODE>(wd, e, tv, tab);
-        if (valid) sum = fma(v[(PER * g + e) * kSliceRows], __ldg(x + off), sum);
+        if (valid) sum = fma(v[(PER * g + e) * kSliceRows], xload<COH>(x + off), sum);
       }
   }
   return sum;
@@ -243,15 +259,15 @@ __device__ __forceinline__ T slice_row(const T* v, const uint32_t* iw, int32_t t
 
 // One slice: descriptor pair (d0, d1), table reference info, values v and
 // index words iw (shared memory or global, lane applied), tables tabs (global),
-// gathers from x relative to the lane's row.
-template <typename T>
+// gathers from x relative to the lane's row (COH: plain loads, see xload).
+template <typename T, bool COH = false>
 __device__ __forceinline__ T slice_sum(uint2 d0, uint2 d1, uint32_t info, const T* v, const uint32_t* iw,
                                        const int32_t* __restrict__ tabs, const T* x, bool valid, int lane) {
   const int L = (int)((d1.x - d0.x) >> 5);
   const int32_t* tab = tabs + (info & ~kSliceW4);
-  if (info & kSliceW4) return slice_row<T, kIdx4>(v, iw, __ldg(tab + (lane & 15)), tab, x, valid, L);
-  if (__ldg(tab - 1) <= 32) return slice_row<T, kIdx8Shfl>(v, iw, __ldg(tab + lane), tab, x, valid, L);
-  return slice_row<T, kIdx8Glob>(v, iw, 0, tab, x, valid, L);
+  if (info & kSliceW4) return slice_row<T, kIdx4, COH>(v, iw, __ldg(tab + (lane & 15)), tab, x, valid, L);
+  if (__ldg(tab - 1) <= 32) return slice_row<T, kIdx8Shfl, COH>(v, iw, __ldg(tab + lane), tab, x, valid, L);
+  return slice_row<T, kIdx8Glob, COH>(v, iw, 0, tab, x, valid, L);
 }
 
 template <typename T, class Epi>

@@ -13,6 +13,8 @@ import torch
 from oracle import repart_oracle as O
 from paper_2510_08536_gb300 import build, repart, synth
 
+from gpu_util import check_layout
+
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
@@ -66,10 +68,46 @@ def test_batch_maps_and_values_bit_exact(batch):
     h.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ru"])
-def test_batch_solves_match_oracle(batch, precision):
+def test_batch_sliced_layout_per_system(batch):
+    """Every system gets its own 32-row slices (part-local rows and columns,
+    global CSR positions); the kernel writes their values from the buffer."""
     B, stg, b, refs = batch
     h = repart.batch_build(B.systems)
+    x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
+    repart.batch_update_solve(h, _t(stg), _t(b), x, tol=1e-9, precision="mixed_ru")
+    view = repart.get_sliced_view(h)
+    assert view is not None, "layout not built"
+    soff = np.cumsum([0] + [(ref["n"] + 31) // 32 for ref in refs])
+    assert view["n_slices"] == soff[-1]
+    desc = view["desc"].cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    pos = view["pos"].cpu().numpy().astype(np.int64)
+    vals, vals32 = view["vals"].cpu().numpy(), view["vals32"].cpu().numpy()
+    nnz0 = 0
+    for s, ref in enumerate(refs):
+        s0, s1 = soff[s], soff[s + 1]
+        e0, e1 = desc[s0, 0], desc[s1, 0]
+        local = np.where(pos >= 0, pos - nnz0, -1)
+        sub = dict(view, n_slices=int(s1 - s0), n_entries=int(e1 - e0), desc=view["desc"][2 * s0:2 * (s1 + 1)],
+                   tinfo=view["tinfo"][s0:s1], pos=torch.from_numpy(local))
+        check_layout(sub, ref["map"], ref["n"])
+        lp = local[e0:e1]
+        want = np.where(lp >= 0, ref["vals"][np.maximum(lp, 0)], 0.0)
+        np.testing.assert_array_equal(vals[e0:e1], want, err_msg=str(s))
+        np.testing.assert_array_equal(vals32[e0:e1], want.astype(np.float32), err_msg=str(s))
+        nnz0 += ref["vals"].size
+    h.close()
+
+
+@pytest.mark.parametrize("layout", ["sliced", "csr"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ru"])
+def test_batch_solves_match_oracle(batch, precision, layout):
+    B, stg, b, refs = batch
+    if layout == "csr":
+        h = repart.batch_build(B.systems, layout=repart.RP_LAYOUT_CSR)
+        assert repart.get_sliced_view(h) is None
+    else:
+        h = repart.batch_build(B.systems)
+        assert repart.get_sliced_view(h) is not None
     x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
     infos = repart.batch_update_solve(h, _t(stg), _t(b), x, tol=1e-9, precision=precision)
     xs = x.cpu().numpy()
