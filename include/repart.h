@@ -67,11 +67,12 @@ enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1, RP_MEM_HOST_DIRECT = 2 };
  * the search direction continues (p = z + beta p). */
 enum { RP_FP64 = 0, RP_MIXED = 1, RP_MIXED_RU = 2 };
 /* Matrix layout of the PCG iteration (rp_options.layout). RP_LAYOUT_AUTO:
- * the sliced layout (see rp_get_sliced_view) when the matrix is one part
- * (or, for the batched solve, every system is one), no row has more than 32
+ * the sliced layout (see rp_get_sliced_view; every part, or every system of
+ * a batched handle, in slices of its own) when no row has more than 32
  * entries and no 32-row slice more than 256 distinct column offsets; else
  * CSR. RP_LAYOUT_CSR: always CSR. Both give the same products row by row
- * (same entries, same order). */
+ * (same entries, same order; with several parts the non-local entries of a
+ * row follow its local ones, as in the CSR iteration). */
 enum { RP_LAYOUT_AUTO = 0, RP_LAYOUT_CSR = 1 };
 /* Preconditioner of the PCG solves (rp_options.precond). RP_PRECOND_JACOBI:
  * z = D^-1 r. RP_PRECOND_LINE: block-Jacobi over blocks of 32 consecutive
@@ -223,8 +224,9 @@ rp_status rp_spmv_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_
 /* The sliced layout the PCG iteration multiplies with (the paper has no
  * counterpart: it is this library's device format of the merged matrix, built
  * once next to the CSR map by rp_build_repartition and refilled from the CSR
- * values by every value update). Rows in slices of 32 (n_slices = ceil(n/32),
- * 0 when the layout is not in use), one row per lane. Slice s: desc[2s] = x_s,
+ * values by every value update). Rows in slices of 32 (n_slices = ceil(n/32)
+ * for one part, the sum of ceil(n_p/32) over parts; 0 when the layout is not
+ * in use), one row per lane. Slice s: desc[2s] = x_s,
  * desc[2s+1] = y_s (uint32 pairs; desc[2 n_slices], desc[2 n_slices + 1]
  * close the last slice); L_s = (x_{s+1} - x_s) / 32 entries per row, the
  * longest row of the slice, shorter rows padded with zero values; values of
@@ -235,15 +237,18 @@ rp_status rp_spmv_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_
  * (D <= 16): 4-bit offset indices, entry 8 g + e of lane j in bits 4e..4e+3
  * of ibuf[y_s + 32 g + j]; w4 = 0: 8-bit indices, entry 4 g + e in byte e of
  * ibuf[y_s + 32 g + j]. pos[x_s + 32 k + j] is the CSR position of that entry,
- * -1 for padding. Entry k of a row is its k-th CSR entry. A batched handle
- * (rp_batch_build, several parts) holds the slices of every system one after
- * the other, system p's ceil(n_p / 32) slices after those of systems < p:
- * there rows and column offsets are those of the system's own CSR matrix
- * (rp_get_part_map) and pos holds positions in the handle's value array
- * (rp_get_values); the batched kernel writes these values, the value update
- * of the merged handle's solve refills them too. Device views, owned by the
- * handle; n_entries counts padded entries, ibuf_len index words, tabs_len
- * table words. */
+ * -1 for padding. Entry k of a row is its k-th CSR entry. With several parts
+ * (n_parts > 1, and every batched handle: one part per system) the slices of
+ * every part follow one another, part p's ceil(n_p / 32) slices after those
+ * of parts < p; rows and column offsets are those of the part's local CSR
+ * matrix (rp_get_part_map), pos holds positions in the handle's value array
+ * (rp_get_values), and srow[2s] = the first merged row of slice s,
+ * srow[2s+1] = p << 6 | (rows of the part in the slice, at most 32); srow is
+ * NULL for one part (slice s holds rows 32 s ..). The non-local entries of a
+ * part stay in its non-local CSR. The batched kernel writes the sliced values
+ * itself; every value update refills them. Device views, owned by the handle;
+ * n_entries counts padded entries, ibuf_len index words, tabs_len table
+ * words. */
 typedef struct rp_sliced_view {
   int64_t n_slices, n_entries, ibuf_len, tabs_len;
   const uint32_t* desc;
@@ -253,6 +258,7 @@ typedef struct rp_sliced_view {
   const int32_t* pos;
   const double* vals;
   const float* vals32;
+  const int32_t* srow;
 } rp_sliced_view;
 rp_status rp_get_sliced_view(const rp_handle* h, rp_sliced_view* out);
 

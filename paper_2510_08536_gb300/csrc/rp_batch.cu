@@ -651,7 +651,7 @@ rp_status batch_prepare(rp_handle* h) {
   if (h->n_parts != h->k) return fail(RP_EINVAL, "batched solves need one system per part (n_parts == k)");
   if (h->nl_nnz != 0) return fail(RP_EINVAL, "batched systems must be independent (no processor interfaces)");
   const int ns = h->n_parts;
-  if (h->sl_slices == 0) RP_TRY(build_sliced(h, 0, true));  // every system sliced (when all fit)
+  if (h->sl_slices == 0) RP_TRY(build_sliced(h, 0));  // every system sliced (when all fit)
   std::vector<int32_t> order(ns);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {

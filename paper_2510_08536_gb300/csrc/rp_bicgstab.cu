@@ -210,16 +210,16 @@ __global__ void __launch_bounds__(kThreads) k_bs_spmv(BsArgs a) {
     spmv_csr_body<double>(a.n, a.parts, a.row_ptr, a.col, a.vals, a.shat, a.t, e);
   }
 }
-template <int WHICH>
+template <int WHICH, bool MP>
 __global__ void __launch_bounds__(kSlThreads, 5) k_bs_spmv_sl(BsArgs a) {
   BsCtl* c = a.c;
   if (c->stop || (WHICH == 2 && c->half)) return;
   if constexpr (WHICH == 1) {
     BsEpiV e{a.rhat, c, a.partials};
-    spmv_sl_body<double>(a.sl, a.n, a.phat, a.v, e);
+    spmv_sl_body<double, MP>(a.sl, a.parts, a.n, a.phat, a.v, e);
   } else {
     BsEpiT e{a.s, c, a.partials};
-    spmv_sl_body<double>(a.sl, a.n, a.shat, a.t, e);
+    spmv_sl_body<double, MP>(a.sl, a.parts, a.n, a.shat, a.t, e);
   }
 }
 
@@ -328,7 +328,7 @@ rp_status ensure_bs(rp_handle* h) {
     return (int)(want < 1 ? 1 : want < cap ? want : cap);
   };
   b->grid_vec = grid(resident_blocks((const void*)k_bs_xr, kThreads, 0));
-  b->grid_sl = grid(resident_blocks((const void*)k_bs_spmv_sl<2>, kSlThreads, SlStage<double>::kSmem));
+  b->grid_sl = grid(resident_blocks((const void*)k_bs_spmv_sl<2, false>, kSlThreads, SlStage<double>::kSmem));
   return RP_OK;
 }
 
@@ -392,12 +392,13 @@ struct BsLaunch {
 };
 void bs_inner(const rp_handle* h, BsLaunch (&k)[5]) {
   const BsState* b = h->bs;
-  const bool sl = h->sl_slices > 0 && h->n_parts == 1;  // as sliced64
+  const bool sl = h->sl_slices > 0;  // as sliced64
   const int gs = sl ? b->grid_sl : h->grid, ts = sl ? kSlThreads : kThreads, ms = sl ? SlStage<double>::kSmem : 0;
   k[0] = {(void*)k_bs_p, b->grid_vec, kThreads, 0};
-  k[1] = {sl ? (void*)k_bs_spmv_sl<1> : (void*)k_bs_spmv<1>, gs, ts, ms};
+  const bool mp = h->sl_srow != nullptr;
+  k[1] = {sl ? (mp ? (void*)k_bs_spmv_sl<1, true> : (void*)k_bs_spmv_sl<1, false>) : (void*)k_bs_spmv<1>, gs, ts, ms};
   k[2] = {(void*)k_bs_s, b->grid_vec, kThreads, 0};
-  k[3] = {sl ? (void*)k_bs_spmv_sl<2> : (void*)k_bs_spmv<2>, gs, ts, ms};
+  k[3] = {sl ? (mp ? (void*)k_bs_spmv_sl<2, true> : (void*)k_bs_spmv_sl<2, false>) : (void*)k_bs_spmv<2>, gs, ts, ms};
   k[4] = {(void*)k_bs_xr, b->grid_vec, kThreads, 0};
 }
 

@@ -129,6 +129,10 @@ struct Sliced {
   const int32_t* ibuf;
   const T* vals;
   int64_t spin;      // iteration limit of every shared-memory barrier wait
+  // several parts: per slice (first global row, part << 6 | rows of the part in
+  // it); the non-local entries of those rows follow in the part's CSR. nullptr:
+  // one part, slice s holds rows 32 s ..
+  const int2* srow = nullptr;
 };
 constexpr int kSliceDescPad = 8;  // bulk copies of descriptor runs may read past the end
 // Probe bound of the wait for a block's own bulk copies after another wait
@@ -140,6 +144,7 @@ constexpr int64_t kDrainProbes = int64_t(1) << 22;
 // fit on the SMs at once (by each kernel's register use), capped by the rows.
 struct IterGrid {
   int k1 = 1, k1s = 1, k2 = 1, k3 = 1;  // K1 on CSR, K1 on the sliced layout, K2, K3
+  int k1sm = 1;                         // K1 on the sliced layout of several parts
   int k2l = 1, k3l = 1;                 // K2, K3 with the line preconditioner
 };
 
@@ -255,13 +260,14 @@ struct rp_handle {
   float* dinv32 = nullptr;    // n
   double* dinvT = nullptr;
 
-  // sliced layout (n_parts == 1, or every system of a batch handle; built when
+  // sliced layout (every part's rows cut into their own slices; built when
   // every slice fits; see Sliced)
   int64_t sl_slices = 0;     // 0: the iteration runs on the CSR arrays
   int64_t sl_entries = 0;    // padded entries (32 per slice and width unit)
   int64_t sl_ibuf_len = 0;   // index words
   int64_t sl_tabs_len = 0;   // int32 words of the distinct tables
   int64_t* sl_part_soff = nullptr;  // [n_parts + 1] first slice of each part (device)
+  int2* sl_srow = nullptr;           // [sl_slices] first row, part << 6 | rows (n_parts > 1)
   uint2* sl_desc = nullptr;  // [sl_slices + 1]
   uint32_t* sl_tinfo = nullptr;  // [sl_slices]
   int32_t* sl_tabs = nullptr;
@@ -316,7 +322,7 @@ inline int grid_for(const rp_handle* h, int64_t n) {
 }
 
 rp_status ensure_solver_buffers(rp_handle* h);
-rp_status build_sliced(rp_handle* h, cudaStream_t s, bool parts = false);  // after the CSR map; parts: every part sliced (batch handles)
+rp_status build_sliced(rp_handle* h, cudaStream_t s);  // after the CSR map
 rp_status fill_sliced(rp_handle* h, cudaStream_t s);   // after every value update
 void free_sliced(rp_handle* h);
 void free_bicgstab(rp_handle* h);

@@ -1,5 +1,5 @@
-// Sliced layout of the merged matrix: the device format the PCG iteration
-// multiplies with when the matrix is one part (n_parts == 1).
+// Sliced layout of the merged matrix: the device format the iteration
+// multiplies with (every part's rows cut into slices of their own).
 //
 // The CSR arrays of the map stay the reference layout (the map, the value
 // update, residual passes, adjoint and gradients use them). For the
@@ -21,6 +21,7 @@
 // writes index words and the CSR position of every padded entry. The layout
 // is not built (the iteration keeps the CSR kernels) when a row has more than
 // 32 entries or a slice more than 256 distinct offsets.
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -241,11 +242,12 @@ struct Tmp {
 }  // namespace
 
 void free_sliced(rp_handle* h) {
-  void* ptrs[] = {h->sl_part_soff, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_pos, h->sl_vals,
-                  h->sl_vals32};
+  void* ptrs[] = {h->sl_part_soff, h->sl_srow, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_pos,
+                  h->sl_vals, h->sl_vals32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->sl_part_soff = nullptr;
+  h->sl_srow = nullptr;
   h->sl_desc = nullptr;
   h->sl_tinfo = nullptr;
   h->sl_tabs = nullptr;
@@ -256,8 +258,8 @@ void free_sliced(rp_handle* h) {
   h->sl_slices = h->sl_entries = h->sl_ibuf_len = h->sl_tabs_len = 0;
 }
 
-rp_status build_sliced(rp_handle* h, cudaStream_t st, bool parts) {
-  if ((h->n_parts != 1 && !parts) || h->n == 0 || h->opts.layout == RP_LAYOUT_CSR) return RP_OK;
+rp_status build_sliced(rp_handle* h, cudaStream_t st) {
+  if (h->n == 0 || h->opts.layout == RP_LAYOUT_CSR) return RP_OK;
   const int P = h->n_parts;
   std::vector<int64_t> soff(P + 1, 0);
   for (int p = 0; p < P; ++p)
@@ -340,6 +342,17 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st, bool parts) {
     if (s_ != RP_OK) return undo(s_); \
   } while (0)
   SL_TRY(salloc(&h->sl_part_soff, P + 1));
+  std::vector<int2> srow;
+  if (P > 1) {
+    srow.resize(S);
+    for (int p = 0; p < P; ++p) {
+      const int64_t r0 = h->part_row_off[p], np = h->part_row_off[p + 1] - r0;
+      for (int64_t j = 0; j < soff[p + 1] - soff[p]; ++j)
+        srow[soff[p] + j] = make_int2((int)(r0 + kSliceRows * j),
+                                      (int)(((int64_t)p << 6) | std::min<int64_t>(kSliceRows, np - kSliceRows * j)));
+    }
+    SL_TRY(salloc(&h->sl_srow, S));
+  }
   SL_TRY(salloc(&h->sl_desc, S + 1 + kSliceDescPad));
   SL_TRY(salloc(&h->sl_tinfo, S + kSliceDescPad));
   SL_TRY(salloc(&h->sl_tabs, (int64_t)tabs.size()));
@@ -356,6 +369,9 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st, bool parts) {
             "sliced descriptor upload"));
   RP_TRY(cu(cudaMemcpyAsync(h->sl_part_soff, soff.data(), 8 * (P + 1), cudaMemcpyHostToDevice, st),
             "sliced part offsets upload"));
+  if (P > 1)
+    RP_TRY(cu(cudaMemcpyAsync(h->sl_srow, srow.data(), sizeof(int2) * S, cudaMemcpyHostToDevice, st),
+              "sliced row records upload"));
   RP_TRY(cu(cudaMemcpyAsync(h->sl_tinfo, tinfo.data(), 4 * tinfo.size(), cudaMemcpyHostToDevice, st),
             "sliced table reference upload"));
   RP_TRY(cu(cudaMemcpyAsync(h->sl_tabs, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, st),
@@ -405,5 +421,6 @@ extern "C" rp_status rp_get_sliced_view(const rp_handle* h, rp_sliced_view* out)
   out->pos = h->sl_pos;
   out->vals = h->sl_vals;
   out->vals32 = h->sl_vals32;
+  out->srow = reinterpret_cast<const int32_t*>(h->sl_srow);
   return RP_OK;
 }

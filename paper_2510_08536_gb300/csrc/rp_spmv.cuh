@@ -19,9 +19,40 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ row_ptr, const 
   return sum;
 }
 
+// The non-local entries of row i (part p) added to sum in their CSR order:
+// the part's non-local CSR, whose compressed columns name the halo rows -- on
+// one GPU the halo exchange is this gather from x (global vector).
+template <typename T>
+__device__ __forceinline__ T nonlocal_add(const Parts<T>& P, int p, int64_t i, const T* __restrict__ x, T sum) {
+  const int64_t r0 = __ldg(P.row_off + p), li = i - r0;
+  const int32_t* nrp = P.nl_row_ptr + r0 + p;
+  const int64_t nlo = __ldg(P.nl_off + p), nco = __ldg(P.nlcol_off + p);
+  for (int j = __ldg(nrp + li); j < __ldg(nrp + li + 1); ++j)
+    sum = fma(__ldg(P.nl_vals + nlo + j), __ldg(x + __ldg(P.nl_cols + nco + __ldg(P.nl_col + nlo + j))), sum);
+  return sum;
+}
+
+// The same in two steps, so that the loads of the range can be issued before
+// the row's local sum: nonlocal_range, then nonlocal_sum.
+struct NlRange {
+  int j0, j1;
+  int64_t nlo, nco;
+};
+template <typename T>
+__device__ __forceinline__ NlRange nonlocal_range(const Parts<T>& P, int p, int64_t i) {
+  const int64_t r0 = __ldg(P.row_off + p), li = i - r0;
+  const int32_t* nrp = P.nl_row_ptr + r0 + p;
+  return NlRange{__ldg(nrp + li), __ldg(nrp + li + 1), __ldg(P.nl_off + p), __ldg(P.nlcol_off + p)};
+}
+template <typename T>
+__device__ __forceinline__ T nonlocal_sum(const Parts<T>& P, const NlRange& r, const T* __restrict__ x, T sum) {
+  for (int j = r.j0; j < r.j1; ++j)
+    sum = fma(__ldg(P.nl_vals + r.nlo + j), __ldg(x + __ldg(P.nl_cols + r.nco + __ldg(P.nl_col + r.nlo + j))), sum);
+  return sum;
+}
+
 // Row i of the matrix split into parts (Sec. 3): the part's local CSR (part-
-// local columns) plus its non-local CSR, whose compressed columns name the
-// halo rows -- on one GPU the halo exchange is this gather from x.
+// local columns), then its non-local entries.
 template <typename T>
 __device__ __forceinline__ T row_dot_parts(const Parts<T>& P, const int32_t* __restrict__ row_ptr,
                                            const int32_t* __restrict__ col, const T* __restrict__ vals,
@@ -33,11 +64,7 @@ __device__ __forceinline__ T row_dot_parts(const Parts<T>& P, const int32_t* __r
   T sum = T(0);
   for (int j = __ldg(rp + li); j < __ldg(rp + li + 1); ++j)
     sum = fma(__ldg(vals + no + j), __ldg(x + r0 + __ldg(col + no + j)), sum);
-  const int32_t* nrp = P.nl_row_ptr + r0 + p;
-  const int64_t nlo = __ldg(P.nl_off + p), nco = __ldg(P.nlcol_off + p);
-  for (int j = __ldg(nrp + li); j < __ldg(nrp + li + 1); ++j)
-    sum = fma(__ldg(P.nl_vals + nlo + j), __ldg(x + __ldg(P.nl_cols + nco + __ldg(P.nl_col + nlo + j))), sum);
-  return sum;
+  return nonlocal_add<T>(P, p, i, x, sum);
 }
 
 inline Parts<double> parts64(const rp_handle* h) {
@@ -56,17 +83,31 @@ __device__ __forceinline__ T row_dot_any(const Parts<T>& P, const int32_t* __res
   return P.n > 1 ? row_dot_parts<T>(P, row_ptr, col, vals, x, i) : row_dot<T>(row_ptr, col, vals, x, i);
 }
 
-// The sliced layout for the single-matrix iteration (a batch handle's per-system
-// layout is only for the batched kernel; GPU parts iterate over CSR).
+// The sliced layout of the iteration (with per-slice row records when the
+// matrix has several parts).
 inline Sliced<double> sliced64(const rp_handle* h, const double* vals) {
-  if (h->sl_slices == 0 || h->n_parts != 1 || vals != h->vals) return Sliced<double>{};  // e.g. transposed values
+  if (h->sl_slices == 0 || vals != h->vals) return Sliced<double>{};  // e.g. transposed values
   return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_vals,
-                        h->opts.spin_limit};
+                        h->opts.spin_limit, h->sl_srow};
 }
 inline Sliced<float> sliced32(const rp_handle* h) {
-  if (h->sl_slices == 0 || h->n_parts != 1 || !h->sl_vals32) return Sliced<float>{};
+  if (h->sl_slices == 0 || !h->sl_vals32) return Sliced<float>{};
   return Sliced<float>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_vals32,
-                       h->opts.spin_limit};
+                       h->opts.spin_limit, h->sl_srow};
+}
+
+// Rows of slice s: the first (global) row, how many of its 32 lanes hold a
+// row (a part's last slice may be short) and the part.
+struct SliceRows {
+  int row0, rows, part;
+};
+template <typename T>
+__device__ __forceinline__ SliceRows slice_rows(const Sliced<T>& sl, int s, int n) {
+  if (sl.srow) {
+    const int2 r = __ldg(sl.srow + s);
+    return SliceRows{r.x, r.y & 63, r.y >> 6};
+  }
+  return SliceRows{s * kSliceRows, min(kSliceRows, n - s * kSliceRows), 0};
 }
 
 // 16-byte vectors of the streaming kernels
@@ -270,8 +311,11 @@ __device__ __forceinline__ T slice_sum(uint2 d0, uint2 d1, uint32_t info, const 
   return slice_row<T, kIdx8Glob, COH>(v, iw, 0, tab, x, valid, L);
 }
 
-template <typename T, class Epi>
-__device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, int64_t n64, const T* xin, T* yout, Epi& epi) {
+// MP: several parts (slice rows from the per-slice records, non-local sums);
+// instantiated separately so that the one-part body keeps its registers.
+template <typename T, bool MP, class Epi>
+__device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, const Parts<T>& parts, int64_t n64, const T* xin,
+                                             T* yout, Epi& epi) {
   using St = SlStage<T>;
   constexpr int kStages = St::kStages;
   extern __shared__ __align__(128) unsigned char sbuf[];
@@ -348,8 +392,13 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, int64_t n64, co
       }
       const int s = ch * kChunk + w;
       if (s < S) {
-        const int row = s * kSliceRows + lane;
-        const bool valid = row < n;
+        SliceRows sr{s * kSliceRows, 0, 0};
+        if constexpr (MP) sr = slice_rows(sl, s, n);
+        const int row = sr.row0 + lane;
+        const bool valid = MP ? lane < sr.rows : row < n;
+        NlRange nl{0, 0, 0, 0};
+        if constexpr (MP)
+          if (valid) nl = nonlocal_range<T>(parts, sr.part, row);
         const T* x = xin + row;
         const unsigned char* base = sbuf + st * St::kBytes;
         T sum;
@@ -365,6 +414,7 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, int64_t n64, co
           sum = slice_sum<T>(d0, d1, __ldg(sl.tinfo + s), sl.vals + d0.x + lane,
                              reinterpret_cast<const uint32_t*>(sl.ibuf + d0.y) + lane, sl.tabs, x, valid, lane);
         }
+        if constexpr (MP) sum = nonlocal_sum<T>(parts, nl, xin, sum);
         if (valid) {
           yout[row] = sum;
           epi.row(row, sum);

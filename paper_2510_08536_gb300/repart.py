@@ -57,7 +57,7 @@ class SolveInfo(ctypes.Structure):
 
 class SlicedView(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("n_slices", "n_entries", "ibuf_len", "tabs_len")] + \
-               [(k, ctypes.c_void_p) for k in ("desc", "tinfo", "tabs", "ibuf", "pos", "vals", "vals32")]
+               [(k, ctypes.c_void_p) for k in ("desc", "tinfo", "tabs", "ibuf", "pos", "vals", "vals32", "srow")]
 
 
 class MapView(ctypes.Structure):
@@ -296,7 +296,8 @@ def get_sliced_view(h: Handle) -> dict:
                 ibuf=_view(v.ibuf, v.ibuf_len, "<i4").clone(),
                 pos=_view(v.pos, v.n_entries, "<i4").clone(),
                 vals=_view(v.vals, v.n_entries, "<f8").clone(),
-                vals32=_view(v.vals32, v.n_entries, "<f4").clone() if v.vals32 else None)
+                vals32=_view(v.vals32, v.n_entries, "<f4").clone() if v.vals32 else None,
+                srow=_view(v.srow, 2 * v.n_slices, "<i4").clone() if v.srow else None)
 
 
 def batch_build(systems, want_fp32: bool = True, **opts) -> Handle:

@@ -6,6 +6,8 @@ FP64 ||x_s - x_ref,s|| / ||x_ref,s|| <= 1e-7 against the oracle PCG at the same
 tolerance, iteration counts within 2; every system's true residual <= 1e-9;
 mixed: error against the FP64 solution <= 1e-6.
 """
+import types
+
 import numpy as np
 import pytest
 import torch
@@ -176,3 +178,77 @@ def test_batch_autotune_and_host_buffer(batch):
     repart.batch_update_solve(h, _t(stg), bd, x2, tol=1e-9)
     assert torch.equal(xd, x2)
     h.close()
+
+
+def _ldu(n, pairs):
+    """One independent system from cell pairs: SPD staging [diag | upper | lower]."""
+    pairs = np.unique(np.sort(np.asarray(pairs, np.int64), axis=1), axis=0)
+    pairs = pairs[pairs[:, 0] != pairs[:, 1]]
+    z = np.zeros(0, np.int32)
+    rank = types.SimpleNamespace(n_cells=n, lower_addr=pairs[:, 0].astype(np.int32),
+                                 upper_addr=pairs[:, 1].astype(np.int32), iface_row=z, iface_nbr_rank=z,
+                                 iface_nbr_col=z)
+    a = np.random.default_rng(n).lognormal(0.0, 0.5, pairs.shape[0])
+    diag = np.ones(n)
+    np.add.at(diag, rank.lower_addr, a)
+    np.add.at(diag, rank.upper_addr, a)
+    return rank, np.concatenate([diag, -a, -a])
+
+
+def _scrambled(nx, ny, nz, seed):
+    r = synth.box_mesh(nx, ny, nz, 1, 1, 1).ranks[0]
+    perm = np.random.default_rng(seed).permutation(r.n_cells)
+    return _ldu(r.n_cells, np.stack([perm[r.lower_addr], perm[r.upper_addr]], 1))
+
+
+def _banded(n, offsets):
+    return _ldu(n, [(i, i + d) for d in offsets for i in range(n - d)])
+
+
+def _box1(nx, ny, nz):
+    r = synth.box_mesh(nx, ny, nz, 1, 1, 1).ranks[0]
+    return _ldu(r.n_cells, np.stack([r.lower_addr, r.upper_addr], 1))
+
+
+def _solve_each(systems, layout_expected):
+    ranks = [r for r, _ in systems]
+    stg = np.concatenate([s for _, s in systems])
+    h = repart.batch_build(ranks)
+    assert (repart.get_sliced_view(h) is not None) == layout_expected
+    refs, ro = [], 0
+    for rank, s in systems:
+        (m,) = O.repartition_map([rank], 1)
+        vals = O.update_values(m.src_of, s)
+        A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
+        dinv = O.jacobi_inverse(m.row_ptr, m.col_idx, vals, m.diag_pos)
+        b = np.random.default_rng(ro + 7).uniform(-1.0, 1.0, rank.n_cells)
+        refs.append((A, dinv, b, ro, rank.n_cells))
+        ro += rank.n_cells
+    bb = np.concatenate([r[2] for r in refs])
+    for precision in ("fp64", "mixed", "mixed_ru"):
+        x = torch.zeros(ro, dtype=torch.float64, device=DEV)
+        infos = repart.batch_update_solve(h, _t(stg), _t(bb), x, tol=1e-9, precision=precision)
+        xs = x.cpu().numpy()
+        for s, (A, dinv, b, o, n) in enumerate(refs):
+            xi = xs[o:o + n]
+            assert infos[s]["status"] == 0, (precision, s, infos[s])
+            assert np.linalg.norm(b - A @ xi) / np.linalg.norm(b) <= 1e-9, (precision, s)
+            if precision == "fp64":
+                ref = O.pcg(A, dinv, b, tol=1e-9)
+                assert np.linalg.norm(xi - ref.x) / np.linalg.norm(ref.x) <= 1e-7, s
+                assert abs(infos[s]["iterations"] - ref.iterations) <= 2, (s, infos[s], ref.iterations)
+    h.close()
+
+
+def test_batch_mixed_slice_shapes():
+    """Systems whose slices need 8-bit indices (scrambled numbering), tables longer
+    than 32 offsets and rows longer than the staged width (wide band: read from
+    global memory), next to plain boxes and a system smaller than one slice."""
+    _solve_each([_scrambled(9, 8, 7, 3), _banded(1500, [1, 2, 3, 5, 8, 13, 21, 34, 55, 89, 144, 233]),
+                 _box1(13, 7, 9), _box1(2, 1, 1), _scrambled(6, 5, 4, 8)], True)
+
+
+def test_batch_falls_back_to_csr():
+    """A system with a row of more than 32 entries keeps the whole batch on CSR."""
+    hub = _ldu(200, [(i, i + 1) for i in range(199)] + [(0, j) for j in range(2, 42)])
+    _solve_each([_box1(13, 7, 9), hub, _scrambled(6, 5, 4, 8)], False)

@@ -226,8 +226,68 @@ def test_layout_falls_back_to_csr(make):
     h.close()
 
 
-def test_multi_part_runs_on_csr():
-    c = Case((12, 10, 8), (2, 2, 1), oracle_map=False)
-    h = repart.build_repartition(c.mesh.ranks, n_parts=2)
-    assert repart.get_sliced_view(h) is None
+@pytest.mark.parametrize("dims,parts,n_parts", [((12, 10, 8), (2, 2, 1), 2), ((13, 7, 9), (3, 2, 1), 3),
+                                                 ((13, 7, 9), (3, 2, 1), 6), ((40, 3, 2), (4, 1, 1), 4)])
+def test_multi_part_sliced(dims, parts, n_parts):
+    """Several GPU parts: each part's rows in slices of their own (ragged part
+    ends), local entries in the slices, non-local entries after them -- the
+    same row sums as the CSR iteration bit for bit, solves as the oracle's."""
+    c = Case(dims, parts, oracle_map=False)
+    h = repart.build_repartition(c.mesh.ranks, n_parts=n_parts)
+    hc = repart.build_repartition(c.mesh.ranks, n_parts=n_parts, layout=repart.RP_LAYOUT_CSR)
+    assert repart.get_sliced_view(hc) is None
+    for hh in (h, hc):
+        repart.update_values_packed(hh, _t(c.staging))
+    view = repart.get_sliced_view(h)
+    assert view is not None, "layout not built"
+    maps = O.repartition_map(c.mesh.ranks, n_parts)
+    srow = view["srow"].cpu().numpy().reshape(-1, 2)
+    desc = view["desc"].cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    pos = view["pos"].cpu().numpy().astype(np.int64)
+    vals = repart.get_values(h)["vals"].cpu().numpy()
+    s0 = r0 = nnz0 = 0
+    for p, m in enumerate(maps):
+        n_p = m.row_ptr.shape[0] - 1
+        S_p = (n_p + 31) // 32
+        np.testing.assert_array_equal(srow[s0:s0 + S_p, 0], r0 + 32 * np.arange(S_p))
+        np.testing.assert_array_equal(srow[s0:s0 + S_p, 1] >> 6, p)
+        np.testing.assert_array_equal(srow[s0:s0 + S_p, 1] & 63, np.minimum(32, n_p - 32 * np.arange(S_p)))
+        e0, e1 = desc[s0, 0], desc[s0 + S_p, 0]
+        local = np.where(pos >= 0, pos - nnz0, -1)
+        sub = dict(view, n_slices=S_p, n_entries=int(e1 - e0), desc=view["desc"][2 * s0:2 * (s0 + S_p + 1)],
+                   tinfo=view["tinfo"][s0:s0 + S_p], pos=torch.from_numpy(local))
+        check_layout(sub, m, n_p)
+        lp = pos[e0:e1]
+        np.testing.assert_array_equal(view["vals"].cpu().numpy()[e0:e1], np.where(lp >= 0, vals[np.maximum(lp, 0)], 0.0))
+        s0 += S_p
+        r0 += n_p
+        nnz0 += m.col_idx.shape[0]
+    assert s0 == view["n_slices"]
+    # products: bitwise those of the CSR iteration
+    n = c.mesh.n_cells
+    x = _t(np.random.default_rng(2).uniform(-1.0, 1.0, n))
+    ys = [torch.empty_like(x) for _ in range(2)]
+    for hh, y in zip((h, hc), ys):
+        repart.iter_spmv(hh, x, y, "fp64")
+    assert torch.equal(ys[0], ys[1])
+    x32 = x.float()
+    ys = [torch.empty_like(x32) for _ in range(2)]
+    for hh, y in zip((h, hc), ys):
+        repart.iter_spmv(hh, x32, y, "mixed")
+    assert torch.equal(ys[0], ys[1])
+    # solves: the oracle's system, all three precisions
+    (m1,) = O.repartition_map(c.mesh.ranks, 1)
+    A = O.csr_matrix(m1.row_ptr, m1.col_idx, O.update_values(m1.src_of, c.staging))
+    dinv = O.jacobi_inverse(m1.row_ptr, m1.col_idx, O.update_values(m1.src_of, c.staging), m1.diag_pos)
+    ref = O.pcg(A, dinv, c.b, tol=1e-9)
+    for precision in ("fp64", "mixed", "mixed_ru"):
+        xs = torch.zeros(n, dtype=torch.float64, device=DEV)
+        info = repart.solve(h, _t(c.b), xs, tol=1e-9, precision=precision)
+        xn = xs.cpu().numpy()
+        assert info["status"] == 0, (precision, info)
+        assert np.linalg.norm(c.b - A @ xn) / np.linalg.norm(c.b) <= 1e-9, precision
+        if precision == "fp64":
+            assert np.linalg.norm(xn - ref.x) / np.linalg.norm(ref.x) <= 1e-7
+            assert abs(info["iterations"] - ref.iterations) <= 2
     h.close()
+    hc.close()
