@@ -3,7 +3,8 @@
 // With A x = b and a loss L(x), the adjoint lambda solves A^T lambda = dL/dx;
 // then dL/db = lambda and dL/da_ij = -lambda_i x_j for every stored entry.
 // A^T reuses A's pattern: valsT[p] = vals[tpos[p]] (one gather pass), and the
-// Jacobi diagonal is unchanged by transposition. Symmetric storage needs no
+// Jacobi diagonal is unchanged by transposition; the sliced layout of A then
+// serves A^T with its values gathered from valsT. Symmetric storage needs no
 // transpose at all.
 #include "rp_common.cuh"
 
@@ -87,6 +88,7 @@ extern "C" rp_status rp_solve_adjoint(rp_handle* h, const double* g, double* lam
   }
   k_transpose_vals<<<grid_for(h, h->nnz), kThreads, 0, s>>>(h->nnz, h->tpos, h->vals, h->valsT);
   RP_TRY_CUDA(cudaGetLastError());
+  RP_TRY(fill_sliced_transposed(h, s));  // the iteration multiplies with the sliced layout of A^T
   return solve_common(h, false, h->valsT, h->dinv, &h->graphs.adjoint, g, lambda, tol, 0, RP_MEM_DEVICE, info, s);
 }
 

@@ -274,6 +274,7 @@ struct rp_handle {
   int32_t* sl_ibuf = nullptr;
   int32_t* sl_pos = nullptr;  // CSR position of each padded entry, -1 = padding
   double* sl_vals = nullptr;
+  double* sl_valsT = nullptr;  // sliced transposed values (adjoint of general storage, on demand)
   float* sl_vals32 = nullptr;
 
   // solver work space
@@ -323,6 +324,7 @@ inline int grid_for(const rp_handle* h, int64_t n) {
 
 rp_status ensure_solver_buffers(rp_handle* h);
 rp_status build_sliced(rp_handle* h, cudaStream_t s);  // after the CSR map
+rp_status fill_sliced_transposed(rp_handle* h, cudaStream_t s);  // sl_valsT from valsT
 rp_status fill_sliced(rp_handle* h, cudaStream_t s);   // after every value update
 void free_sliced(rp_handle* h);
 void free_bicgstab(rp_handle* h);

@@ -243,7 +243,7 @@ struct Tmp {
 
 void free_sliced(rp_handle* h) {
   void* ptrs[] = {h->sl_part_soff, h->sl_srow, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_pos,
-                  h->sl_vals, h->sl_vals32};
+                  h->sl_vals, h->sl_vals32, h->sl_valsT};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->sl_part_soff = nullptr;
@@ -255,6 +255,7 @@ void free_sliced(rp_handle* h) {
   h->sl_pos = nullptr;
   h->sl_vals = nullptr;
   h->sl_vals32 = nullptr;
+  h->sl_valsT = nullptr;
   h->sl_slices = h->sl_entries = h->sl_ibuf_len = h->sl_tabs_len = 0;
 }
 
@@ -400,6 +401,19 @@ rp_status fill_sliced(rp_handle* h, cudaStream_t s) {
     k_slice_vals<true><<<g, kThreads, 0, s>>>(nq4, pos, h->vals, out, reinterpret_cast<float4*>(h->sl_vals32));
   else
     k_slice_vals<false><<<g, kThreads, 0, s>>>(nq4, pos, h->vals, out, nullptr);
+  RP_TRY_CUDA(cudaGetLastError());
+  return RP_OK;
+}
+
+// The transposed matrix of a structurally symmetric pattern (every entry has
+// its transposed position) has the same slices: entry q of the layout takes
+// valsT at the same CSR position.
+rp_status fill_sliced_transposed(rp_handle* h, cudaStream_t s) {
+  if (h->sl_slices == 0 || !h->valsT) return RP_OK;
+  if (!h->sl_valsT) RP_TRY(salloc(&h->sl_valsT, h->sl_entries));
+  const int64_t nq4 = h->sl_entries / 4;
+  k_slice_vals<false><<<grid_for(h, nq4), kThreads, 0, s>>>(nq4, reinterpret_cast<const int4*>(h->sl_pos), h->valsT,
+                                                            reinterpret_cast<double2*>(h->sl_valsT), nullptr);
   RP_TRY_CUDA(cudaGetLastError());
   return RP_OK;
 }

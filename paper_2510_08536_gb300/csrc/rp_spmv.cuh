@@ -86,9 +86,10 @@ __device__ __forceinline__ T row_dot_any(const Parts<T>& P, const int32_t* __res
 // The sliced layout of the iteration (with per-slice row records when the
 // matrix has several parts).
 inline Sliced<double> sliced64(const rp_handle* h, const double* vals) {
-  if (h->sl_slices == 0 || vals != h->vals) return Sliced<double>{};  // e.g. transposed values
-  return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_vals,
-                        h->opts.spin_limit, h->sl_srow};
+  const double* v = vals == h->vals ? h->sl_vals : vals == h->valsT ? h->sl_valsT : nullptr;
+  if (h->sl_slices == 0 || !v) return Sliced<double>{};
+  return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, v, h->opts.spin_limit,
+                        h->sl_srow};
 }
 inline Sliced<float> sliced32(const rp_handle* h) {
   if (h->sl_slices == 0 || !h->sl_vals32) return Sliced<float>{};
