@@ -9,6 +9,9 @@
 * 128^3 adjoint: dL/db and the face gradient against central finite
   differences (h = 1e-6) on 50 cells and 50 faces, relative error
   |g_fd - g| / max(|g|, 1e-3 max|g|) <= 1e-5.
+* the batched workload (256 uneven systems, autotuned launch): every
+  system's true residual from its LDU products, sampled systems' maps and
+  values bit-exact and FP64 solves against the oracle's.
 """
 import json
 import os
@@ -173,4 +176,49 @@ def test_adjoint_workload_128_finite_differences():
         fdv = fd((up, dn), (rho - hstep * dax, rho + hstep * dax))
         g = gf_np[foff[r] + f]
         assert rel(fdv, g, np.abs(gf_np).max()) <= 1e-5, (r, f, fdv, g)
+    h.close()
+
+
+def test_batched_workload_256():
+    """The batched workload at full size (256 uneven systems, the bench's
+    autotuned launch): every system's true residual from the LDU products of
+    its own coefficients (no repartitioning involved), the reported residual
+    equal to it, maps and values of sampled systems bit-exact, and sampled
+    FP64 solves against the oracle's."""
+    B = synth.Batch(256, 8000, 300000, seed=0)
+    stg = B.staging(0.5, 100)
+    b = B.rhs(0)
+    h = repart.batch_build(B.systems)
+    x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
+    repart.batch_autotune(h, _t(stg), _t(b), x, tol=1e-9, precision="fp64")
+    ro = np.cumsum([0] + [m.n_cells for m in B.meshes])
+    so = np.cumsum([0] + [m.staging_size() for m in B.meshes])
+    order = np.argsort([m.n_cells for m in B.meshes])
+    sample = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    for precision in ("fp64", "mixed", "mixed_ru"):
+        x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
+        infos = repart.batch_update_solve(h, _t(stg), _t(b), x, tol=1e-9, precision=precision)
+        xs = x.cpu().numpy()
+        for s, rank in enumerate(B.systems):
+            xi, bi = xs[ro[s]:ro[s + 1]], b[ro[s]:ro[s + 1]]
+            r = bi - O.ldu_matvec([rank], stg[so[s]:so[s + 1]], xi)
+            tr = np.linalg.norm(r) / np.linalg.norm(bi)
+            assert infos[s]["status"] == 0 and tr <= 1e-9, (precision, s, infos[s], tr)
+            assert abs(infos[s]["rel_residual"] - tr) <= 1e-12, (precision, s)
+        if precision == "fp64":
+            vals_all = repart.get_values(h)["vals"].cpu().numpy()
+            nnz0 = np.cumsum([0] + [m.nnz() for m in B.meshes])
+            for s in sample:
+                (m,) = O.repartition_map([B.systems[s]], 1)
+                got = repart.get_part_map(h, s)
+                for key in ("row_ptr", "col_idx", "src_of", "diag_pos"):
+                    np.testing.assert_array_equal(got[key].cpu().numpy(), getattr(m, key), err_msg=f"{s} {key}")
+                vals = O.update_values(m.src_of, stg[so[s]:so[s + 1]])
+                np.testing.assert_array_equal(vals_all[nnz0[s]:nnz0[s + 1]], vals)
+                A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
+                bi = b[ro[s]:ro[s + 1]]
+                ref = O.pcg(A, O.jacobi_inverse(m.row_ptr, m.col_idx, vals, m.diag_pos), bi, tol=1e-9)
+                xi = xs[ro[s]:ro[s + 1]]
+                assert np.linalg.norm(xi - ref.x) / np.linalg.norm(ref.x) <= 1e-7, s
+                assert abs(infos[s]["iterations"] - ref.iterations) <= 2, (s, infos[s], ref.iterations)
     h.close()
