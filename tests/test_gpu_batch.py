@@ -252,3 +252,27 @@ def test_batch_falls_back_to_csr():
     """A system with a row of more than 32 entries keeps the whole batch on CSR."""
     hub = _ldu(200, [(i, i + 1) for i in range(199)] + [(0, j) for j in range(2, 42)])
     _solve_each([_box1(13, 7, 9), hub, _scrambled(6, 5, 4, 8)], False)
+
+
+def test_batch_with_empty_and_single_cell_systems():
+    """A system without cells (nothing to solve: status OK, no iterations) and a
+    1 x 1 system next to ordinary ones."""
+    z = np.zeros(0, np.int32)
+    empty = (types.SimpleNamespace(n_cells=0, lower_addr=z, upper_addr=z, iface_row=z, iface_nbr_rank=z,
+                                   iface_nbr_col=z), np.zeros(0))
+    one = (types.SimpleNamespace(n_cells=1, lower_addr=z, upper_addr=z, iface_row=z, iface_nbr_rank=z,
+                                 iface_nbr_col=z), np.array([4.0]))
+    systems = [_box1(13, 7, 9), empty, one, _scrambled(6, 5, 4, 8)]
+    ranks = [r for r, _ in systems]
+    stg = np.concatenate([s for _, s in systems])
+    n = sum(r.n_cells for r in ranks)
+    h = repart.batch_build(ranks)
+    b = np.random.default_rng(1).uniform(-1.0, 1.0, n)
+    for precision in ("fp64", "mixed", "mixed_ru"):
+        x = torch.zeros(n, dtype=torch.float64, device=DEV)
+        infos = repart.batch_update_solve(h, _t(stg), _t(b), x, tol=1e-9, precision=precision)
+        assert [i["status"] for i in infos] == [0, 0, 0, 0], (precision, infos)
+        assert infos[1]["iterations"] == 0
+        i1 = ranks[0].n_cells
+        assert abs(float(x[i1]) - b[i1] / 4.0) <= 1e-15 * abs(b[i1])
+    h.close()
