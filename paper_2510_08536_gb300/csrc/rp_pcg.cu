@@ -178,8 +178,9 @@ __global__ void __launch_bounds__(kThreads) k_it_spmv(IterArgs<T> a) {
 // PCG iteration. An instance of spmv_sl_body with PcgK1Epi computes the same
 // but measured 5-7% slower for FP32 on GB300 (0.152-0.154 ms against 0.144 ms
 // per launch at 256^3, same registers), so the hot kernel keeps its own copy.
+// MP: several parts (k_it_spmv_sl_mp below).
 template <typename T, bool MP>
-__global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
+__device__ __forceinline__ void it_spmv_sl(const IterArgs<T>& a) {
   Ctl* c = a.ctl;
   if (c->stop) return;
   using St = SlStage<T>;
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
         if constexpr (MP) sr = slice_rows(a.sl, s, n);  // several parts: per-slice records
         const int row = sr.row0 + lane;
         const bool valid = MP ? lane < sr.rows : row < n;
-        NlRange nl{0, 0, 0, 0};
+        NlRange nl{0, 0};
         if constexpr (MP)
           if (valid) nl = nonlocal_range<T>(a.parts, sr.part, row);
         const T* x = a.p + row;
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
           sum = slice_sum<T>(d0, d1, __ldg(a.sl.tinfo + s), a.sl.vals + d0.x + lane,
                              reinterpret_cast<const uint32_t*>(a.sl.ibuf + d0.y) + lane, a.sl.tabs, x, valid, lane);
         }
-        if constexpr (MP) sum = nonlocal_sum<T>(a.parts, nl, a.p, sum);
+        if constexpr (MP) sum = nonlocal_sum<T>(a.parts, sr.part, nl, a.p, sum);
         if (valid) {
           a.q[row] = sum;
           acc = fma(a.p[row], sum, acc);
@@ -307,9 +308,21 @@ __global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
 }
 
 template <typename T>
+__global__ void __launch_bounds__(kSlThreads) k_it_spmv_sl(IterArgs<T> a) {
+  it_spmv_sl<T, false>(a);
+}
+// Several parts: the FP32 instance is held to the registers of seven blocks an
+// SM, which the one-part FP32 kernel reaches without a bound (FP64: five, its
+// shared-memory limit).
+template <typename T>
+__global__ void __launch_bounds__(kSlThreads, sizeof(T) == 4 ? 7 : 5) k_it_spmv_sl_mp(IterArgs<T> a) {
+  it_spmv_sl<T, true>(a);
+}
+
+template <typename T>
 void* k1_kernel(const IterArgs<T>& a) {
   if (a.sl.n_slices == 0) return (void*)k_it_spmv<T>;
-  return a.sl.srow ? (void*)k_it_spmv_sl<T, true> : (void*)k_it_spmv_sl<T, false>;
+  return a.sl.srow ? (void*)k_it_spmv_sl_mp<T> : (void*)k_it_spmv_sl<T>;
 }
 template <typename T>
 int k1_grid(const IterArgs<T>& a, const IterGrid& g) {
@@ -325,8 +338,8 @@ int k1_threads(const IterArgs<T>& a) {
 }
 template <typename T>
 void launch_k1(const IterArgs<T>& a, int grid, cudaStream_t s) {
-  if (a.sl.n_slices > 0 && a.sl.srow) k_it_spmv_sl<T, true><<<grid, kSlThreads, SlStage<T>::kSmem, s>>>(a);
-  else if (a.sl.n_slices > 0) k_it_spmv_sl<T, false><<<grid, kSlThreads, SlStage<T>::kSmem, s>>>(a);
+  if (a.sl.n_slices > 0 && a.sl.srow) k_it_spmv_sl_mp<T><<<grid, kSlThreads, SlStage<T>::kSmem, s>>>(a);
+  else if (a.sl.n_slices > 0) k_it_spmv_sl<T><<<grid, kSlThreads, SlStage<T>::kSmem, s>>>(a);
   else k_it_spmv<T><<<grid, kThreads, 0, s>>>(a);
 }
 
@@ -895,14 +908,14 @@ IterGrid iter_grid(const rp_handle* h) {
     int64_t cap = (int64_t)h->num_sms * per_sm;
     return (int)(want < 1 ? 1 : want < cap ? want : cap);
   };
-  const void* sl = (const void*)k_it_spmv_sl<T, false>;
-  for (const void* f : {sl, (const void*)k_it_spmv_sl<T, true>})
+  const void* sl = (const void*)k_it_spmv_sl<T>;
+  for (const void* f : {sl, (const void*)k_it_spmv_sl_mp<T>})
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SlStage<T>::kSmem) != cudaSuccess)
       cudaGetLastError();  // the launch reports it
   IterGrid gr;
   gr.k1 = g(resident((const void*)k_it_spmv<T>));
   gr.k1s = g(resident(sl, SlStage<T>::kSmem, kSlThreads));
-  gr.k1sm = g(resident((const void*)k_it_spmv_sl<T, true>, SlStage<T>::kSmem, kSlThreads));
+  gr.k1sm = g(resident((const void*)k_it_spmv_sl_mp<T>, SlStage<T>::kSmem, kSlThreads));
   gr.k2 = g(resident((const void*)k_it_resid<T, false>));
   gr.k3 = g(resident((const void*)k_it_xp<T, false>));
   gr.k2l = g(resident((const void*)k_it_resid<T, true>));

@@ -32,22 +32,25 @@ __device__ __forceinline__ T nonlocal_add(const Parts<T>& P, int p, int64_t i, c
   return sum;
 }
 
-// The same in two steps, so that the loads of the range can be issued before
-// the row's local sum: nonlocal_range, then nonlocal_sum.
+// The same in two steps, so that the row's non-local range is loaded before
+// its local sum: nonlocal_range, then nonlocal_sum (the part's offsets are
+// read again there, from L1, to keep few registers live across the sum).
 struct NlRange {
   int j0, j1;
-  int64_t nlo, nco;
 };
 template <typename T>
 __device__ __forceinline__ NlRange nonlocal_range(const Parts<T>& P, int p, int64_t i) {
   const int64_t r0 = __ldg(P.row_off + p), li = i - r0;
   const int32_t* nrp = P.nl_row_ptr + r0 + p;
-  return NlRange{__ldg(nrp + li), __ldg(nrp + li + 1), __ldg(P.nl_off + p), __ldg(P.nlcol_off + p)};
+  return NlRange{__ldg(nrp + li), __ldg(nrp + li + 1)};
 }
 template <typename T>
-__device__ __forceinline__ T nonlocal_sum(const Parts<T>& P, const NlRange& r, const T* __restrict__ x, T sum) {
+__device__ __forceinline__ T nonlocal_sum(const Parts<T>& P, int p, const NlRange& r, const T* __restrict__ x,
+                                          T sum) {
+  if (r.j0 == r.j1) return sum;
+  const int64_t nlo = __ldg(P.nl_off + p), nco = __ldg(P.nlcol_off + p);
   for (int j = r.j0; j < r.j1; ++j)
-    sum = fma(__ldg(P.nl_vals + r.nlo + j), __ldg(x + __ldg(P.nl_cols + r.nco + __ldg(P.nl_col + r.nlo + j))), sum);
+    sum = fma(__ldg(P.nl_vals + nlo + j), __ldg(x + __ldg(P.nl_cols + nco + __ldg(P.nl_col + nlo + j))), sum);
   return sum;
 }
 
@@ -397,7 +400,7 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, const Parts<T>&
         if constexpr (MP) sr = slice_rows(sl, s, n);
         const int row = sr.row0 + lane;
         const bool valid = MP ? lane < sr.rows : row < n;
-        NlRange nl{0, 0, 0, 0};
+        NlRange nl{0, 0};
         if constexpr (MP)
           if (valid) nl = nonlocal_range<T>(parts, sr.part, row);
         const T* x = xin + row;
@@ -415,7 +418,7 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, const Parts<T>&
           sum = slice_sum<T>(d0, d1, __ldg(sl.tinfo + s), sl.vals + d0.x + lane,
                              reinterpret_cast<const uint32_t*>(sl.ibuf + d0.y) + lane, sl.tabs, x, valid, lane);
         }
-        if constexpr (MP) sum = nonlocal_sum<T>(parts, nl, xin, sum);
+        if constexpr (MP) sum = nonlocal_sum<T>(parts, sr.part, nl, xin, sum);
         if (valid) {
           yout[row] = sum;
           epi.row(row, sum);
