@@ -12,9 +12,11 @@
 //   5. transpose positions by binary search in the partner row
 //   6. non-local columns compressed per part by mark + scan
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <memory>
-#include <tuple>
+#include <thread>
+#include <vector>
 
 #include "rp_common.cuh"
 
@@ -360,6 +362,49 @@ struct DeviceGuard {
   }
 };
 
+// f(i) for i in [0, n) on up to 16 host threads (dynamic schedule); on one
+// thread when threads cannot be started.
+template <class F>
+void parallel_for(int64_t n, F&& f) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int64_t T = std::min<int64_t>(n, std::min<unsigned>(hw ? hw : 1u, 16u));
+  std::atomic<int64_t> next{0};
+  auto work = [&]() {
+    for (int64_t i; (i = next.fetch_add(1)) < n;) f(i);
+  };
+  std::vector<std::thread> th;
+  try {
+    for (int64_t t = 1; t < T; ++t) th.emplace_back(work);
+  } catch (...) {  // no more threads: the ones started and this one finish the work
+  }
+  work();
+  for (auto& t : th) t.join();
+}
+
+// Ascending sort of 64-bit keys: LSD radix, 8-bit digits, skipping digits
+// that are equal in every key.
+void radix_sort_u64(std::vector<uint64_t>& v) {
+  std::vector<uint64_t> tmp(v.size());
+  uint64_t any = 0, all = ~0ull;
+  for (uint64_t x : v) {
+    any |= x;
+    all &= x;
+  }
+  for (int sh = 0; sh < 64; sh += 8) {
+    if ((((any ^ all) >> sh) & 0xffu) == 0) continue;
+    uint32_t cnt[256] = {0};
+    for (uint64_t x : v) ++cnt[(x >> sh) & 0xffu];
+    uint32_t run = 0;
+    for (uint32_t& c : cnt) {
+      const uint32_t t = c;
+      c = run;
+      run += t;
+    }
+    for (uint64_t x : v) tmp[cnt[(x >> sh) & 0xffu]++] = x;
+    v.swap(tmp);
+  }
+}
+
 rp_status validate(const rp_ldu_desc* ranks, int32_t k, const rp_options& o) {
   if (!ranks || k < 1) return fail(RP_EINVAL, "need k >= 1 rank descriptors");
   if (o.n_parts < 1 || k % o.n_parts) return fail(RP_EINVAL, "n_parts=%d must divide k=%d", o.n_parts, k);
@@ -374,6 +419,7 @@ rp_status validate(const rp_ldu_desc* ranks, int32_t k, const rp_options& o) {
   if (o.precond == RP_PRECOND_LINE && o.n_parts != 1)
     return fail(RP_EUNSUPPORTED, "the line preconditioner needs n_parts = 1");
   int64_t n = 0, nnz = 0, slots = 0;
+  std::vector<int64_t> off(k + 1, 0), eoff(k + 1, 0);
   for (int r = 0; r < k; ++r) {
     const rp_ldu_desc& d = ranks[r];
     if (d.n_cells < 0 || d.n_faces < 0 || d.n_iface < 0)
@@ -384,12 +430,32 @@ rp_status validate(const rp_ldu_desc* ranks, int32_t k, const rp_options& o) {
     n += d.n_cells;
     nnz += (int64_t)d.n_cells + 2 * (int64_t)d.n_faces + d.n_iface;
     slots += (int64_t)d.n_cells + (o.symmetric ? 1 : 2) * (int64_t)d.n_faces + d.n_iface;
+    off[r + 1] = off[r] + d.n_cells;
+    eoff[r + 1] = eoff[r] + d.n_iface;
   }
   const int64_t lim = 2147483647LL - 1024;
   if (n > lim || nnz > lim || slots > lim)
     return fail(RP_EOVERFLOW, "rows=%lld entries=%lld slots=%lld exceed the 32-bit index range",
                 (long long)n, (long long)nnz, (long long)slots);
+  // every rank at once, without branches; a rank that fails is scanned again to name the entry
+  std::vector<char> bad(k, 0);
+  parallel_for(k, [&](int64_t r) {
+    const rp_ldu_desc& d = ranks[r];
+    const int32_t nc = d.n_cells;
+    int b = 0;
+    for (int32_t f = 0; f < d.n_faces; ++f) {
+      const int32_t l = d.lower_addr[f], u = d.upper_addr[f];
+      b |= (l < 0) | (u >= nc) | (l >= u);  // with l < u these bound both addresses
+    }
+    for (int32_t e = 0; e < d.n_iface; ++e) {
+      const int32_t row = d.iface_row[e], q = d.iface_nbr_rank[e], c = d.iface_nbr_col[e];
+      b |= (row < 0) | (row >= nc) | (q < 0) | (q >= k) | (q == (int32_t)r);
+      if (q >= 0 && q < k) b |= (c < 0) | (c >= ranks[q].n_cells);
+    }
+    bad[r] = (char)b;
+  });
   for (int r = 0; r < k; ++r) {
+    if (!bad[r]) continue;
     const rp_ldu_desc& d = ranks[r];
     for (int32_t f = 0; f < d.n_faces; ++f) {
       int32_t l = d.lower_addr[f], u = d.upper_addr[f];
@@ -406,17 +472,19 @@ rp_status validate(const rp_ldu_desc* ranks, int32_t k, const rp_options& o) {
         return fail(RP_ERANGE, "rank %d iface %d: column %d outside rank %d", r, e, c, q);
     }
   }
-  // interfaces must come in transposed pairs
-  std::vector<std::tuple<int32_t, int32_t, int32_t, int32_t>> a, b;
-  for (int r = 0; r < k; ++r) {
+  // interfaces must come in transposed pairs: the merged (row, col) of every
+  // interface entry, as a multiset, equals that of the transposed entries
+  std::vector<uint64_t> a(eoff[k]), b(eoff[k]);
+  parallel_for(k, [&](int64_t r) {
     const rp_ldu_desc& d = ranks[r];
     for (int32_t e = 0; e < d.n_iface; ++e) {
-      a.emplace_back(r, d.iface_row[e], d.iface_nbr_rank[e], d.iface_nbr_col[e]);
-      b.emplace_back(d.iface_nbr_rank[e], d.iface_nbr_col[e], r, d.iface_row[e]);
+      const uint64_t gr = (uint64_t)(off[r] + d.iface_row[e]);
+      const uint64_t gc = (uint64_t)(off[d.iface_nbr_rank[e]] + d.iface_nbr_col[e]);
+      a[eoff[r] + e] = gr << 32 | gc;
+      b[eoff[r] + e] = gc << 32 | gr;
     }
-  }
-  std::sort(a.begin(), a.end());
-  std::sort(b.begin(), b.end());
+  });
+  parallel_for(2, [&](int64_t i) { radix_sort_u64(i ? b : a); });
   if (a != b) return fail(RP_EINVAL, "processor interfaces are not paired (rank q must hold the transposed entry)");
   return RP_OK;
 }
