@@ -22,7 +22,8 @@ written for a reader to check against the paper by eye:
 * Jacobi-preconditioned CG for the merged pressure system (the paper solves
   it with CG, Sec. 4; the preconditioner is Jacobi here);
 * Jacobi-preconditioned BiCGStab for the non-symmetric momentum system (the
-  paper's momentum solver, Sec. 4);
+  paper's momentum solver, Sec. 4), in FP64 and as FP32-inner / FP64-outer
+  refinement;
 * FP32-inner / FP64-outer iterative refinement, the adjoint solve and the
   gradients with respect to the stored entries (plain definitions).
 
@@ -495,6 +496,99 @@ def bicgstab(A, dinv, b, tol=1e-9, max_iter=10000, x0=None) -> SolveResult:
         rho = float(rhat @ r)
     tr = b - A @ x
     return SolveResult(x, it, status, float(np.sqrt(rr / bb)), float(np.sqrt((tr @ tr) / bb)))
+
+
+def bicgstab_fp32(A32, dinv32, rhs32, rel_tol=1e-5, max_iter=10000, dtype=np.float32):
+    """Inner BiCGStab of the mixed form for the momentum system, x0 = 0.
+
+    The recurrence of ``bicgstab`` (same order of steps, half step when ||s|| is
+    small enough) with vectors, values and products in ``dtype``; the dot
+    products are accumulated in FP64 and alpha, omega and beta are rounded to
+    ``dtype`` before use. No restarts: it stops when the recursive residual
+    (||s|| at a half step, else ||r||) is at most rel_tol ||rhs||, on a breakdown
+    (rho = 0, (rhat, v) = 0, (t, t) = 0 or omega = 0) or after max_iter
+    iterations. Returns (d, iterations, status)."""
+    f = dtype
+
+    def dot(u, w):
+        return float(u.astype(np.float64) @ w.astype(np.float64))
+
+    d = np.zeros_like(rhs32)
+    r = rhs32.copy()
+    thresh = rel_tol * rel_tol * dot(r, r)
+    if thresh == 0.0 and dot(r, r) == 0.0:
+        return d, 0, OK
+    rhat = r.copy()
+    rho_old = alpha = omega = 1.0
+    p = np.zeros_like(r)
+    v = np.zeros_like(r)
+    rho = dot(rhat, r)
+    it = 0
+    while it < max_iter:
+        if rho == 0.0:
+            return d, it, BREAKDOWN
+        beta = f((rho / rho_old) * (alpha / omega))
+        p = r + beta * (p - f(omega) * v)
+        phat = dinv32 * p
+        v = A32 @ phat
+        rv = dot(rhat, v)
+        if rv == 0.0:
+            return d, it, BREAKDOWN
+        alpha = rho / rv
+        s = r - f(alpha) * v
+        it += 1
+        if dot(s, s) <= thresh:
+            return d + f(alpha) * phat, it, OK
+        shat = dinv32 * s
+        t = A32 @ shat
+        tt = dot(t, t)
+        if not tt > 0.0:
+            return d, it, BREAKDOWN
+        omega = dot(t, s) / tt
+        d = d + f(alpha) * phat + f(omega) * shat
+        r = s - f(omega) * t
+        if dot(r, r) <= thresh:
+            return d, it, OK
+        if omega == 0.0:
+            return d, it, BREAKDOWN
+        rho_old = rho
+        rho = dot(rhat, r)
+    return d, it, NOT_CONVERGED
+
+
+def bicgstab_mixed_ir(A64, A32, dinv32, b, tol=1e-9, inner_tol=1e-5, max_outer=50, max_iter=10000,
+                      dtype=np.float32) -> SolveResult:
+    """FP32-inner / FP64-outer iterative refinement around BiCGStab.
+
+    x = 0; repeat: r = b - A x with FP64 values; stop when ||r|| <= tol ||b||;
+    solve A32 d = fl(r) by ``bicgstab_fp32`` to inner_tol relative (a new
+    shadow residual every time); x += d in FP64. ``max_iter`` bounds the inner
+    iterations of all passes together."""
+    b = np.asarray(b, np.float64)
+    bb = float(b @ b)
+    x = np.zeros_like(b)
+    if bb == 0.0:
+        return SolveResult(x, 0, OK, 0.0, 0.0, 0)
+    total = 0
+    status = NOT_CONVERGED
+    outer = 0
+    while True:
+        r = b - A64 @ x
+        rr = float(r @ r)
+        if rr <= tol * tol * bb:
+            status = OK
+            break
+        if outer >= max_outer or total >= max_iter:
+            break
+        d, it, st = bicgstab_fp32(A32, dinv32, r.astype(dtype), inner_tol, max_iter - total, dtype)
+        total += it
+        outer += 1
+        if st == BREAKDOWN:
+            status = BREAKDOWN
+            break
+        x += d.astype(np.float64)
+    rel = float(np.sqrt(rr / bb))
+    return SolveResult(x, total, status, rel, rel, outer)
 
 
 def pcg_fp32(A32, dinv32, rhs32, rel_tol=1e-5, max_iter=10000):

@@ -489,6 +489,49 @@ def test_bicgstab_edge_cases():
     assert res.status == O.OK and res.iterations == 0
 
 
+def test_bicgstab_fp32_inner_in_fp64_is_the_fp64_recurrence():
+    """The inner solver run in FP64 from x0 = 0 is bicgstab itself: the same
+    iterates after k iterations (a wrong step order, sign or scalar would differ)."""
+    mesh, stg, m, A, dinv, b = _momentum((10, 8, 6), (2, 1, 1))
+    for k in (1, 2, 7, 20):
+        d, it, st = O.bicgstab_fp32(A, dinv, b.copy(), rel_tol=0.0, max_iter=k, dtype=np.float64)
+        ref = O.bicgstab(A, dinv, b, tol=0.0, max_iter=k)
+        assert it == k == ref.iterations and st == O.NOT_CONVERGED
+        assert np.linalg.norm(d - ref.x) / np.linalg.norm(ref.x) <= 1e-12, k
+
+
+def test_bicgstab_mixed_refinement_reaches_fp64_residual():
+    """FP32 inner BiCGStab (FP32 values, vectors and products) inside FP64 refinement:
+    the true FP64 residual reaches 1e-9 although one FP32 pass stalls near 1e-7, and the
+    result agrees with the FP64 solve; with an FP64 inner solve one pass suffices."""
+    mesh, stg, m, A, dinv, b = _momentum((14, 12, 10), (2, 2, 1))
+    vals = O.update_values(m.src_of, stg)
+    v32 = O.to_fp32(vals)
+    A32 = O.csr_matrix(m.row_ptr, m.col_idx, v32)
+    d32 = np.float32(1) / v32[m.diag_pos]
+    res = O.bicgstab_mixed_ir(A, A32, d32, b, tol=1e-9, inner_tol=1e-5)
+    assert res.status == O.OK and res.true_rel_residual <= 1e-9
+    assert res.outer_iterations >= 2
+    ref = O.bicgstab(A, dinv, b, tol=1e-12)
+    assert np.linalg.norm(res.x - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+    one = O.bicgstab_mixed_ir(A, A, dinv, b, tol=1e-9, inner_tol=1e-11, dtype=np.float64)
+    assert one.status == O.OK and one.outer_iterations == 1
+
+
+def test_bicgstab_mixed_edge_cases():
+    mesh, stg, m, A, dinv, b = _momentum((5, 4, 3), (1, 1, 1))
+    A32 = A.astype(np.float32)
+    res = O.bicgstab_mixed_ir(A, A32, dinv.astype(np.float32), np.zeros_like(b))
+    assert res.status == O.OK and res.iterations == 0 and not res.x.any()
+    d = np.random.default_rng(3).uniform(1.0, 5.0, 40)
+    D = sp.csr_matrix(sp.diags(d))
+    bd = np.random.default_rng(4).uniform(-1.0, 1.0, 40)
+    res = O.bicgstab_mixed_ir(D, D.astype(np.float32), (1.0 / d).astype(np.float32), bd, tol=1e-9)
+    # a diagonal system: every inner solve ends at its first half step
+    assert res.status == O.OK and res.iterations == res.outer_iterations
+    np.testing.assert_allclose(res.x, bd / d, rtol=1e-9)
+
+
 # ---------------------------------------------------------------- line (block-tridiagonal) preconditioner
 
 
