@@ -272,7 +272,8 @@ def run_adjoint(dev, reps=3):
 
 def run_bicgstab(dev, steps, warmup, draws=2):
     """Non-symmetric momentum system on the headline mesh (256^3, k = 128): per step a
-    value update (new coefficient draw) + rp_solve_bicgstab to 1e-9 from x = 0, FP64."""
+    value update (new coefficient draw) + a BiCGStab solve to 1e-9 from x = 0, in FP64
+    (rp_solve_bicgstab) and as FP32-inner / FP64-outer refinement (rp_solve_bicgstab_mixed)."""
     import torch
 
     from paper_2510_08536_gb300 import repart, synth
@@ -282,30 +283,34 @@ def run_bicgstab(dev, steps, warmup, draws=2):
     b = torch.from_numpy(synth.uniform_vector(mesh, 0)).to(dev)
     x = torch.zeros(mesh.n_cells, dtype=torch.float64, device=dev)
     setup_s = time.time() - t0
-    h = repart.build_repartition(mesh.ranks, want_fp32=False)
+    h = repart.build_repartition(mesh.ranks)
     n, sliced = mesh.n_cells, repart.sliced_sizes(h)
     entries = sliced[1] if sliced else h.nnz
-    for t in range(warmup):
-        repart.update_values_packed(h, stg[t % draws])
-        repart.solve_bicgstab(h, b, x, tol=1e-9)
-    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    infos = []
-    e0.record(stream)
-    for t in range(steps):
-        repart.update_values_packed(h, stg[(warmup + t) % draws])
-        infos.append(repart.solve_bicgstab(h, b, x, tol=1e-9))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+    runs = {}
+    for prec in ("fp64", "mixed"):
+        for t in range(warmup):
+            repart.update_values_packed(h, stg[t % draws])
+            repart.solve_bicgstab(h, b, x, tol=1e-9, precision=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(stream)
+        for t in range(steps):
+            repart.update_values_packed(h, stg[(warmup + t) % draws])
+            infos.append(repart.solve_bicgstab(h, b, x, tol=1e-9, precision=prec))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        runs[prec] = (e0.elapsed_time(e1) / steps, infos)
     h.close()
+    ms, infos = runs["fp64"]
     it = statistics.mean(i["iterations"] for i in infos)
     # per iteration: two products (one FMA per stored entry + the fused dots) and
     # ~14 FP64 instructions per row in the three vector kernels
     ops = it * (2 * entries + 14 * n)
     peak = fp64_peak_tflops(dev, MAX_SM_MHZ)
     ach = 2 * ops / (ms * 1e-3) / 1e12
+    mms, minfos = runs["mixed"]
     return {"workload": "momentum_256: 256^3 cells, k=128 (8x4x4) merged, upwind convection-diffusion "
                         "(lognormal(0,0.5) diffusion, cavity-vortex flux, ct=0.1), rhs U[-1,1] seed 0, "
                         "rel. residual 1e-9 from x=0, FP64",
@@ -313,7 +318,12 @@ def run_bicgstab(dev, steps, warmup, draws=2):
             "statuses": sorted({i["status"] for i in infos}),
             "max_rel_residual": max(i["rel_residual"] for i in infos), "input_setup_s": round(setup_s, 1),
             "fp64_alu": {"bound": "alu", "unit": "TFLOP/s", "achieved": round(ach, 4), "peak": round(peak, 4),
-                         "frac": round(ach / peak, 4)}}
+                         "frac": round(ach / peak, 4)},
+            "mixed": {"ms_per_step": round(mms, 3),
+                      "inner_iterations_mean": statistics.mean(i["iterations"] for i in minfos),
+                      "refinements_mean": statistics.mean(i["outer_iterations"] for i in minfos),
+                      "statuses": sorted({i["status"] for i in minfos}),
+                      "max_rel_residual": max(i["rel_residual"] for i in minfos)}}
 
 
 # ---------------------------------------------------------------- batched form

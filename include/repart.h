@@ -311,6 +311,21 @@ rp_status rp_solve(rp_handle* h, const double* b, double* x, double tol, int32_t
 rp_status rp_solve_bicgstab(rp_handle* h, const double* b, double* x, double tol, int32_t x_is_guess,
                             int32_t where, rp_solve_info* info, void* stream);
 
+/* The same system by FP32-inner / FP64-outer iterative refinement (needs
+ * want_fp32): repeat { r = b - A x with the FP64 values (true residual); stop
+ * when ||r|| <= tol ||b||; solve A32 d = fl32(r) by Jacobi-preconditioned
+ * BiCGStab on the FP32 values, vectors and products (dot products combined in
+ * FP64; alpha, omega, beta rounded to FP32), from d = 0 with the shadow
+ * residual fl32(r), to ||r_inner|| <= inner_tol ||fl32(r)|| (a half step counts
+ * with ||s||); x += d in FP64 }. max_outer caps the refinements, max_iter the
+ * inner iterations of all refinements together (RP_NOT_CONVERGED); a
+ * breakdown of an inner solve ends with RP_BREAKDOWN. info->iterations =
+ * inner iterations, info->outer_iterations = refinements, rel_residual = the
+ * last FP64 residual. Other arguments as in rp_solve_bicgstab. Allocates five
+ * FP32 n-vectors on first use. */
+rp_status rp_solve_bicgstab_mixed(rp_handle* h, const double* b, double* x, double tol, int32_t x_is_guess,
+                                  int32_t where, rp_solve_info* info, void* stream);
+
 /* ---- Batched form: many independent systems in one persistent launch ----
  * Each system is one LDU matrix without interfaces (n_iface = 0); system s
  * becomes GPU part s (n_parts = count, alpha = 1, Sec. 3). Rows, buffers and

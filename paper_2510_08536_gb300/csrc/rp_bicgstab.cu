@@ -1,6 +1,7 @@
 // Jacobi-preconditioned BiCGStab (van der Vorst, 1992) on the merged matrix:
 // the solver of the non-symmetric momentum system (the paper solves momentum
-// with BiCGStab, pressure with CG; Sec. 4). FP64 throughout.
+// with BiCGStab, pressure with CG; Sec. 4). FP64 throughout, or (mixed) an
+// FP32 BiCGStab on the FP32 values inside FP64 iterative refinement.
 //
 // One CUDA graph per handle: while (outer) { residual pass; while (inner) {
 // B1; B2; B3; B4; B5 } }, every loop bounded by device counters.
@@ -17,8 +18,13 @@
 // memory and are written only by the last block of a kernel. The SpMVs run
 // over the sliced layout when the handle has it (spmv_sl_body), else CSR.
 //
+// Mixed: while (outer) { FP64 residual pass r = b - A x, r32 = fl(r), d = 0;
+// while (inner) { B1..B5 in FP32 on d } ; x += d }, the inner loop stopping
+// at inner_tol relative to its start (a new shadow residual every pass).
+//
 // Roofline: FP64-FMA bound on GB300 (one FMA per stored entry per product,
-// two products per iteration, ~14 FP64 instructions per row in B1/B3/B5).
+// two products per iteration, ~14 FP64 instructions per row in B1/B3/B5); the
+// FP32 inner loop is bound by HBM and the products' gathers instead.
 #include "rp_common.cuh"
 #include "rp_spmv.cuh"
 
@@ -27,19 +33,29 @@ namespace rp {
 struct BsCtl {
   double bb, thresh, tol, rr, ss;
   double rho, rho_old, alpha, omega;
+  double ithresh, inner_tol;  // the inner loop's target: thresh (FP64); inner_tol^2 (r32, r32) (mixed)
   int32_t iter, max_iter, stop, status, pass, restarts, max_restarts, half, x_zero;
+  int32_t outer, max_outer;
   unsigned int ticket;
+};
+
+// the vectors and the matrix of one working precision
+template <typename T>
+struct BsVecs {
+  const T* vals;
+  const T* dinv;
+  Parts<T> parts;
+  Sliced<T> sl;
+  T *r, *rhat, *p, *v, *s, *t, *phat, *shat;
+  T* x;  // FP32: the correction d; FP64: unused (the caller's x, through SolveIO)
 };
 
 struct BsArgs {
   int64_t n;
   const int32_t* row_ptr;
   const int32_t* col;
-  const double* vals;
-  const double* dinv;
-  Parts<double> parts;
-  Sliced<double> sl;
-  double *r, *rhat, *p, *v, *s, *t, *phat, *shat;
+  BsVecs<double> d;  // FP64 solve; its matrix also serves the residual passes
+  BsVecs<float> f;   // FP32 inner solve (mixed)
   BsCtl* c;
   SolveIO* io;
   double* partials;
@@ -49,22 +65,37 @@ struct BsArgs {
 
 struct BsState {
   double *rhat = nullptr, *s = nullptr, *t = nullptr, *phat = nullptr, *shat = nullptr;
+  float *rhat32 = nullptr, *s32 = nullptr, *t32 = nullptr, *phat32 = nullptr, *shat32 = nullptr;
   BsCtl* ctl = nullptr;
   SolveIO* io = nullptr;
-  cudaGraphExec_t graph = nullptr;
-  int grid_vec = 1, grid_sl = 1;
+  cudaGraphExec_t graph = nullptr, graph_mixed = nullptr;
+  int grid_vec = 1, grid_sl = 1, grid_sl32 = 1;
 };
 
 namespace {
 
+template <typename T>
+__device__ __forceinline__ const BsVecs<T>& vecs(const BsArgs& a);
+template <>
+__device__ __forceinline__ const BsVecs<double>& vecs<double>(const BsArgs& a) {
+  return a.d;
+}
+template <>
+__device__ __forceinline__ const BsVecs<float>& vecs<float>(const BsArgs& a) {
+  return a.f;
+}
+
 __global__ void k_bs_setup(BsCtl* c, SolveIO* io, const double* b, double* x, double tol, int x_zero, int max_iter,
-                           int max_restarts) {
+                           int max_restarts, int max_outer, double inner_tol) {
   io->b = b;
   io->x = x;
   c->tol = tol;
   c->x_zero = x_zero;
   c->max_iter = max_iter;
   c->max_restarts = max_restarts;
+  c->max_outer = max_outer;
+  c->inner_tol = inner_tol;
+  c->outer = 0;
   c->iter = 0;
   c->pass = 0;
   c->restarts = 0;
@@ -89,12 +120,12 @@ __global__ void __launch_bounds__(kThreads) k_bs_res(BsArgs a) {
       ri = bi;
       x[i] = 0.0;
     } else {
-      ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
+      ri = bi - row_dot_any<double>(a.d.parts, a.row_ptr, a.col, a.d.vals, x, i);
     }
-    a.r[i] = ri;
-    a.rhat[i] = ri;
-    a.p[i] = 0.0;
-    a.v[i] = 0.0;
+    a.d.r[i] = ri;
+    a.d.rhat[i] = ri;
+    a.d.p[i] = 0.0;
+    a.d.v[i] = 0.0;
     rr += ri * ri;
     bb += bi * bi;
   }
@@ -119,6 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_bs_res(BsArgs a) {
       c->rho = tot[0];  // (rhat, r) with rhat = r
       c->rho_old = c->alpha = c->omega = 1.0;
       c->half = 0;
+      c->ithresh = c->thresh;
       go = true;
     }
     c->stop = go ? 0 : 1;
@@ -129,31 +161,105 @@ __global__ void __launch_bounds__(kThreads) k_bs_res(BsArgs a) {
   }
 }
 
+// mixed residual pass: r = b - A x in FP64 (cold start: r = b, x = 0); the FP32
+// inner solve starts from r32 = fl(r), rhat = r32, p = v = d = 0; decides
+__global__ void __launch_bounds__(kThreads) k_bs_res_mixed(BsArgs a) {
+  BsCtl* c = a.c;
+  const bool first = c->pass == 0;
+  const bool cold = first && c->x_zero;
+  const double* __restrict__ b = a.io->b;
+  double* __restrict__ x = a.io->x;
+  const BsVecs<float>& F = a.f;
+  double rr = 0.0, bb = 0.0;
+  float ff = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    double ri;
+    if (cold) {
+      ri = bi;
+      x[i] = 0.0;
+    } else {
+      ri = bi - row_dot_any<double>(a.d.parts, a.row_ptr, a.col, a.d.vals, x, i);
+    }
+    const float r32 = (float)ri;
+    F.r[i] = r32;
+    F.rhat[i] = r32;
+    F.p[i] = 0.f;
+    F.v[i] = 0.f;
+    F.x[i] = 0.f;
+    rr += ri * ri;
+    bb += bi * bi;
+    ff = fmaf(r32, r32, ff);
+  }
+  double v[3] = {rr, bb, (double)ff}, tot[3];
+  if (reduce_last_block<3>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
+    if (first) {
+      c->bb = tot[1];
+      c->thresh = c->tol * c->tol * tot[1];
+    }
+    c->rr = tot[0];
+    c->pass += 1;
+    bool go = false;
+    if (tot[0] <= c->thresh) {
+      c->status = RP_OK;
+    } else if (c->status == RP_BREAKDOWN || c->status == RP_DEVICE_TIMEOUT) {
+    } else if (!isfinite(tot[0])) {
+      c->status = RP_BREAKDOWN;
+    } else if (c->iter >= c->max_iter || c->outer >= c->max_outer) {
+      c->status = RP_NOT_CONVERGED;
+    } else {
+      c->outer += 1;
+      c->rho = tot[2];  // (rhat, r) with rhat = r32
+      c->rho_old = c->alpha = c->omega = 1.0;
+      c->half = 0;
+      c->ithresh = c->inner_tol * c->inner_tol * tot[2];
+      go = true;
+    }
+    c->stop = go ? 0 : 1;
+    if (a.in_graph) {
+      cudaGraphSetConditional(a.inner, go ? 1u : 0u);
+      cudaGraphSetConditional(a.outer, go ? 1u : 0u);
+    }
+  }
+}
+
+// x += d in FP64 after an inner solve (not after a breakdown or a timeout, nor
+// when the residual pass has ended the solve)
+__global__ void __launch_bounds__(kThreads) k_bs_correct(BsArgs a) {
+  if (a.c->status >= 0) return;
+  double* __restrict__ x = a.io->x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)a.f.x[i];
+}
+
 // B1: p = r + beta (p - omega v); phat = D^-1 p
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bs_p(BsArgs a) {
   const BsCtl* c = a.c;
   if (c->stop) return;
-  const double beta = (c->rho / c->rho_old) * (c->alpha / c->omega), omega = c->omega;
+  const BsVecs<T>& V = vecs<T>(a);
+  const T beta = (T)((c->rho / c->rho_old) * (c->alpha / c->omega)), omega = (T)c->omega;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double pi = fma(beta, fma(-omega, a.v[i], a.p[i]), a.r[i]);
-    a.p[i] = pi;
-    a.phat[i] = a.dinv[i] * pi;
+    const T pi = fma(beta, fma(-omega, V.v[i], V.p[i]), V.r[i]);
+    V.p[i] = pi;
+    V.phat[i] = V.dinv[i] * pi;
   }
 }
 
 // B2 epilogue: (rhat, v) -> alpha
+template <typename T>
 struct BsEpiV {
-  const double* rhat;
+  const T* rhat;
   BsCtl* c;
   double* partials;
-  double acc = 0.0;
-  __device__ __forceinline__ void row(int64_t i, double y) { acc = fma(rhat[i], y, acc); }
+  T acc = T(0);
+  __device__ __forceinline__ void row(int64_t i, T y) { acc = fma(rhat[i], y, acc); }
   __device__ __forceinline__ void timeout() {
     c->status = RP_DEVICE_TIMEOUT;
     c->stop = 1;
   }
   __device__ __forceinline__ void finish() {
-    double v[1] = {acc}, tot[1];
+    double v[1] = {(double)acc}, tot[1];
     if (reduce_last_block<1>(v, partials, &c->ticket, tot) && threadIdx.x == 0) {
       if (c->status == RP_DEVICE_TIMEOUT) {
         c->stop = 1;
@@ -168,12 +274,13 @@ struct BsEpiV {
 };
 
 // B4 epilogue: (t, s), (t, t) -> omega
+template <typename T>
 struct BsEpiT {
-  const double* s;
+  const T* s;
   BsCtl* c;
   double* partials;
-  double ts = 0.0, tt = 0.0;
-  __device__ __forceinline__ void row(int64_t i, double y) {
+  T ts = T(0), tt = T(0);
+  __device__ __forceinline__ void row(int64_t i, T y) {
     ts = fma(y, s[i], ts);
     tt = fma(y, y, tt);
   }
@@ -182,7 +289,7 @@ struct BsEpiT {
     c->stop = 1;
   }
   __device__ __forceinline__ void finish() {
-    double v[2] = {ts, tt}, tot[2];
+    double v[2] = {(double)ts, (double)tt}, tot[2];
     if (reduce_last_block<2>(v, partials, &c->ticket, tot) && threadIdx.x == 0) {
       const double omega = tot[0] / tot[1];
       if (c->status == RP_DEVICE_TIMEOUT) {
@@ -198,75 +305,83 @@ struct BsEpiT {
 };
 
 // B2 / B4 over CSR (any number of parts) or the sliced layout
-template <int WHICH>
+template <int WHICH, typename T>
 __global__ void __launch_bounds__(kThreads) k_bs_spmv(BsArgs a) {
   BsCtl* c = a.c;
   if (c->stop || (WHICH == 2 && c->half)) return;
+  const BsVecs<T>& V = vecs<T>(a);
   if constexpr (WHICH == 1) {
-    BsEpiV e{a.rhat, c, a.partials};
-    spmv_csr_body<double>(a.n, a.parts, a.row_ptr, a.col, a.vals, a.phat, a.v, e);
+    BsEpiV<T> e{V.rhat, c, a.partials};
+    spmv_csr_body<T>(a.n, V.parts, a.row_ptr, a.col, V.vals, V.phat, V.v, e);
   } else {
-    BsEpiT e{a.s, c, a.partials};
-    spmv_csr_body<double>(a.n, a.parts, a.row_ptr, a.col, a.vals, a.shat, a.t, e);
+    BsEpiT<T> e{V.s, c, a.partials};
+    spmv_csr_body<T>(a.n, V.parts, a.row_ptr, a.col, V.vals, V.shat, V.t, e);
   }
 }
-template <int WHICH, bool MP>
-__global__ void __launch_bounds__(kSlThreads, 5) k_bs_spmv_sl(BsArgs a) {
+template <int WHICH, bool MP, typename T>
+__global__ void __launch_bounds__(kSlThreads, sizeof(T) == 4 ? 7 : 5) k_bs_spmv_sl(BsArgs a) {
   BsCtl* c = a.c;
   if (c->stop || (WHICH == 2 && c->half)) return;
+  const BsVecs<T>& V = vecs<T>(a);
   if constexpr (WHICH == 1) {
-    BsEpiV e{a.rhat, c, a.partials};
-    spmv_sl_body<double, MP>(a.sl, a.parts, a.n, a.phat, a.v, e);
+    BsEpiV<T> e{V.rhat, c, a.partials};
+    spmv_sl_body<T, MP>(V.sl, V.parts, a.n, V.phat, V.v, e);
   } else {
-    BsEpiT e{a.s, c, a.partials};
-    spmv_sl_body<double, MP>(a.sl, a.parts, a.n, a.shat, a.t, e);
+    BsEpiT<T> e{V.s, c, a.partials};
+    spmv_sl_body<T, MP>(V.sl, V.parts, a.n, V.shat, V.t, e);
   }
 }
 
 // B3: s = r - alpha v; shat = D^-1 s; (s, s)
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bs_s(BsArgs a) {
   BsCtl* c = a.c;
   if (c->stop) return;
-  const double alpha = c->alpha;
-  double ss = 0.0;
+  const BsVecs<T>& V = vecs<T>(a);
+  const T alpha = (T)c->alpha;
+  T ss = T(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double si = fma(-alpha, a.v[i], a.r[i]);
-    a.s[i] = si;
-    a.shat[i] = a.dinv[i] * si;
+    const T si = fma(-alpha, V.v[i], V.r[i]);
+    V.s[i] = si;
+    V.shat[i] = V.dinv[i] * si;
     ss = fma(si, si, ss);
   }
-  double v[1] = {ss}, tot[1];
+  double v[1] = {(double)ss}, tot[1];
   if (reduce_last_block<1>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
     c->ss = tot[0];
-    c->half = tot[0] <= c->thresh ? 1 : 0;
+    c->half = tot[0] <= c->ithresh ? 1 : 0;
   }
 }
 
 // B5: x += alpha phat + omega shat; r = s - omega t; (r, r), (rhat, r)
 // (half step: x += alpha phat; r = s); decides the next iteration
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bs_xr(BsArgs a) {
   BsCtl* c = a.c;
   if (c->stop) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.in_graph) cudaGraphSetConditional(a.inner, 0);
     return;
   }
+  const BsVecs<T>& V = vecs<T>(a);
   const bool half = c->half;
-  const double alpha = c->alpha, omega = c->omega;
-  double* __restrict__ x = a.io->x;
-  double rr = 0.0, rhr = 0.0;
+  const T alpha = (T)c->alpha, omega = (T)c->omega;
+  T* __restrict__ x;
+  if constexpr (sizeof(T) == 8) x = a.io->x;
+  else x = V.x;
+  T rr = T(0), rhr = T(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     if (half) {
-      x[i] = fma(alpha, a.phat[i], x[i]);
-      a.r[i] = a.s[i];
+      x[i] = fma(alpha, V.phat[i], x[i]);
+      V.r[i] = V.s[i];
     } else {
-      x[i] = fma(omega, a.shat[i], fma(alpha, a.phat[i], x[i]));
-      const double ri = fma(-omega, a.t[i], a.s[i]);
-      a.r[i] = ri;
+      x[i] = fma(omega, V.shat[i], fma(alpha, V.phat[i], x[i]));
+      const T ri = fma(-omega, V.t[i], V.s[i]);
+      V.r[i] = ri;
       rr = fma(ri, ri, rr);
-      rhr = fma(a.rhat[i], ri, rhr);
+      rhr = fma(V.rhat[i], ri, rhr);
     }
   }
-  double v[2] = {rr, rhr}, tot[2];
+  double v[2] = {(double)rr, (double)rhr}, tot[2];
   if (reduce_last_block<2>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {
     c->iter += 1;
     if (half) {
@@ -274,7 +389,7 @@ __global__ void __launch_bounds__(kThreads) k_bs_xr(BsArgs a) {
       c->stop = 1;  // the residual pass confirms with b - A x
     } else {
       c->rr = tot[0];
-      if (tot[0] <= c->thresh) {
+      if (tot[0] <= c->ithresh) {
         c->stop = 1;
       } else if (c->iter >= c->max_iter) {
         c->stop = 1;
@@ -322,13 +437,21 @@ rp_status ensure_bs(rp_handle* h) {
   RP_TRY(balloc(&b->shat, n));
   RP_TRY(balloc(&b->ctl, 1));
   RP_TRY(balloc(&b->io, 1));
+  if (h->want_fp32) {
+    RP_TRY(balloc(&b->rhat32, n));
+    RP_TRY(balloc(&b->s32, n));
+    RP_TRY(balloc(&b->t32, n));
+    RP_TRY(balloc(&b->phat32, n));
+    RP_TRY(balloc(&b->shat32, n));
+  }
   const int64_t want = (h->n + kThreads - 1) / kThreads;
   auto grid = [&](int per_sm) {
     const int64_t cap = (int64_t)h->num_sms * per_sm;
     return (int)(want < 1 ? 1 : want < cap ? want : cap);
   };
-  b->grid_vec = grid(resident_blocks((const void*)k_bs_xr, kThreads, 0));
-  b->grid_sl = grid(resident_blocks((const void*)k_bs_spmv_sl<2, false>, kSlThreads, SlStage<double>::kSmem));
+  b->grid_vec = grid(resident_blocks((const void*)k_bs_xr<double>, kThreads, 0));
+  b->grid_sl = grid(resident_blocks((const void*)k_bs_spmv_sl<2, false, double>, kSlThreads, SlStage<double>::kSmem));
+  b->grid_sl32 = grid(resident_blocks((const void*)k_bs_spmv_sl<2, false, float>, kSlThreads, SlStage<float>::kSmem));
   return RP_OK;
 }
 
@@ -338,18 +461,34 @@ BsArgs bs_args(rp_handle* h, cudaGraphConditionalHandle inner, cudaGraphConditio
   a.n = h->n;
   a.row_ptr = h->row_ptr;
   a.col = h->col_idx;
-  a.vals = h->vals;
-  a.dinv = h->dinv;
-  a.parts = parts64(h);
-  a.sl = sliced64(h, h->vals);
-  a.r = h->r;
-  a.rhat = b->rhat;
-  a.p = h->p;
-  a.v = h->q;
-  a.s = b->s;
-  a.t = b->t;
-  a.phat = b->phat;
-  a.shat = b->shat;
+  a.d.vals = h->vals;
+  a.d.dinv = h->dinv;
+  a.d.parts = parts64(h);
+  a.d.sl = sliced64(h, h->vals);
+  a.d.r = h->r;
+  a.d.rhat = b->rhat;
+  a.d.p = h->p;
+  a.d.v = h->q;
+  a.d.s = b->s;
+  a.d.t = b->t;
+  a.d.phat = b->phat;
+  a.d.shat = b->shat;
+  a.d.x = nullptr;
+  if (h->want_fp32) {
+    a.f.vals = h->vals32;
+    a.f.dinv = h->dinv32;
+    a.f.parts = parts32(h);
+    a.f.sl = sliced32(h);
+    a.f.r = h->r32;
+    a.f.rhat = b->rhat32;
+    a.f.p = h->p32;
+    a.f.v = h->q32;
+    a.f.s = b->s32;
+    a.f.t = b->t32;
+    a.f.phat = b->phat32;
+    a.f.shat = b->shat32;
+    a.f.x = h->d32;
+  }
   a.c = b->ctl;
   a.io = b->io;
   a.partials = h->partials;
@@ -390,19 +529,24 @@ struct BsLaunch {
   void* fn;
   int grid, threads, smem;
 };
+template <typename T>
 void bs_inner(const rp_handle* h, BsLaunch (&k)[5]) {
   const BsState* b = h->bs;
-  const bool sl = h->sl_slices > 0;  // as sliced64
-  const int gs = sl ? b->grid_sl : h->grid, ts = sl ? kSlThreads : kThreads, ms = sl ? SlStage<double>::kSmem : 0;
-  k[0] = {(void*)k_bs_p, b->grid_vec, kThreads, 0};
+  const bool sl = h->sl_slices > 0 && (sizeof(T) == 8 || h->sl_vals32);  // as sliced64 / sliced32
+  const int gs = sl ? (sizeof(T) == 8 ? b->grid_sl : b->grid_sl32) : h->grid, ts = sl ? kSlThreads : kThreads;
+  const int ms = sl ? SlStage<T>::kSmem : 0;
   const bool mp = h->sl_srow != nullptr;
-  k[1] = {sl ? (mp ? (void*)k_bs_spmv_sl<1, true> : (void*)k_bs_spmv_sl<1, false>) : (void*)k_bs_spmv<1>, gs, ts, ms};
-  k[2] = {(void*)k_bs_s, b->grid_vec, kThreads, 0};
-  k[3] = {sl ? (mp ? (void*)k_bs_spmv_sl<2, true> : (void*)k_bs_spmv_sl<2, false>) : (void*)k_bs_spmv<2>, gs, ts, ms};
-  k[4] = {(void*)k_bs_xr, b->grid_vec, kThreads, 0};
+  k[0] = {(void*)k_bs_p<T>, b->grid_vec, kThreads, 0};
+  k[1] = {sl ? (mp ? (void*)k_bs_spmv_sl<1, true, T> : (void*)k_bs_spmv_sl<1, false, T>) : (void*)k_bs_spmv<1, T>, gs,
+          ts, ms};
+  k[2] = {(void*)k_bs_s<T>, b->grid_vec, kThreads, 0};
+  k[3] = {sl ? (mp ? (void*)k_bs_spmv_sl<2, true, T> : (void*)k_bs_spmv_sl<2, false, T>) : (void*)k_bs_spmv<2, T>, gs,
+          ts, ms};
+  k[4] = {(void*)k_bs_xr<T>, b->grid_vec, kThreads, 0};
 }
 
-rp_status build_bs_graph(rp_handle* h, cudaGraphExec_t* exec) {
+// mixed: the FP64 residual pass, the FP32 inner loop, then the correction
+rp_status build_bs_graph(rp_handle* h, bool mixed, cudaGraphExec_t* exec) {
   cudaGraph_t top = nullptr;
   RP_TRY_CUDA(cudaGraphCreate(&top, 0));
   struct Guard {
@@ -416,25 +560,32 @@ rp_status build_bs_graph(rp_handle* h, cudaGraphExec_t* exec) {
   RP_TRY(while_node(top, &wout, nullptr, hout, &obody));
   RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hin, obody, 0, 0));
   BsArgs a = bs_args(h, hin, hout, 1);
-  RP_TRY(node(obody, &nres, nullptr, (void*)k_bs_res, h->grid, kThreads, 0, &a));
+  RP_TRY(node(obody, &nres, nullptr, mixed ? (void*)k_bs_res_mixed : (void*)k_bs_res, h->grid, kThreads, 0, &a));
   RP_TRY(while_node(obody, &win, &nres, hin, &ibody));
   BsLaunch k[5];
-  bs_inner(h, k);
+  if (mixed) bs_inner<float>(h, k);
+  else bs_inner<double>(h, k);
   for (int j = 0; j < 5; ++j)
     RP_TRY(node(ibody, &nk[j], j ? &nk[j - 1] : nullptr, k[j].fn, k[j].grid, k[j].threads, k[j].smem, &a));
+  if (mixed) {
+    cudaGraphNode_t ncor;
+    RP_TRY(node(obody, &ncor, &win, (void*)k_bs_correct, h->bs->grid_vec, kThreads, 0, &a));
+  }
   RP_TRY_CUDA(cudaGraphInstantiate(exec, top, 0));
   return RP_OK;
 }
 
 // the same kernel sequence launched from the host (profilers that cannot see
 // inside conditional graphs); the control block is read after every kernel group
-rp_status bs_host_loop(rp_handle* h, cudaStream_t s) {
+rp_status bs_host_loop(rp_handle* h, bool mixed, cudaStream_t s) {
   BsArgs a = bs_args(h, 0, 0, 0);
   BsLaunch k[5];
-  bs_inner(h, k);
+  if (mixed) bs_inner<float>(h, k);
+  else bs_inner<double>(h, k);
   BsCtl c;
   for (;;) {
-    k_bs_res<<<h->grid, kThreads, 0, s>>>(a);
+    if (mixed) k_bs_res_mixed<<<h->grid, kThreads, 0, s>>>(a);
+    else k_bs_res<<<h->grid, kThreads, 0, s>>>(a);
     RP_TRY_CUDA(cudaGetLastError());
     RP_TRY_CUDA(cudaMemcpyAsync(&c, h->bs->ctl, sizeof(BsCtl), cudaMemcpyDeviceToHost, s));
     RP_TRY_CUDA(cudaStreamSynchronize(s));
@@ -447,6 +598,10 @@ rp_status bs_host_loop(rp_handle* h, cudaStream_t s) {
       RP_TRY_CUDA(cudaMemcpyAsync(&c, h->bs->ctl, sizeof(BsCtl), cudaMemcpyDeviceToHost, s));
       RP_TRY_CUDA(cudaStreamSynchronize(s));
     }
+    if (mixed) {
+      k_bs_correct<<<h->bs->grid_vec, kThreads, 0, s>>>(a);
+      RP_TRY_CUDA(cudaGetLastError());
+    }
   }
   return RP_OK;
 }
@@ -454,19 +609,21 @@ rp_status bs_host_loop(rp_handle* h, cudaStream_t s) {
 }  // namespace
 
 void drop_bicgstab_graph(rp_handle* h) {
-  if (h->bs && h->bs->graph) {
-    cudaGraphExecDestroy(h->bs->graph);
-    h->bs->graph = nullptr;
-  }
+  if (!h->bs) return;
+  for (cudaGraphExec_t* g : {&h->bs->graph, &h->bs->graph_mixed})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
 }
 
 void free_bicgstab(rp_handle* h) {
   BsState* b = h->bs;
   if (!b) return;
-  void* ptrs[] = {b->rhat, b->s, b->t, b->phat, b->shat, b->ctl, b->io};
+  void* ptrs[] = {b->rhat, b->s, b->t, b->phat, b->shat, b->rhat32, b->s32, b->t32, b->phat32, b->shat32, b->ctl, b->io};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  if (b->graph) cudaGraphExecDestroy(b->graph);
+  drop_bicgstab_graph(h);
   delete b;
   h->bs = nullptr;
 }
@@ -475,11 +632,15 @@ void free_bicgstab(rp_handle* h) {
 
 using namespace rp;
 
-extern "C" rp_status rp_solve_bicgstab(rp_handle* h, const double* b, double* x, double tol, int32_t x_is_guess,
-                                       int32_t where, rp_solve_info* info, void* stream) {
+namespace rp {
+namespace {
+
+rp_status bicgstab_run(rp_handle* h, bool mixed, const double* b, double* x, double tol, int32_t x_is_guess,
+                       int32_t where, rp_solve_info* info, void* stream) {
   if (!h || (!b && h->n) || (!x && h->n)) return fail(RP_EINVAL, "null argument");
   if (!(tol >= 0.0)) return fail(RP_EINVAL, "tol must be >= 0");
   if (where != RP_MEM_DEVICE && where != RP_MEM_HOST) return fail(RP_EINVAL, "where must be RP_MEM_DEVICE or RP_MEM_HOST");
+  if (mixed && !h->want_fp32) return fail(RP_EINVAL, "mixed precision needs want_fp32");
   if (h->n == 0) {
     if (info) *info = rp_solve_info{RP_OK, 0, 0, 0, 0, 0.0};
     return RP_OK;
@@ -487,7 +648,8 @@ extern "C" rp_status rp_solve_bicgstab(rp_handle* h, const double* b, double* x,
   cudaStream_t s = (cudaStream_t)stream;
   RP_TRY(ensure_bs(h));
   BsState* bs = h->bs;
-  if (!bs->graph && !h->opts.host_loop) RP_TRY(build_bs_graph(h, &bs->graph));
+  cudaGraphExec_t& graph = mixed ? bs->graph_mixed : bs->graph;
+  if (!graph && !h->opts.host_loop) RP_TRY(build_bs_graph(h, mixed, &graph));
   const double* bd = b;
   double* xd = x;
   if (where == RP_MEM_HOST) {
@@ -501,10 +663,10 @@ extern "C" rp_status rp_solve_bicgstab(rp_handle* h, const double* b, double* x,
     xd = h->x_host_stage;
   }
   k_bs_setup<<<1, 1, 0, s>>>(bs->ctl, bs->io, bd, xd, tol, x_is_guess ? 0 : 1, h->opts.max_iter,
-                             h->opts.max_restarts);
+                             h->opts.max_restarts, h->opts.max_outer, h->opts.inner_tol);
   RP_TRY_CUDA(cudaGetLastError());
-  if (h->opts.host_loop) RP_TRY(bs_host_loop(h, s));
-  else RP_TRY_CUDA(cudaGraphLaunch(bs->graph, s));
+  if (h->opts.host_loop) RP_TRY(bs_host_loop(h, mixed, s));
+  else RP_TRY_CUDA(cudaGraphLaunch(graph, s));
   if (where == RP_MEM_HOST) RP_TRY_CUDA(cudaMemcpyAsync(x, h->x_host_stage, 8 * h->n, cudaMemcpyDeviceToHost, s));
   if (!info) return RP_OK;
   BsCtl c;
@@ -512,9 +674,22 @@ extern "C" rp_status rp_solve_bicgstab(rp_handle* h, const double* b, double* x,
   RP_TRY_CUDA(cudaStreamSynchronize(s));
   info->status = c.status < 0 ? RP_NOT_CONVERGED : c.status;
   info->iterations = c.iter;
-  info->outer_iterations = 0;
+  info->outer_iterations = mixed ? c.outer : 0;
   info->restarts = c.restarts;
   info->passes = c.pass;
   info->rel_residual = c.bb > 0.0 ? sqrt(c.rr / c.bb) : 0.0;
   return (rp_status)info->status;
+}
+
+}  // namespace
+}  // namespace rp
+
+extern "C" rp_status rp_solve_bicgstab(rp_handle* h, const double* b, double* x, double tol, int32_t x_is_guess,
+                                       int32_t where, rp_solve_info* info, void* stream) {
+  return bicgstab_run(h, false, b, x, tol, x_is_guess, where, info, stream);
+}
+
+extern "C" rp_status rp_solve_bicgstab_mixed(rp_handle* h, const double* b, double* x, double tol,
+                                             int32_t x_is_guess, int32_t where, rp_solve_info* info, void* stream) {
+  return bicgstab_run(h, true, b, x, tol, x_is_guess, where, info, stream);
 }

@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_float), vp]),
         "rp_solve": (i32, [vp, vp, vp, dbl, i32, i32, i32, ctypes.POINTER(SolveInfo), vp]),
         "rp_solve_bicgstab": (i32, [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveInfo), vp]),
+        "rp_solve_bicgstab_mixed": (i32, [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveInfo), vp]),
         "rp_solve_adjoint": (i32, [vp, vp, vp, dbl, ctypes.POINTER(SolveInfo), vp]),
         "rp_profile_iteration": (i32, [vp, vp, i32, i32, ctypes.POINTER(ctypes.c_float), vp]),
         "rp_entry_grad": (i32, [vp, vp, vp, vp, vp]),
@@ -380,15 +381,20 @@ def solve(h: Handle, b, x, tol: float = 1e-9, precision: str = "fp64", x_is_gues
 
 
 def solve_bicgstab(h: Handle, b, x, tol: float = 1e-9, x_is_guess: bool = False, stream=None,
-                   wait: bool = True, raise_on_status: bool = False):
-    """rp_solve_bicgstab (non-symmetric systems); returns the SolveInfo as a dict when ``wait``."""
+                   wait: bool = True, raise_on_status: bool = False, precision: str = "fp64"):
+    """rp_solve_bicgstab (non-symmetric systems; precision "fp64") or
+    rp_solve_bicgstab_mixed ("mixed": FP32 inner solves in FP64 refinement);
+    returns the SolveInfo as a dict when ``wait``."""
     _f64(b, "b"); _f64(x, "x")
     if b.is_cuda != x.is_cuda:
         raise ValueError("b and x must both live on the device or both on the host")
+    if precision not in ("fp64", "mixed"):
+        raise ValueError("precision must be 'fp64' or 'mixed'")
+    name = "rp_solve_bicgstab" if precision == "fp64" else "rp_solve_bicgstab_mixed"
     info = SolveInfo()
-    st = load().rp_solve_bicgstab(h.ptr, _ptr(b), _ptr(x), float(tol), int(x_is_guess), _where(b),
-                                  ctypes.byref(info) if wait else None, _stream(stream))
-    _check(st, "rp_solve_bicgstab", ok=(RP_OK,) if raise_on_status else (RP_OK, RP_NOT_CONVERGED, RP_BREAKDOWN))
+    st = getattr(load(), name)(h.ptr, _ptr(b), _ptr(x), float(tol), int(x_is_guess), _where(b),
+                               ctypes.byref(info) if wait else None, _stream(stream))
+    _check(st, name, ok=(RP_OK,) if raise_on_status else (RP_OK, RP_NOT_CONVERGED, RP_BREAKDOWN))
     return info.as_dict() if wait else None
 
 
@@ -424,4 +430,4 @@ class Exports:
                     "rp_solve_adjoint", "rp_profile_iteration", "rp_entry_grad", "rp_face_grad", "rp_destroy", "rp_status_str",
                     "rp_last_error", "rp_spmv_noalloc", "rp_batch_build", "rp_batch_update_solve",
                     "rp_batch_set_config", "rp_batch_autotune", "rp_set_solver_options", "rp_iter_spmv",
-                    "rp_get_sliced_view", "rp_solve_bicgstab")
+                    "rp_get_sliced_view", "rp_solve_bicgstab", "rp_solve_bicgstab_mixed")

@@ -1,11 +1,14 @@
-"""rp_solve_bicgstab (Jacobi-preconditioned BiCGStab, FP64) against the oracle.
+"""rp_solve_bicgstab (Jacobi-preconditioned BiCGStab, FP64) and
+rp_solve_bicgstab_mixed (FP32 inner BiCGStab in FP64 refinement) against the oracle.
 
 Tolerances: the oracle runs the same recurrence to the same tolerance, so
 ||x - x_ref|| / ||x_ref|| <= 1e-7 at rel. residual 1e-9 (summation order and
 FMA contraction differ); the true residual of the GPU result, recomputed with
 the oracle's matrix, <= 1e-9; iteration counts within max(3, 10%) of the
 oracle's. Sliced and CSR layouts give bitwise-identical solves (same
-products, same grids at these sizes).
+products, same grids at these sizes). Mixed: the true FP64 residual <= 1e-9,
+the solution within 1e-7 of the FP64 one, inner iterations at most 1.25 x the
+oracle's (FP32 rounding order differs) + 10.
 """
 import types
 
@@ -39,6 +42,7 @@ class Mom:
         self.stg = synth.momentum_staging(self.mesh, 0.5, seed)
         (self.map,) = O.repartition_map(self.mesh.ranks, 1)
         vals = O.update_values(self.map.src_of, self.stg)
+        self.vals = vals
         self.A = O.csr_matrix(self.map.row_ptr, self.map.col_idx, vals)
         self.dinv = O.jacobi_inverse(self.map.row_ptr, self.map.col_idx, vals, self.map.diag_pos)
         self.b = synth.uniform_vector(self.mesh, 0)
@@ -46,6 +50,12 @@ class Mom:
 
     def true_rel(self, x):
         return float(np.linalg.norm(self.b - self.A @ x) / np.linalg.norm(self.b))
+
+    def mixed_ref(self, inner_tol=1e-5):
+        v32 = O.to_fp32(self.vals)
+        A32 = O.csr_matrix(self.map.row_ptr, self.map.col_idx, v32)
+        return O.bicgstab_mixed_ir(self.A, A32, np.float32(1) / v32[self.map.diag_pos], self.b, tol=1e-9,
+                                   inner_tol=inner_tol)
 
 
 MESHES = [
@@ -169,3 +179,50 @@ def test_bicgstab_on_spd_matches_pcg_solution():
     assert ib["status"] == 0 and ic["status"] == 0
     assert float(torch.linalg.norm(xb - xc) / torch.linalg.norm(xc)) <= 1e-8
     h.close()
+
+
+@pytest.mark.parametrize("dims,parts", MESHES)
+def test_bicgstab_mixed_parity(dims, parts):
+    M = Mom(dims, parts)
+    h = repart.build_repartition(M.mesh.ranks)
+    repart.update_values_packed(h, _t(M.stg))
+    x, info = _solve(h, _t(M.b), M.n, precision="mixed")
+    ref = M.mixed_ref()
+    xs = x.cpu().numpy()
+    assert info["status"] == 0 and ref.status == O.OK, info
+    assert M.true_rel(xs) <= 1e-9
+    assert abs(info["rel_residual"] - M.true_rel(xs)) <= 1e-12
+    ref64 = O.bicgstab(M.A, M.dinv, M.b, tol=1e-12)
+    assert np.linalg.norm(xs - ref64.x) / np.linalg.norm(ref64.x) <= 1e-7
+    assert info["outer_iterations"] >= 1
+    assert info["iterations"] <= 1.25 * ref.iterations + 10, (info, ref.iterations, ref.outer_iterations)
+    h.close()
+
+
+def test_bicgstab_mixed_layouts_parts_and_edges():
+    M = Mom((24, 20, 16), (2, 2, 1))
+    hs = repart.build_repartition(M.mesh.ranks)
+    hc = repart.build_repartition(M.mesh.ranks, layout=repart.RP_LAYOUT_CSR)
+    hp = repart.build_repartition(M.mesh.ranks, n_parts=2)
+    out = []
+    for h in (hs, hc, hp):
+        repart.update_values_packed(h, _t(M.stg))
+        out.append(_solve(h, _t(M.b), M.n, precision="mixed"))
+    assert out[0][1] == out[1][1] and out[0][1]["status"] == 0
+    assert torch.equal(out[0][0], out[1][0])  # the same products and reductions on both layouts
+    assert out[2][1]["status"] == 0 and M.true_rel(out[2][0].cpu().numpy()) <= 1e-9
+    # b = 0: x = 0 without iterations; host buffers give the device result
+    x = torch.full((M.n,), 2.0, dtype=torch.float64, device=DEV)
+    info = repart.solve_bicgstab(hs, torch.zeros(M.n, dtype=torch.float64, device=DEV), x, precision="mixed")
+    assert info["status"] == 0 and info["iterations"] == 0 and not x.any()
+    xh = torch.zeros(M.n, dtype=torch.float64)
+    info_h = repart.solve_bicgstab(hs, torch.from_numpy(M.b.copy()), xh, tol=1e-9, precision="mixed")
+    assert info_h == out[0][1] and torch.equal(xh, out[0][0].cpu())
+    for h in (hs, hc, hp):
+        h.close()
+    h = repart.build_repartition(M.mesh.ranks, want_fp32=False)
+    with pytest.raises(repart.RepartError) as e:
+        repart.solve_bicgstab(h, _t(M.b), torch.zeros(M.n, dtype=torch.float64, device=DEV), precision="mixed")
+    assert e.value.status == repart.RP_EINVAL
+    h.close()
+

@@ -1,7 +1,8 @@
 """Failure detection without a GPU fault: a device wait that runs out.
 
 spin_limit = 0 makes every mbarrier wait of the sliced SpMV give up at once
-(its bulk copies are still in flight), so each block records the timeout,
+(its bulk copies are still in flight; FP64 and mixed PCG, FP64 and mixed
+BiCGStab), so each block records the timeout,
 waits (bounded) for the copies it issued, and the solve ends with
 RP_DEVICE_TIMEOUT instead of a result. The context stays usable: with the
 default limit restored, the same handle solves exactly as a fresh handle does
@@ -41,10 +42,11 @@ def test_wait_runs_out_and_context_survives():
             repart.solve(h, b, x, tol=1e-9, precision=precision)
         assert e.value.status == repart.RP_DEVICE_TIMEOUT, precision
     repart.update_values_packed(h, mstg)
-    x = torch.zeros(n, dtype=torch.float64, device=DEV)
-    with pytest.raises(repart.RepartError) as e:
-        repart.solve_bicgstab(h, b, x, tol=1e-9)
-    assert e.value.status == repart.RP_DEVICE_TIMEOUT
+    for precision in ("fp64", "mixed"):
+        x = torch.zeros(n, dtype=torch.float64, device=DEV)
+        with pytest.raises(repart.RepartError) as e:
+            repart.solve_bicgstab(h, b, x, tol=1e-9, precision=precision)
+        assert e.value.status == repart.RP_DEVICE_TIMEOUT, precision
     torch.cuda.synchronize()
 
     # the default limit restored: the same handle matches a fresh one bit for bit
@@ -59,9 +61,10 @@ def test_wait_runs_out_and_context_survives():
         assert torch.equal(xs[0], xs[1])
     for hh in (h, fresh):
         repart.update_values_packed(hh, mstg)
-    xs = [torch.zeros(n, dtype=torch.float64, device=DEV) for _ in range(2)]
-    infos = [repart.solve_bicgstab(hh, b, xx, tol=1e-9) for hh, xx in zip((h, fresh), xs)]
-    assert infos[0] == infos[1] and infos[0]["status"] == 0
-    assert torch.equal(xs[0], xs[1])
+    for precision in ("fp64", "mixed"):
+        xs = [torch.zeros(n, dtype=torch.float64, device=DEV) for _ in range(2)]
+        infos = [repart.solve_bicgstab(hh, b, xx, tol=1e-9, precision=precision) for hh, xx in zip((h, fresh), xs)]
+        assert infos[0] == infos[1] and infos[0]["status"] == 0, precision
+        assert torch.equal(xs[0], xs[1]), precision
     h.close()
     fresh.close()
