@@ -239,7 +239,43 @@ __global__ void __launch_bounds__(kThreads) k_bs_p(BsArgs a) {
   if (c->stop) return;
   const BsVecs<T>& V = vecs<T>(a);
   const T beta = (T)((c->rho / c->rho_old) * (c->alpha / c->omega)), omega = (T)c->omega;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  int64_t i0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    // FP32: 16-byte vectors, two of each stream in flight per thread
+    const float4* __restrict__ R = reinterpret_cast<const float4*>(V.r);
+    const float4* __restrict__ Vv = reinterpret_cast<const float4*>(V.v);
+    const float4* __restrict__ D = reinterpret_cast<const float4*>(V.dinv);
+    float4* __restrict__ P = reinterpret_cast<float4*>(V.p);
+    float4* __restrict__ H = reinterpret_cast<float4*>(V.phat);
+    auto step = [&](float4& p, const float4& r, const float4& v, const float4& d, float4& h) {
+      p.x = fmaf(beta, fmaf(-omega, v.x, p.x), r.x);
+      p.y = fmaf(beta, fmaf(-omega, v.y, p.y), r.y);
+      p.z = fmaf(beta, fmaf(-omega, v.z, p.z), r.z);
+      p.w = fmaf(beta, fmaf(-omega, v.w, p.w), r.w);
+      h = make_float4(d.x * p.x, d.y * p.y, d.z * p.z, d.w * p.w);
+    };
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, nv = a.n / 4;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; k + stride < nv; k += 2 * stride) {
+      float4 p0 = P[k], p1 = P[k + stride], h0, h1;
+      const float4 r0 = R[k], r1 = R[k + stride], v0 = Vv[k], v1 = Vv[k + stride], d0 = D[k], d1 = D[k + stride];
+      step(p0, r0, v0, d0, h0);
+      step(p1, r1, v1, d1, h1);
+      P[k] = p0;
+      P[k + stride] = p1;
+      H[k] = h0;
+      H[k + stride] = h1;
+    }
+    for (; k < nv; k += stride) {
+      float4 p0 = P[k], h0;
+      step(p0, R[k], Vv[k], D[k], h0);
+      P[k] = p0;
+      H[k] = h0;
+    }
+    i0 = nv * 4;
+  }
+  for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const T pi = fma(beta, fma(-omega, V.v[i], V.p[i]), V.r[i]);
     V.p[i] = pi;
     V.phat[i] = V.dinv[i] * pi;
@@ -340,7 +376,43 @@ __global__ void __launch_bounds__(kThreads) k_bs_s(BsArgs a) {
   const BsVecs<T>& V = vecs<T>(a);
   const T alpha = (T)c->alpha;
   T ss = T(0);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  int64_t i0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    const float4* __restrict__ R = reinterpret_cast<const float4*>(V.r);
+    const float4* __restrict__ Vv = reinterpret_cast<const float4*>(V.v);
+    const float4* __restrict__ D = reinterpret_cast<const float4*>(V.dinv);
+    float4* __restrict__ Sv = reinterpret_cast<float4*>(V.s);
+    float4* __restrict__ H = reinterpret_cast<float4*>(V.shat);
+    auto step = [&](const float4& r, const float4& v, const float4& d, float4& s, float4& h) {
+      s = make_float4(fmaf(-alpha, v.x, r.x), fmaf(-alpha, v.y, r.y), fmaf(-alpha, v.z, r.z), fmaf(-alpha, v.w, r.w));
+      h = make_float4(d.x * s.x, d.y * s.y, d.z * s.z, d.w * s.w);
+      ss = fmaf(s.x, s.x, ss);
+      ss = fmaf(s.y, s.y, ss);
+      ss = fmaf(s.z, s.z, ss);
+      ss = fmaf(s.w, s.w, ss);
+    };
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, nv = a.n / 4;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; k + stride < nv; k += 2 * stride) {
+      const float4 r0 = R[k], r1 = R[k + stride], v0 = Vv[k], v1 = Vv[k + stride], d0 = D[k], d1 = D[k + stride];
+      float4 s0, s1, h0, h1;
+      step(r0, v0, d0, s0, h0);
+      step(r1, v1, d1, s1, h1);
+      Sv[k] = s0;
+      Sv[k + stride] = s1;
+      H[k] = h0;
+      H[k + stride] = h1;
+    }
+    for (; k < nv; k += stride) {
+      float4 s0, h0;
+      step(R[k], Vv[k], D[k], s0, h0);
+      Sv[k] = s0;
+      H[k] = h0;
+    }
+    i0 = nv * 4;
+  }
+  for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const T si = fma(-alpha, V.v[i], V.r[i]);
     V.s[i] = si;
     V.shat[i] = V.dinv[i] * si;
@@ -369,7 +441,65 @@ __global__ void __launch_bounds__(kThreads) k_bs_xr(BsArgs a) {
   if constexpr (sizeof(T) == 8) x = a.io->x;
   else x = V.x;
   T rr = T(0), rhr = T(0);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+  int64_t i0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    const float4* __restrict__ PH = reinterpret_cast<const float4*>(V.phat);
+    const float4* __restrict__ SH = reinterpret_cast<const float4*>(V.shat);
+    const float4* __restrict__ Tt = reinterpret_cast<const float4*>(V.t);
+    const float4* __restrict__ Sv = reinterpret_cast<const float4*>(V.s);
+    const float4* __restrict__ RH = reinterpret_cast<const float4*>(V.rhat);
+    float4* __restrict__ X = reinterpret_cast<float4*>(x);
+    float4* __restrict__ R = reinterpret_cast<float4*>(V.r);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, nv = a.n / 4;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (half) {
+      for (; k < nv; k += stride) {
+        const float4 ph = PH[k];
+        float4 xv = X[k];
+        xv = make_float4(fmaf(alpha, ph.x, xv.x), fmaf(alpha, ph.y, xv.y), fmaf(alpha, ph.z, xv.z),
+                         fmaf(alpha, ph.w, xv.w));
+        X[k] = xv;
+        R[k] = Sv[k];
+      }
+    } else {
+      auto step = [&](float4& xv, const float4& ph, const float4& sh, const float4& t, const float4& s,
+                      const float4& rh, float4& r) {
+        xv = make_float4(fmaf(omega, sh.x, fmaf(alpha, ph.x, xv.x)), fmaf(omega, sh.y, fmaf(alpha, ph.y, xv.y)),
+                         fmaf(omega, sh.z, fmaf(alpha, ph.z, xv.z)), fmaf(omega, sh.w, fmaf(alpha, ph.w, xv.w)));
+        r = make_float4(fmaf(-omega, t.x, s.x), fmaf(-omega, t.y, s.y), fmaf(-omega, t.z, s.z),
+                        fmaf(-omega, t.w, s.w));
+        rr = fmaf(r.x, r.x, rr);
+        rr = fmaf(r.y, r.y, rr);
+        rr = fmaf(r.z, r.z, rr);
+        rr = fmaf(r.w, r.w, rr);
+        rhr = fmaf(rh.x, r.x, rhr);
+        rhr = fmaf(rh.y, r.y, rhr);
+        rhr = fmaf(rh.z, r.z, rhr);
+        rhr = fmaf(rh.w, r.w, rhr);
+      };
+      for (; k + stride < nv; k += 2 * stride) {
+        float4 x0 = X[k], x1 = X[k + stride], r0, r1;
+        const float4 ph0 = PH[k], ph1 = PH[k + stride], sh0 = SH[k], sh1 = SH[k + stride];
+        const float4 t0 = Tt[k], t1 = Tt[k + stride], s0 = Sv[k], s1 = Sv[k + stride];
+        const float4 rh0 = RH[k], rh1 = RH[k + stride];
+        step(x0, ph0, sh0, t0, s0, rh0, r0);
+        step(x1, ph1, sh1, t1, s1, rh1, r1);
+        X[k] = x0;
+        X[k + stride] = x1;
+        R[k] = r0;
+        R[k + stride] = r1;
+      }
+      for (; k < nv; k += stride) {
+        float4 x0 = X[k], r0;
+        step(x0, PH[k], SH[k], Tt[k], Sv[k], RH[k], r0);
+        X[k] = x0;
+        R[k] = r0;
+      }
+    }
+    i0 = nv * 4;
+  }
+  for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
     if (half) {
       x[i] = fma(alpha, V.phat[i], x[i]);
       V.r[i] = V.s[i];
