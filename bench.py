@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--only-bicgstab", action="store_true",
+                    help="run only the momentum (BiCGStab) measurement, FP64 and mixed: profiling runs")
     ap.add_argument("--only-batch", action="store_true",
                     help="run only the batched form (default launch shape, no loop baseline): profiling runs")
     ap.add_argument("--batch-systems", type=int, default=256)
@@ -270,7 +272,7 @@ def run_adjoint(dev, reps=3):
 # ---------------------------------------------------------------- momentum (BiCGStab)
 
 
-def run_bicgstab(dev, steps, warmup, draws=2):
+def run_bicgstab(dev, steps, warmup, draws=2, host_loop=False):
     """Non-symmetric momentum system on the headline mesh (256^3, k = 128): per step a
     value update (new coefficient draw) + a BiCGStab solve to 1e-9 from x = 0, in FP64
     (rp_solve_bicgstab) and as FP32-inner / FP64-outer refinement (rp_solve_bicgstab_mixed)."""
@@ -283,7 +285,7 @@ def run_bicgstab(dev, steps, warmup, draws=2):
     b = torch.from_numpy(synth.uniform_vector(mesh, 0)).to(dev)
     x = torch.zeros(mesh.n_cells, dtype=torch.float64, device=dev)
     setup_s = time.time() - t0
-    h = repart.build_repartition(mesh.ranks)
+    h = repart.build_repartition(mesh.ranks, host_loop=int(host_loop))
     n, sliced = mesh.n_cells, repart.sliced_sizes(h)
     entries = sliced[1] if sliced else h.nnz
     stream = torch.cuda.current_stream()
@@ -846,6 +848,14 @@ def main():
         torch.cuda.set_device(0)
         repart.load()
         print(json.dumps(run_alpha_sweep(args, torch.device("cuda", 0))))
+        return
+    if args.only_bicgstab and args.impl == "ours":
+        import torch
+        from paper_2510_08536_gb300 import repart
+        torch.cuda.set_device(0)
+        repart.load()
+        print(json.dumps({"bicgstab": run_bicgstab(torch.device("cuda", 0), steps=args.steps, warmup=args.warmup,
+                                                   host_loop=args.host_loop)}))
         return
     if args.only_batch and args.impl == "ours":
         import torch
