@@ -226,3 +226,20 @@ def test_bicgstab_mixed_layouts_parts_and_edges():
     assert e.value.status == repart.RP_EINVAL
     h.close()
 
+
+
+def test_bicgstab_host_loop_matches_graph():
+    """The host-launched loop (for profilers) runs the graph's kernels in the same
+    order: the same bits in both precisions."""
+    M = Mom((20, 16, 12), (2, 2, 1))
+    out = {}
+    for host_loop in (0, 1):
+        h = repart.build_repartition(M.mesh.ranks, host_loop=host_loop)
+        repart.update_values_packed(h, _t(M.stg))
+        for precision in ("fp64", "mixed"):
+            out[host_loop, precision] = _solve(h, _t(M.b), M.n, precision=precision)
+        h.close()
+    for precision in ("fp64", "mixed"):
+        (xg, ig), (xl, il) = out[0, precision], out[1, precision]
+        assert ig == il and ig["status"] == 0, precision
+        assert torch.equal(xg, xl), precision
