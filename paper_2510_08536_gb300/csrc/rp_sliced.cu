@@ -20,7 +20,10 @@
 // host removes duplicate tables and sizes the slices; a third warp pass
 // writes index words and the CSR position of every padded entry. The layout
 // is not built (the iteration keeps the CSR kernels) when a row has more than
-// 32 entries or a slice more than 256 distinct offsets.
+// 32 entries or a slice more than 256 distinct offsets. With several parts
+// every part's local entries get slices of their own (part-local rows and
+// offsets, a record per slice with its first row, part and row count); the
+// non-local entries stay in the part's non-local CSR.
 #include <algorithm>
 #include <cstring>
 #include <memory>
