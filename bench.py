@@ -759,14 +759,15 @@ def run_ours(args):
     del stg_dev
     torch.cuda.empty_cache()
 
+    # the other forms are measured on one GPU only: a replica run times the headline step
     batched = None
-    if not args.no_batch:
+    if not args.no_batch and world == 1:
         batched = run_batch(args, dev, steps=max(1, min(args.steps, 5)), warmup=max(1, min(args.warmup, 2)))
     adj = None
-    if not args.no_bicgstab and args.workload == "mixed_256":
+    if not args.no_bicgstab and args.workload == "mixed_256" and world == 1:
         adj = run_adjoint(dev)
     bicg = None
-    if not args.no_bicgstab and args.workload == "mixed_256":
+    if not args.no_bicgstab and args.workload == "mixed_256" and world == 1:
         bicg = run_bicgstab(dev, steps=max(1, min(args.steps, 3)), warmup=max(1, min(args.warmup, 2)))
 
     cpu = None
