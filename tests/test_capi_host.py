@@ -127,3 +127,18 @@ def test_rejects_bad_solver_choices(lib):
     assert _status(_ranks(), n_parts=2, precond=repart.RP_PRECOND_LINE) == repart.RP_EUNSUPPORTED
     o = repart.default_options()
     assert o.precond == repart.RP_PRECOND_JACOBI and o.layout == repart.RP_LAYOUT_AUTO and o.spare == 0
+
+
+def test_null_handle_solvers(lib):
+    """Every solver entry point rejects a null handle on the host (RP_EINVAL)."""
+    info = repart.SolveInfo()
+    for name in ("rp_solve_bicgstab", "rp_solve_bicgstab_mixed"):
+        st = getattr(lib, name)(None, None, None, 1e-9, 0, 0, ctypes.byref(info), None)
+        assert st == repart.RP_EINVAL, name
+
+
+def test_binding_rejects_unknown_precision(lib):
+    import torch
+    b = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        repart.solve_bicgstab(None, b, b.clone(), precision="fp16")
