@@ -13,12 +13,16 @@ refinement); ``--precision`` picks the headline ``value``. Inputs are
 resident in HBM when the timed region starts and are larger than L2
 (0.94 GB coefficient buffer, 1.4 GB matrix), so no L2 flush is needed.
 
-``--impl reference`` times the CPU oracle instead (a bounded sample per
-step, scaled to a per-time-step figure with the oracle's own iteration
-counts): the paper ships no code, so the oracle is the reference arm.
+``--impl reference`` times the CPU oracle instead (its C / OpenMP
+restatement on every host core, full time steps of the same workload, each
+timed end to end): the paper ships no code, so the oracle is the reference
+arm. ``cpu_baseline`` in the GPU line reports the same oracle on all cores
+and on one, and on the 32^3 and 128^3 configurations.
 
 Multi-GPU (torchrun): the path does not shard; every rank runs an
-independent replica of the workload and ``value`` aggregates them.
+independent replica of the workload (weak scaling): ``value`` is the slowest
+replica's ms per time step, the whole job's time steps per second are
+reported beside it.
 """
 from __future__ import annotations
 
@@ -77,6 +81,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the 32^3 and 128^3 configurations")
     ap.add_argument("--only-bicgstab", action="store_true",
                     help="run only the momentum (BiCGStab) measurement, FP64 and mixed: profiling runs")
     ap.add_argument("--only-batch", action="store_true",
@@ -89,7 +94,7 @@ def parse():
                     help="repartitioning-ratio study at 128^3: GPU parts and CPU ranks merged")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solve kernels from the host (for profilers; not a timing mode)")
-    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -158,65 +163,102 @@ def make_inputs(workload, draws, symmetric=False):
 # ---------------------------------------------------------------- oracle leg
 
 
-def oracle_sample(workload, seeds, iters, counts):
-    """Time the CPU oracle: per step one value update plus a bounded FP64 PCG.
+def oracle_leg(spec):
+    """Time the CPU oracle (runs in a child process, no GPU): its C / OpenMP
+    restatement of the value update and FP64 Jacobi-PCG (pinned against the
+    Python oracle), on the merged map of the Python oracle.
 
-    t_fixed = pcg with 0 iterations (initial z, p and the final true
-    residual); t_iter = (pcg(iters) - t_fixed) / iters. Estimated ms per time
-    step = t_update + t_fixed + I * t_iter, with I the FP64 iteration count of
-    that step's system. Returns per-step estimates in ms."""
+    spec = {"workload", "seeds", "threads", "mode", "iters", "warmup"}. Per
+    seed, one time step: value update vals = buf[src_of], Jacobi diagonal and
+    PCG to relative residual 1e-9 from x = 0, timed end to end ("full"); or
+    the update plus ``iters`` PCG iterations, scaled to the oracle's iteration
+    count for that system ("sample", labelled extrapolated). The coefficient
+    buffers are drawn before the timing; ``warmup`` untimed update-only steps
+    come first."""
     import numpy as np
 
+    from oracle import pcg_omp as C
     from oracle import repart_oracle as O
     from paper_2510_08536_gb300 import synth
-    w = synth.WORKLOADS[workload]
-    mesh = synth.workload_mesh(workload)
+    t0 = time.perf_counter()
+    w = synth.WORKLOADS[spec["workload"]]
+    mesh = synth.workload_mesh(spec["workload"])
     asm = synth.Assembler(mesh)
     (m,) = O.repartition_map(mesh.ranks, 1)
     b = synth.uniform_vector(mesh, 0)
-    out = []
-    for seed, count in zip(seeds, counts):
-        stg = asm.staging(synth.face_coeffs(mesh, w["sigma"], seed))
-        t0 = time.perf_counter()
-        vals = O.update_values(m.src_of, stg)
-        dinv = O.jacobi_inverse(m.row_ptr, m.col_idx, vals, m.diag_pos)
-        A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
-        t1 = time.perf_counter()
-        O.pcg(A, dinv, b, tol=0.0, max_iter=0)
-        t2 = time.perf_counter()
-        O.pcg(A, dinv, b, tol=0.0, max_iter=iters)
-        t3 = time.perf_counter()
-        t_upd, t_fix = t1 - t0, t2 - t1
-        t_it = max(0.0, (t3 - t2) - t_fix) / iters
-        out.append({"ms": 1e3 * (t_upd + t_fix + count * t_it), "update_ms": 1e3 * t_upd,
-                    "fixed_ms": 1e3 * t_fix, "iter_ms": 1e3 * t_it, "iterations": count,
-                    "sample_s": t3 - t0})
-        del stg, vals, A, dinv
-    return out
+    seeds = spec["seeds"]
+    bufs = {s: asm.staging(synth.face_coeffs(mesh, w["sigma"], s)) for s in sorted(set(seeds))}
+    th = int(spec.get("threads", 0))
+    setup_s = time.perf_counter() - t0
+    for k in range(int(spec.get("warmup", 0))):
+        C.update_values(m.src_of, bufs[seeds[k % len(seeds)]], threads=th)
+    steps = []
+    for s in seeds:
+        ta = time.perf_counter()
+        vals = C.update_values(m.src_of, bufs[s], threads=th)
+        dinv = C.jacobi_inverse(m.diag_pos, vals, threads=th)
+        tb = time.perf_counter()
+        if spec["mode"] == "full":
+            r = C.pcg(m.row_ptr, m.col_idx, vals, dinv, b, tol=1e-9, threads=th)
+            tc = time.perf_counter()
+            steps.append({"ms": 1e3 * (tc - ta), "update_ms": 1e3 * (tb - ta), "pcg_ms": 1e3 * (tc - tb),
+                          "iterations": r.iterations, "status": r.status, "true_rel_residual": r.true_rel_residual})
+        else:
+            iters, count = int(spec["iters"]), int(spec["count"])
+            C.pcg(m.row_ptr, m.col_idx, vals, dinv, b, tol=0.0, max_iter=iters, threads=th)
+            tc = time.perf_counter()
+            it_ms = 1e3 * (tc - tb) / iters
+            steps.append({"ms": 1e3 * (tb - ta) + count * it_ms, "update_ms": 1e3 * (tb - ta), "iter_ms": it_ms,
+                          "iterations_timed": iters, "iterations_scaled_to": count})
+        del vals, dinv
+    return {"workload": spec["workload"], "threads": C.threads(th), "mode": spec["mode"],
+            "setup_s": round(setup_s, 1), "steps": steps}
 
 
-def run_oracle_subprocess(workload, seeds, iters, counts, timeout=1800):
+def run_oracle_subprocess(spec, timeout=1800):
+    """oracle_leg in a child process without a GPU, on the cores this process may use."""
     env = dict(os.environ)
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    arg = json.dumps({"workload": workload, "seeds": seeds, "iters": iters, "counts": counts})
-    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", arg], env=env,
+    env["OMP_NUM_THREADS"] = str(len(os.sched_getaffinity(0)))
+    env.pop("OMP_PROC_BIND", None)
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg", json.dumps(spec)], env=env,
                        capture_output=True, text=True, timeout=timeout)
     if p.returncode:
-        raise RuntimeError("oracle sample failed: " + p.stderr[-2000:])
+        raise RuntimeError("oracle leg failed: " + p.stderr[-2000:])
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
-def oracle_counts(workload, seeds):
-    p = os.path.join(ROOT, "tests", "golden", "iteration_counts.json")
-    d = json.load(open(p)).get(workload, {}) if os.path.exists(p) else {}
-    got = [d.get(str(s), {}).get("iterations") for s in seeds]
-    if any(c is None for c in got):
-        known = [v["iterations"] for v in d.values()]
-        fill = int(round(statistics.mean(known))) if known else None
-        got = [fill if c is None else c for c in got]
-    return got
+def cpu_baseline(args, fp64_iterations):
+    """The oracle on the host cores, same workload and tolerance as the GPU line:
+    one full 256^3 time step on every core (measured), the 1-core figure from a
+    bounded sample (extrapolated, labelled), and full time steps of the 32^3 and
+    128^3 configurations on every core and on one."""
+    cores = len(os.sched_getaffinity(0))
+    legs = []
+    full = run_oracle_subprocess({"workload": args.workload, "seeds": [100], "threads": cores, "mode": "full",
+                                  "warmup": 1})
+    st = full["steps"][0]
+    legs.append({"workload": args.workload, "cores": full["threads"], "kind": "oracle", "measured": True,
+                 "ms": round(st["ms"], 1), "update_ms": round(st["update_ms"], 1), "pcg_ms": round(st["pcg_ms"], 1),
+                 "iterations": st["iterations"], "true_rel_residual": st["true_rel_residual"]})
+    one = run_oracle_subprocess({"workload": args.workload, "seeds": [100], "threads": 1, "mode": "sample",
+                                 "iters": 20, "count": st["iterations"]})
+    s1 = one["steps"][0]
+    legs.append({"workload": args.workload, "cores": 1, "kind": "oracle, extrapolated", "measured": False,
+                 "ms": round(s1["ms"], 1), "update_ms": round(s1["update_ms"], 1), "iter_ms": round(s1["iter_ms"], 2),
+                 "sample": f"value update + 20 PCG iterations on one core, per-iteration time scaled to the "
+                           f"{st['iterations']} iterations of the measured all-core step"})
+    for wl in ("plain_fp64_32", "update_128"):
+        for th in (cores, 1):
+            r = run_oracle_subprocess({"workload": wl, "seeds": [100], "threads": th, "mode": "full", "warmup": 1})
+            q = r["steps"][0]
+            legs.append({"workload": wl, "cores": r["threads"], "kind": "oracle", "measured": True,
+                         "ms": round(q["ms"], 2), "iterations": q["iterations"]})
+    return {"value": legs[0]["ms"], "unit": "ms/time-step", "cores": legs[0]["cores"], "kind": "oracle",
+            "sample": f"one full time step of the workload (draw seed 100): value update, Jacobi diagonal and FP64 "
+                      f"Jacobi-PCG to 1e-9 from x = 0, by the oracle's C / OpenMP restatement on all {cores} host "
+                      f"cores, timed end to end (measured, not scaled)",
+            "legs": legs, "gpu_fp64_iterations": fp64_iterations}
 
 
 # ---------------------------------------------------------------- adjoint (gradients)
@@ -457,6 +499,95 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
     return out
 
 
+# ---------------------------------------------------------------- configurations C0, C1
+
+
+def reference_errors(workload, x):
+    """Distance of a solution (device tensor, draw seed 100) to the oracle's, on the rows
+    sampled in tests/golden/reference_solutions.json (written by a script that calls only
+    the oracle): against its FP64 PCG at 1e-9 (the same recurrence) and at 1e-13."""
+    import numpy as np
+    p = os.path.join(ROOT, "tests", "golden", "reference_solutions.json")
+    if not os.path.exists(p):
+        return None
+    g = json.load(open(p)).get(workload)
+    if g is None or g["n"] != x.numel():
+        return None
+    import torch
+    xs = x[torch.tensor(g["idx"], device=x.device)].cpu().numpy()
+    xr, xe = np.asarray(g["x_ref"]), np.asarray(g["x_exact"])
+    return {"vs_oracle_1e-9": float(np.linalg.norm(xs - xr) / np.linalg.norm(xr)),
+            "vs_oracle_1e-13": float(np.linalg.norm(xs - xe) / np.linalg.norm(xe)),
+            "oracle_1e-9_vs_1e-13": g["ref_vs_exact"], "rows_sampled": len(g["idx"])}
+
+
+def run_small_configs(dev, steps=20):
+    """C0: 32^3 / k = 8, uniform coefficients, FP64 PCG to 1e-9 (latency-bound, L2
+    resident): us per time step. C1: 128^3 / k = 64, 20 time steps each with a new
+    lognormal(0, 0.5) draw, update + FP64 PCG to 1e-9: map build, update, solve, SpMV
+    GB/s; the mean over steps excludes the first (the paper's protocol). Errors
+    against the oracle's solutions for draw seed 100."""
+    import torch
+
+    from paper_2510_08536_gb300 import repart, synth
+    stream = torch.cuda.current_stream()
+    hbm_peak, _ = load_peaks()
+    out = {}
+    for name, wl in (("C0", "plain_fp64_32"), ("C1", "update_128")):
+        w = synth.WORKLOADS[wl]
+        mesh = synth.workload_mesh(wl)
+        asm = synth.Assembler(mesh)
+        k = steps if w["sigma"] is not None else 1
+        stg = [torch.from_numpy(asm.staging(synth.face_coeffs(mesh, w["sigma"], 100 + t))).to(dev) for t in range(k)]
+        b = torch.from_numpy(synth.uniform_vector(mesh, 0)).to(dev)
+        x = torch.zeros(mesh.n_cells, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = repart.build_repartition(mesh.ranks)
+        build_ms = 1e3 * (time.perf_counter() - t0)
+        n, nnz, sl = h.n, h.nnz, repart.sliced_sizes(h)
+        for t in range(3):  # warm-up: graphs instantiated, clocks up
+            repart.update_values_packed(h, stg[t % k])
+            repart.solve(h, b, x, tol=1e-9)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps)]
+        infos = []
+        for t in range(steps):
+            ev[3 * t].record(stream)
+            repart.update_values_packed(h, stg[t % k])
+            ev[3 * t + 1].record(stream)
+            infos.append(repart.solve(h, b, x, tol=1e-9))
+            ev[3 * t + 2].record(stream)
+            if t == 0:
+                err = reference_errors(wl, x)
+        torch.cuda.synchronize()
+        upd = [ev[3 * t].elapsed_time(ev[3 * t + 1]) for t in range(1, steps)]
+        sol = [ev[3 * t + 1].elapsed_time(ev[3 * t + 2]) for t in range(1, steps)]
+        spmv_ms = repart.profile_iteration(h, b, "fp64", iters=20)["spmv"]
+        if sl:
+            spmv_bytes = 8 * sl[1] + 4 * sl[2] + 4 * sl[0] + 4 * sl[3] + 8 * (sl[0] + 1) + 16 * n
+        else:
+            spmv_bytes = 12 * nnz + 4 * (n + 1) + 16 * n
+        r = {"workload": f"{wl}: {WORKLOAD_TEXT[wl]}", "steps": steps, "steps_averaged": steps - 1,
+             "map_build_ms": round(build_ms, 2), "update_ms": round(statistics.mean(upd), 4),
+             "solve_ms": round(statistics.mean(sol), 4),
+             "ms_per_step": round(statistics.mean(u + v for u, v in zip(upd, sol)), 4),
+             "iterations_mean": statistics.mean(i["iterations"] for i in infos[1:]),
+             "statuses": sorted({i["status"] for i in infos}),
+             "max_rel_residual": max(i["rel_residual"] for i in infos),
+             "spmv_fp64_ms": round(spmv_ms, 5), "spmv_fp64_GBps": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9, 1),
+             "spmv_frac_of_hbm": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9 / hbm_peak, 4),
+             "error_vs_oracle_draw100": err}
+        if name == "C0":
+            r["us_per_step"] = round(1e3 * r["ms_per_step"], 1)
+            r["note"] = "L2 resident (1.3 MB of vectors, 2.7 MB of matrix): latency-bound, GB/s not meaningful"
+        out[name] = r
+        h.close()
+        del stg
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- alpha sweep
 
 
@@ -514,18 +645,22 @@ def run_alpha_sweep(args, dev):
 
 
 def replica_ms_per_step(ms_local, steps, device=None):
-    """Whole-job ms per time step of N independent replicas: each rank timed `steps`
-    steps in ms_local; the job took the slowest rank's time (max over ranks) for
-    N * steps steps. Works over any initialised process group (NCCL on the GPUs,
-    gloo in the CPU tests)."""
+    """Timing of N independent replicas (weak scaling: every rank solves a whole
+    time step of the workload per step). Each rank timed `steps` steps in
+    ms_local; the job took the slowest rank's time (max over ranks). Returns
+    (ms per time step of the slowest replica, that rank's ms, time steps per
+    second of the whole job = N * steps / slowest time). Works over any
+    initialised process group (NCCL on the GPUs, gloo in the CPU tests)."""
     import torch
     import torch.distributed as dist
-    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
-        return ms_local / steps, ms_local
-    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    return ms_max / (steps * dist.get_world_size()), ms_max
+    world = 1
+    ms_max = float(ms_local)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        world = dist.get_world_size()
+        t = torch.tensor([ms_max], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return ms_max / steps, ms_max, world * steps / (ms_max * 1e-3)
 
 
 def dist_env():
@@ -601,11 +736,11 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         clocks[prec] = sampler.stop()
-        ms_step, ms = replica_ms_per_step(e0.elapsed_time(e1), args.steps, dev)
+        ms_step, ms, job_rate = replica_ms_per_step(e0.elapsed_time(e1), args.steps, dev)
         bad = [i for i in infos if i["status"] != 0]
         results[prec] = {
             "ms_per_step": ms_step,
-            "ms_per_step_per_replica": ms / args.steps,
+            "job_time_steps_per_s": job_rate,
             "iterations_mean": statistics.mean(i["iterations"] for i in infos),
             "outer_mean": statistics.mean(i["outer_iterations"] for i in infos),
             "max_rel_residual": max(i["rel_residual"] for i in infos),
@@ -613,14 +748,16 @@ def run_ours(args):
             "gpu_launches": sum(launches(prec, i) for i in infos),
         }
 
-    # error of each mixed result against the FP64 result of the same system (the FP64 path
-    # is checked against the oracle in the tests; the oracle's own 256^3 solve takes minutes)
+    # error of each result (draw seed 100) against the oracle's solutions of the same
+    # system (sampled rows, tests/golden/reference_solutions.json) and, whole vector,
+    # against the FP64 result of this path
     repart.update_values_packed(h, stg_dev[0])
     sols = {}
     for prec in precs:
         xx = torch.zeros(n, dtype=torch.float64, device=dev)
         repart.solve(h, b, xx, tol=1e-9, precision=prec)
         sols[prec] = xx
+        results[prec]["error_vs_oracle_draw100"] = reference_errors(args.workload, xx)
     if "fp64" in sols:
         ref_norm = float(torch.linalg.norm(sols["fp64"]))
         for prec in precs:
@@ -731,35 +868,81 @@ def run_ours(args):
             update_paths[name] = round(ev[0].elapsed_time(ev[1]) / reps, 3)
         update_paths["host_bytes_per_update"] = 8 * n_slots
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: every step uploads its coefficient
+    # buffer and b from pinned host memory and reads x back. Pipelined (the headline
+    # e2e): step t+1's buffer goes up on the handle's copy stream (RP_MEM_HOST_ASYNC)
+    # while step t solves, and rp_get_solve_info reads step t's outcome after that
+    # upload is queued. Serial: each step's upload waits for the previous solve.
     e2e = None
     if not args.no_e2e:
         b_pin = torch.from_numpy(b_np).pin_memory()
         x_pin = torch.zeros(n, dtype=torch.float64).pin_memory()
-        for t in range(max(1, args.warmup)):
-            step(t, head, stg_pin, b_pin, x_pin)
+
+        def alone(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for _ in range(reps):
+                fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / reps
+
+        stg_dev0, x_dev = stg_dev[0], torch.empty(n, dtype=torch.float64, device=dev)
+        phases = {"h2d_buffer_ms": alone(lambda: stg_dev0.copy_(stg_pin[0], non_blocking=True)),
+                  "h2d_b_ms": alone(lambda: x_dev.copy_(b_pin, non_blocking=True)),
+                  "d2h_x_ms": alone(lambda: x_pin.copy_(x_dev, non_blocking=True)),
+                  "permute_ms": upd_ms, "solve_ms": results[head]["ms_per_step"] - upd_ms}
+        phases = {k: round(v, 3) for k, v in phases.items()}
+        phases["h2d_buffer_GBps"] = round(8 * n_slots / (phases["h2d_buffer_ms"] * 1e-3) / 1e9, 1)
+        del x_dev
+
+        def pipelined(t0, steps, evs=None):
+            repart.update_values_packed(h, stg_pin[t0 % draws], asynchronous=True)
+            for t in range(steps):
+                repart.solve(h, b_pin, x_pin, tol=1e-9, precision=head, wait=False)
+                if t + 1 < steps:
+                    repart.update_values_packed(h, stg_pin[(t0 + t + 1) % draws], asynchronous=True)
+                info = repart.solve_info(h)
+                assert info["status"] == 0, info
+                if evs is not None:
+                    evs[t + 1].record(stream)
+
+        pipelined(0, max(1, args.warmup))
         barrier()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         evs[0].record(stream)
-        for t in range(args.steps):
-            info = step(args.warmup + t, head, stg_pin, b_pin, x_pin)
-            assert info["status"] == 0, info
-            evs[t + 1].record(stream)
+        pipelined(args.warmup, args.steps, evs)
         barrier()
-        ems_step, _ = replica_ms_per_step(evs[0].elapsed_time(evs[-1]), args.steps, dev)
+        ems_step, _, _ = replica_ms_per_step(evs[0].elapsed_time(evs[-1]), args.steps, dev)
         per_step = [evs[t].elapsed_time(evs[t + 1]) for t in range(args.steps)]
+        # the same steps without the overlap (each call waits for the previous one)
+        s_steps = max(1, min(args.steps, 5))
+        step(0, head, stg_pin, b_pin, x_pin)
+        barrier()
+        ev[0].record(stream)
+        for t in range(s_steps):
+            assert step(args.warmup + t, head, stg_pin, b_pin, x_pin)["status"] == 0
+        ev[1].record(stream)
+        barrier()
         e2e = {"value": round(ems_step, 3), "unit": "ms/time-step",
                "h2d_bytes_per_step": 8 * n_slots + 8 * n, "d2h_bytes_per_step": 8 * n,
-               "path": "rp_update_values_packed + rp_solve with pinned host buffers",
-               "step_ms_median": round(statistics.median(per_step), 3), "step_ms_max": round(max(per_step), 3)}
+               "path": "per step: rp_update_values_packed(RP_MEM_HOST_ASYNC) of the next step's pinned buffer "
+                       "queued behind rp_solve (pinned b, x) + rp_get_solve_info",
+               "step_ms_median": round(statistics.median(per_step), 3), "step_ms_max": round(max(per_step), 3),
+               "serial_ms_per_step": round(ev[0].elapsed_time(ev[1]) / s_steps, 3),
+               "serial_path": "rp_update_values_packed(RP_MEM_HOST) + rp_solve with info, one after the other",
+               "phases_alone": phases}
         del stg_pin
 
-    # parity spot check of the last solve against the oracle SpMV is in the tests; here: residual report
     h.close()
     del stg_dev
     torch.cuda.empty_cache()
 
     # the other forms are measured on one GPU only: a replica run times the headline step
+    small = None
+    if world == 1 and not args.no_small:
+        small = run_small_configs(dev)
     batched = None
     if not args.no_batch and world == 1:
         batched = run_batch(args, dev, steps=max(1, min(args.steps, 5)), warmup=max(1, min(args.warmup, 2)))
@@ -771,18 +954,9 @@ def run_ours(args):
         bicg = run_bicgstab(dev, steps=max(1, min(args.steps, 3)), warmup=max(1, min(args.warmup, 2)))
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and "fp64" in results:
-        seeds = [100 + ((args.warmup + args.steps - 1) % draws)]
-        cnt = [int(round(results["fp64"]["iterations_mean"]))]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            smp = run_oracle_subprocess(args.workload, seeds, 8, cnt)
-            s0 = smp[0]
-            cpu = {"value": round(s0["ms"], 1), "unit": "ms/time-step", "cores": 1, "kind": "oracle",
-                   "precision": "fp64",
-                   "sample": f"one value update + FP64 Jacobi-PCG with 0 and 8 iterations on the full workload "
-                             f"(single thread, {s0['sample_s']:.1f} s), per-iteration cost scaled to "
-                             f"{cnt[0]} iterations (the GPU FP64 mean on the same systems)",
-                   "update_ms": round(s0["update_ms"], 1), "iter_ms": round(s0["iter_ms"], 1)}
+            cpu = cpu_baseline(args, results.get("fp64", {}).get("iterations_mean"))
         except Exception as exc:  # report, do not hide
             cpu = {"value": None, "error": str(exc)[-300:]}
 
@@ -809,45 +983,48 @@ def run_ours(args):
         "roofline_fp64_spmv": fp64_alu,
         "map_build_ms": round(build_ms, 1), "input_setup_s": round(setup_s, 1), "update_paths": update_paths,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": results[head]["gpu_launches"], "batched": batched,
-        "bicgstab": bicg, "line_precond": line, "adjoint": adj,
+        "bicgstab": bicg, "line_precond": line, "adjoint": adj, "configs_small": small,
         "clocks": clocks[head], "clocks_other": {o: clocks[o] for o in other},
     }
     return line
 
 
 def run_reference(args):
+    """The reference arm: the oracle (its C / OpenMP restatement) on every host core.
+    Each timed step is one full time step of the workload -- value update, Jacobi
+    diagonal, FP64 Jacobi-PCG to 1e-9 from x = 0 -- timed end to end, nothing
+    scaled; the coefficient draws cycle like the GPU arm's. Warm-up steps are
+    value updates only (untimed)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return None
     draws = max(1, min(args.draws, args.steps + args.warmup))
-    seeds_all = [100 + (t % draws) for t in range(args.warmup + args.steps)]
-    counts = oracle_counts(args.workload, seeds_all)
-    if any(c is None for c in counts):
-        return {"impl": "reference", "unavailable": "no oracle iteration counts for this workload "
-                                                     "(tests/golden/make_iteration_counts.py)"}
+    seeds = [100 + ((args.warmup + t) % draws) for t in range(args.steps)]
     t0 = time.time()
-    smp = run_oracle_subprocess(args.workload, seeds_all, 4, counts, timeout=3600)
-    timed = smp[args.warmup:]
-    ms = statistics.mean(s["ms"] for s in timed)
+    leg = run_oracle_subprocess({"workload": args.workload, "seeds": seeds, "threads": 0, "mode": "full",
+                                 "warmup": args.warmup}, timeout=3600)
+    ms = statistics.mean(st["ms"] for st in leg["steps"])
     return {
         "impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms/time-step", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "headline": "fp64 oracle"},
-        "cpu_baseline": {"value": round(ms, 1), "unit": "ms/time-step", "cores": 1, "kind": "oracle",
-                         "sample": "per step: one value update + FP64 Jacobi-PCG with 0 and 4 iterations on the "
-                                   "full workload (single thread), per-iteration cost scaled to the oracle's own "
-                                   "iteration count for that draw (tests/golden/iteration_counts.json)"},
+        "cpu_baseline": {"value": round(ms, 1), "unit": "ms/time-step", "cores": leg["threads"], "kind": "oracle",
+                         "sample": f"{args.steps} full time steps (value update, Jacobi diagonal, FP64 Jacobi-PCG "
+                                   f"to 1e-9 from x = 0) of the workload by the oracle's C / OpenMP restatement on "
+                                   f"{leg['threads']} host cores, each timed end to end; {args.warmup} untimed "
+                                   f"update-only warm-up steps"},
         "e2e": {"value": round(ms, 1), "unit": "ms/time-step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "wall_s": round(time.time() - t0, 1),
+        "iterations_mean": statistics.mean(st["iterations"] for st in leg["steps"]),
+        "max_true_rel_residual": max(st["true_rel_residual"] for st in leg["steps"]),
+        "setup_s": leg["setup_s"], "wall_s": round(time.time() - t0, 1),
     }
 
 
 def main():
     args = parse()
-    if args.oracle_sample:
-        a = json.loads(args.oracle_sample)
-        print(json.dumps(oracle_sample(a["workload"], a["seeds"], a["iters"], a["counts"])))
+    if args.oracle_leg:
+        print(json.dumps(oracle_leg(json.loads(args.oracle_leg))))
         return
     if args.alpha_sweep and args.impl == "ours":
         import torch

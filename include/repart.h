@@ -56,10 +56,23 @@ typedef enum rp_status {
  * the GPU reads in place over the CPU-GPU link (pinned memory, or any host
  * memory on systems with pageable-memory access such as Grace), with no copy
  * into the staging buffer -- the analogue of sending the coefficients
- * straight into the device buffer (Sec. 3, update procedure). */
-enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1, RP_MEM_HOST_DIRECT = 2 };
+ * straight into the device buffer (Sec. 3, update procedure).
+ * RP_MEM_HOST_ASYNC (rp_update_values_packed only): host memory copied into
+ * one of two device staging buffers on the handle's own copy stream. The
+ * copy starts at the call -- it does not wait for work queued earlier on the
+ * caller's stream, so it overlaps a solve still running there -- and the
+ * permutation, queued on the caller's stream, waits for it; the next such
+ * upload goes to the other buffer, once the permutation that last read it
+ * is done. The caller keeps the host buffer unchanged until its stream has
+ * passed the update (pinned memory makes the copy asynchronous). The
+ * single-GPU analogue of sending the next time step's coefficients while the
+ * GPU still solves (Sec. 3, update procedure; the GPU-aware communication of
+ * Sec. 4). Allocates the two buffers, a stream and four events on first use. */
+enum { RP_MEM_DEVICE = 0, RP_MEM_HOST = 1, RP_MEM_HOST_DIRECT = 2, RP_MEM_HOST_ASYNC = 3 };
 /* Solve precision. RP_MIXED: FP64 iterative refinement around an FP32 PCG
- * that is restarted (p = z) at every refinement and solved to inner_tol.
+ * that is restarted (p = z) at every refinement and solved to inner_tol
+ * relative to its right-hand side, or to half the outer target tol ||b||
+ * when that is reached first (the last refinement stops near the target).
  * RP_MIXED_RU: the same FP32 values, iterations and FP64 residual / update /
  * convergence test, but the FP32 PCG is not restarted: when its recursive
  * residual has fallen by ru_delta (or below half the outer target) its
@@ -185,6 +198,7 @@ rp_status rp_get_sizes(const rp_handle* h, int64_t* n_rows, int64_t* nnz, int64_
  * pass writes vals[p] = buffer[src_of[p]] (and the FP32 copy, round to
  * nearest even) and the Jacobi diagonal 1/a_ii. Asynchronous. */
 rp_status rp_update_values_packed(rp_handle* h, const double* buffer, int32_t where, void* stream);
+/* (where = RP_MEM_HOST_ASYNC: see the RP_MEM_ enum above.) */
 
 /* Same, from per-rank arrays (k pointers each; lower may be NULL in
  * symmetric mode). The arrays are copied into the staging buffer at their
@@ -215,7 +229,10 @@ rp_status rp_spmv(rp_handle* h, const double* x, double* y, double* xy, void* st
  * Limit: n <= 16,777,216 rows (n above it returns RP_ERANGE, no device
  * work). The first call on a device looks up the array's device address
  * with that device current; make that first call before any stream
- * capture. All calls on a device share the array: calls whose work overlaps
+ * capture. The address stays cached for the life of the process: a reset of
+ * the device (cudaDeviceReset, or of its primary context) invalidates it, so
+ * after one this entry point must not be called again on that device in the
+ * same process. All calls on a device share the array: calls whose work overlaps
  * on the GPU (different streams, no ordering) race and give wrong x.y. y is
  * the same per row as rp_spmv's; x.y agrees to rounding. Asynchronous. */
 rp_status rp_spmv_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
@@ -288,13 +305,23 @@ typedef struct rp_solve_info {
  * system's solution.
  * precision RP_FP64: Jacobi-PCG in FP64. RP_MIXED: iterative refinement with
  * the residual, the update x += d and the convergence test in FP64 and the
- * inner Jacobi-PCG on the FP32 values to inner_tol (needs want_fp32).
+ * inner Jacobi-PCG on the FP32 values to inner_tol, or to half the outer
+ * target when that comes first (needs want_fp32). RP_MIXED_RU: see above.
  * x_is_guess: start from x (else x = 0). where: b and x are host or device.
  * The whole iteration runs on the device (CUDA graph with conditional
  * nodes), with no host synchronisation. If info is not NULL the call waits
  * for the stream and fills it; the return value is then info->status. */
 rp_status rp_solve(rp_handle* h, const double* b, double* x, double tol, int32_t precision,
                    int32_t x_is_guess, int32_t where, rp_solve_info* info, void* stream);
+
+/* Outcome of the latest rp_solve on this handle that was launched with
+ * info = NULL: waits for `stream` and fills info (the return value is then
+ * info->status). Lets a caller queue the next time step's value update
+ * (e.g. RP_MEM_HOST_ASYNC) behind a solve before it waits for the solve.
+ * Value updates in between leave the outcome intact; another solve, adjoint
+ * solve or rp_profile_iteration on the handle replaces it. RP_EINVAL if no
+ * solve has run on the handle. */
+rp_status rp_get_solve_info(rp_handle* h, rp_solve_info* info, void* stream);
 
 /* Solve a non-symmetric system A x = b (the momentum equation, which the paper
  * solves with BiCGStab; Sec. 4) to ||b - A x||_2 <= tol ||b||_2 (true
@@ -327,6 +354,10 @@ rp_status rp_solve_bicgstab_mixed(rp_handle* h, const double* b, double* x, doub
                                   int32_t where, rp_solve_info* info, void* stream);
 
 /* ---- Batched form: many independent systems in one persistent launch ----
+ * The paper has no counterpart: it merges the LDU matrices of one problem.
+ * This form applies the same repartition, update and Jacobi-PCG (Sec. 3-4)
+ * to many uneven independent problems at once; it is this library's
+ * extension of the method, defined by those same steps per system.
  * Each system is one LDU matrix without interfaces (n_iface = 0); system s
  * becomes GPU part s (n_parts = count, alpha = 1, Sec. 3). Rows, buffers and
  * vectors of the systems follow each other in system order.
@@ -369,7 +400,13 @@ rp_status rp_batch_autotune(rp_handle* h, const double* buffer, const double* b,
 rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t precision, int32_t iters,
                                float* ms_out, void* stream);
 
-/* Adjoint solve A^T lambda = g (FP64 Jacobi-PCG on the transposed values,
+/* ---- Differentiation: the paper has no counterpart ----
+ * The adjoint of the pressure solve, this library's extension of the method
+ * on the same merged matrix and map, defined by the plain calculus of a
+ * linear solve: for A x = b and a loss L(x), A^T lambda = dL/dx gives
+ * dL/db = lambda and dL/da_ij = -lambda_i x_j for every stored entry.
+ *
+ * Adjoint solve A^T lambda = g (FP64 Jacobi-PCG on the transposed values,
  * built through tpos; needs want_transpose unless symmetric storage).
  * Device pointers; info as in rp_solve. */
 rp_status rp_solve_adjoint(rp_handle* h, const double* g, double* lambda, double tol,

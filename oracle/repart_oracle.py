@@ -591,55 +591,68 @@ def bicgstab_mixed_ir(A64, A32, dinv32, b, tol=1e-9, inner_tol=1e-5, max_outer=5
     return SolveResult(x, total, status, rel, rel, outer)
 
 
-def pcg_fp32(A32, dinv32, rhs32, rel_tol=1e-5, max_iter=10000):
-    """Inner FP32 PCG of the mixed form, x0 = 0.
+def pcg_fp32(A32, dinv32, rhs32, rel_tol=1e-5, max_iter=10000, dtype=np.float32, stop_abs=0.0):
+    """Inner PCG of the mixed form, x0 = 0, in working precision ``dtype``.
 
-    Vectors, values and products are FP32; the dot products are accumulated
-    in FP64 and alpha / beta are rounded to FP32 before use. Stops on the
-    recursive residual ||r|| <= rel_tol ||rhs||. Returns (d, iterations,
-    status)."""
+    The steps of ``pcg`` without restarts: vectors, values and products are
+    ``dtype`` (FP32 in the mixed form); the dot products are accumulated in
+    FP64 and alpha / beta are rounded to ``dtype`` before use. Stops when the
+    recursive residual satisfies ||r|| <= max(rel_tol ||rhs||, stop_abs), on
+    a breakdown (p.Ap <= 0) or after max_iter iterations. With dtype FP64 and
+    rel_tol = stop_abs = 0 it is ``pcg`` itself, iterate for iterate.
+    Returns (d, iterations, status)."""
     prec = _operator(dinv32)
-    f32 = np.float32
+    f = dtype
+
+    def dot(u, w):
+        return float(u.astype(np.float64) @ w.astype(np.float64))
+
     x = np.zeros_like(rhs32)
     r = rhs32.copy()
-    r64 = r.astype(np.float64)
-    thresh = rel_tol * rel_tol * float(r64 @ r64)
-    if thresh == 0.0:
+    rr0 = dot(r, r)
+    if rr0 == 0.0:
         return x, 0, OK
+    thresh = max(rel_tol * rel_tol * rr0, stop_abs * stop_abs)
     z = prec(r)
     p = z.copy()
-    rz = float(r64 @ z.astype(np.float64))
+    rz = dot(r, z)
     it = 0
     while it < max_iter:
         q = A32 @ p
-        pq = float(p.astype(np.float64) @ q.astype(np.float64))
+        pq = dot(p, q)
         if not pq > 0.0:
             return x, it, BREAKDOWN
-        alpha = f32(rz / pq)
+        alpha = f(rz / pq)
         x += alpha * p
         r -= alpha * q
         it += 1
-        r64 = r.astype(np.float64)
-        if float(r64 @ r64) <= thresh:
+        if dot(r, r) <= thresh:
             return x, it, OK
         z = prec(r)
-        rz_new = float(r64 @ z.astype(np.float64))
-        beta = f32(rz_new / rz)
+        rz_new = dot(r, z)
+        beta = f(rz_new / rz)
         p = z + beta * p
         rz = rz_new
     return x, it, NOT_CONVERGED
 
 
-def mixed_ir(A64, A32, dinv32, b, tol=1e-9, inner_tol=1e-5, max_outer=50, max_inner=10000) -> SolveResult:
+def mixed_ir(A64, A32, dinv32, b, tol=1e-9, inner_tol=1e-5, max_outer=50, max_inner=10000,
+             dtype=np.float32, last_pass=0.5) -> SolveResult:
     """FP32-inner / FP64-outer iterative refinement.
 
     x = 0; repeat: r = b - A x with FP64 values; stop when ||r|| <= tol ||b||;
-    solve A32 d = fl32(r) by FP32 PCG to inner_tol relative; x += d in FP64."""
+    solve A32 d = fl(r) by ``pcg_fp32`` (working precision ``dtype``) from
+    d = 0 to ||r_inner|| <= max(inner_tol ||fl(r)||, last_pass tol ||b||);
+    x += d in FP64. The second bound keeps the last pass from solving far past
+    the outer target: once a reduction by inner_tol would overshoot it, the
+    inner solve stops at a fraction ``last_pass`` of the target (0: no cap).
+    ``max_inner`` caps each inner solve."""
     b = np.asarray(b, np.float64)
     bb = float(b @ b)
     x = np.zeros_like(b)
     if bb == 0.0:
         return SolveResult(x, 0, OK, 0.0, 0.0, 0)
+    stop_abs = last_pass * tol * float(np.sqrt(bb))
     inner_total = 0
     status = NOT_CONVERGED
     outer = 0
@@ -651,7 +664,7 @@ def mixed_ir(A64, A32, dinv32, b, tol=1e-9, inner_tol=1e-5, max_outer=50, max_in
             break
         if outer >= max_outer:
             break
-        d, it, st = pcg_fp32(A32, dinv32, r.astype(np.float32), inner_tol, max_inner)
+        d, it, st = pcg_fp32(A32, dinv32, r.astype(dtype), inner_tol, max_inner, dtype, stop_abs)
         inner_total += it
         outer += 1
         if st == BREAKDOWN:

@@ -466,8 +466,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
           for (int64_t i = i0 + tid; i < i1; i += nth) p[i] = fmaf(beta, p[i], dinv32[i] * r[i]);
         }
         rz = t4[0];
-        const double ithresh = RU ? fmax(a.ru_delta * a.ru_delta * t4[3], 0.25 * thresh)
-                                  : a.inner_tol * a.inner_tol * t4[3];
+        const double ithresh = fmax((RU ? a.ru_delta * a.ru_delta : a.inner_tol * a.inner_tol) * t4[3],
+                                    0.25 * thresh);
         int it = 0;
         bool broke = false;
         for (;;) {

@@ -249,6 +249,13 @@ struct rp_handle {
 
   // values
   double* staging = nullptr;  // n_slots
+  // RP_MEM_HOST_ASYNC uploads: two staging buffers that the handle's own copy
+  // stream fills while earlier work runs; copied[i] is recorded when upload i
+  // has landed, consumed[i] when the permutation that read buffer i is done
+  double* stage_async[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t stage_copied[2] = {nullptr, nullptr}, stage_consumed[2] = {nullptr, nullptr};
+  int stage_next = 0;
   double* vals = nullptr;     // nnz (+pad)
   float* vals32 = nullptr;    // nnz (+pad)
   double* nl_vals = nullptr;
@@ -291,6 +298,7 @@ struct rp_handle {
   rp::IterGrid igrid64, igrid32;   // blocks of the PCG iteration kernels
   rp::Graphs graphs;
   cudaStream_t capture_stream = nullptr;
+  bool solve_ran = false;          // an rp_solve has filled the control block
 
   // line preconditioner (precond == RP_PRECOND_LINE)
   int precond = RP_PRECOND_JACOBI;
@@ -327,6 +335,7 @@ rp_status build_sliced(rp_handle* h, cudaStream_t s);  // after the CSR map
 rp_status fill_sliced_transposed(rp_handle* h, cudaStream_t s);  // sl_valsT from valsT
 rp_status fill_sliced(rp_handle* h, cudaStream_t s);   // after every value update
 void free_sliced(rp_handle* h);
+void free_async_stage(rp_handle* h);  // RP_MEM_HOST_ASYNC buffers, stream, events
 void free_bicgstab(rp_handle* h);
 void drop_bicgstab_graph(rp_handle* h);  // after a change of captured arguments
 rp_status line_factors(rp_handle* h, cudaStream_t s);  // after every value update (precond LINE)

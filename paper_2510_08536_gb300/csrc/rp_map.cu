@@ -544,6 +544,7 @@ static void free_handle_memory(rp_handle* h) {
   free_sliced(h);
   free_bicgstab(h);
   free_line(h);
+  free_async_stage(h);
 }
 
 extern "C" void rp_destroy(rp_handle* h) {

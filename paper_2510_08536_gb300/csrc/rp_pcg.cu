@@ -628,7 +628,9 @@ __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
         // target must still make progress: no endless one-step phases)
         c->inner_thresh = fmax(c->ru_delta * c->ru_delta * tot[3], 0.25 * c->thresh);
       } else {
-        c->inner_thresh = c->inner_tol * c->inner_tol * tot[3];
+        // a reduction by inner_tol, but no further than half the outer target:
+        // the last refinement stops near the target instead of far below it
+        c->inner_thresh = fmax(c->inner_tol * c->inner_tol * tot[3], 0.25 * c->thresh);
         c->iter = 0;
       }
       c->rz = tot[0];
@@ -1083,6 +1085,7 @@ rp_status solve_common(rp_handle* h, int mode, const double* vals, const double*
     RP_TRY(launch_solve(h, *slot, bd, xd, tol, !x_is_guess, h->opts.max_iter, info, s));
   }
   if (where == RP_MEM_HOST) RP_TRY_CUDA(cudaMemcpyAsync(x, h->x_host_stage, 8 * h->n, cudaMemcpyDeviceToHost, s));
+  h->solve_ran = true;
   if (info) {
     RP_TRY(read_info(h, info, s));
     return (rp_status)info->status;
@@ -1112,6 +1115,17 @@ extern "C" rp_status rp_solve(rp_handle* h, const double* b, double* x, double t
   if (precision == RP_MIXED_RU)
     return solve_common(h, 2, h->vals, h->dinv, &h->graphs.mixed_ru, b, x, tol, x_is_guess, where, info, s);
   return solve_common(h, 0, h->vals, h->dinv, &h->graphs.fp64, b, x, tol, x_is_guess, where, info, s);
+}
+
+extern "C" rp_status rp_get_solve_info(rp_handle* h, rp_solve_info* info, void* stream) {
+  if (!h || !info) return fail(RP_EINVAL, "null argument");
+  if (h->n == 0) {
+    *info = rp_solve_info{RP_OK, 0, 0, 0, 0, 0.0};
+    return RP_OK;
+  }
+  if (!h->solve_ran) return fail(RP_EINVAL, "no solve has run on this handle");
+  RP_TRY(read_info(h, info, (cudaStream_t)stream));
+  return (rp_status)info->status;
 }
 
 extern "C" rp_status rp_set_solver_options(rp_handle* h, const rp_options* o) {

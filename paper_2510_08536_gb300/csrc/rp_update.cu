@@ -91,6 +91,55 @@ static rp_status permute_all(rp_handle* h, const double* buf, cudaStream_t s) {
   return fill_sliced(h, s);
 }
 
+// Buffers, copy stream and events of RP_MEM_HOST_ASYNC, made on first use.
+static rp_status ensure_async_stage(rp_handle* h) {
+  if (h->copy_stream) return RP_OK;
+  for (int i = 0; i < 2; ++i) {
+    cudaError_t e = cudaMalloc((void**)&h->stage_async[i], sizeof(double) * (size_t)(h->n_slots > 0 ? h->n_slots : 1));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->stage_async[i] = nullptr;
+      free_async_stage(h);
+      return fail(RP_ENOMEM, "cudaMalloc of the asynchronous staging buffers failed");
+    }
+    RP_TRY_CUDA(cudaEventCreateWithFlags(&h->stage_copied[i], cudaEventDisableTiming));
+    RP_TRY_CUDA(cudaEventCreateWithFlags(&h->stage_consumed[i], cudaEventDisableTiming));
+  }
+  RP_TRY_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+  h->stage_next = 0;
+  return RP_OK;
+}
+
+void free_async_stage(rp_handle* h) {
+  for (int i = 0; i < 2; ++i) {
+    if (h->stage_async[i]) cudaFree(h->stage_async[i]);
+    if (h->stage_copied[i]) cudaEventDestroy(h->stage_copied[i]);
+    if (h->stage_consumed[i]) cudaEventDestroy(h->stage_consumed[i]);
+    h->stage_async[i] = nullptr;
+    h->stage_copied[i] = h->stage_consumed[i] = nullptr;
+  }
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  h->copy_stream = nullptr;
+}
+
+// Upload on the copy stream into the staging buffer whose last permutation has
+// finished, then permute from it on `s` once the upload has landed. The copy
+// does not wait for earlier work on `s`: it overlaps a solve still running.
+static rp_status update_host_async(rp_handle* h, const double* buffer, cudaStream_t s) {
+  RP_TRY(ensure_async_stage(h));
+  const int i = h->stage_next;
+  h->stage_next ^= 1;
+  RP_TRY_CUDA(cudaStreamWaitEvent(h->copy_stream, h->stage_consumed[i], 0));
+  if (h->n_slots > 0)
+    RP_TRY_CUDA(cudaMemcpyAsync(h->stage_async[i], buffer, sizeof(double) * h->n_slots, cudaMemcpyHostToDevice,
+                                h->copy_stream));
+  RP_TRY_CUDA(cudaEventRecord(h->stage_copied[i], h->copy_stream));
+  RP_TRY_CUDA(cudaStreamWaitEvent(s, h->stage_copied[i], 0));
+  RP_TRY(permute_all(h, h->stage_async[i], s));
+  RP_TRY_CUDA(cudaEventRecord(h->stage_consumed[i], s));
+  return RP_OK;
+}
+
 }  // namespace rp
 
 using namespace rp;
@@ -113,9 +162,10 @@ static rp_status check_host_direct(const void* p) {
 
 extern "C" rp_status rp_update_values_packed(rp_handle* h, const double* buffer, int32_t where, void* stream) {
   if (!h || (!buffer && h->n_slots > 0)) return fail(RP_EINVAL, "null argument");
-  if (where != RP_MEM_DEVICE && where != RP_MEM_HOST && where != RP_MEM_HOST_DIRECT)
-    return fail(RP_EINVAL, "where must be RP_MEM_DEVICE, RP_MEM_HOST or RP_MEM_HOST_DIRECT");
+  if (where != RP_MEM_DEVICE && where != RP_MEM_HOST && where != RP_MEM_HOST_DIRECT && where != RP_MEM_HOST_ASYNC)
+    return fail(RP_EINVAL, "where must be RP_MEM_DEVICE, RP_MEM_HOST, RP_MEM_HOST_DIRECT or RP_MEM_HOST_ASYNC");
   cudaStream_t s = (cudaStream_t)stream;
+  if (where == RP_MEM_HOST_ASYNC) return update_host_async(h, buffer, s);
   const double* src = buffer;
   if (where == RP_MEM_HOST_DIRECT && h->n_slots > 0) RP_TRY(check_host_direct(buffer));
   if (where == RP_MEM_HOST) {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "librepart.so")
 
 RP_OK, RP_EINVAL, RP_EDUP, RP_ERANGE, RP_EOVERFLOW, RP_ENOMEM, RP_ECUDA = range(7)
 RP_NOT_CONVERGED, RP_BREAKDOWN, RP_DEVICE_TIMEOUT, RP_EUNSUPPORTED = 7, 8, 9, 10
-RP_MEM_DEVICE, RP_MEM_HOST, RP_MEM_HOST_DIRECT = 0, 1, 2
+RP_MEM_DEVICE, RP_MEM_HOST, RP_MEM_HOST_DIRECT, RP_MEM_HOST_ASYNC = 0, 1, 2, 3
 RP_FP64, RP_MIXED, RP_MIXED_RU = 0, 1, 2
 RP_LAYOUT_AUTO, RP_LAYOUT_CSR = 0, 1
 RP_PRECOND_JACOBI, RP_PRECOND_LINE = 0, 1
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rp_batch_autotune": (i32, [vp, vp, vp, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_float), vp]),
         "rp_solve": (i32, [vp, vp, vp, dbl, i32, i32, i32, ctypes.POINTER(SolveInfo), vp]),
+        "rp_get_solve_info": (i32, [vp, ctypes.POINTER(SolveInfo), vp]),
         "rp_solve_bicgstab": (i32, [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveInfo), vp]),
         "rp_solve_bicgstab_mixed": (i32, [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveInfo), vp]),
         "rp_solve_adjoint": (i32, [vp, vp, vp, dbl, ctypes.POINTER(SolveInfo), vp]),
@@ -243,13 +244,20 @@ def get_values(h: Handle) -> dict:
                 dinv=_view(dinv.value, h.n, "<f8"))
 
 
-def update_values_packed(h: Handle, buffer, stream=None, direct: bool = False):
-    """rp_update_values_packed; a host buffer is copied to the device first, or
-    read in place by the permutation kernel when ``direct``."""
+def update_values_packed(h: Handle, buffer, stream=None, direct: bool = False, asynchronous: bool = False):
+    """rp_update_values_packed; a host buffer is copied to the device first (on
+    the handle's own copy stream, overlapping earlier work, when
+    ``asynchronous``), or read in place by the permutation kernel when ``direct``."""
     _f64(buffer, "buffer")
     if buffer.numel() != h.n_slots:
         raise ValueError(f"buffer has {buffer.numel()} values, the handle needs {h.n_slots}")
-    where = RP_MEM_HOST_DIRECT if (direct and not buffer.is_cuda) else _where(buffer)
+    if direct and asynchronous:
+        raise ValueError("direct and asynchronous exclude each other")
+    where = _where(buffer)
+    if not buffer.is_cuda and direct:
+        where = RP_MEM_HOST_DIRECT
+    elif not buffer.is_cuda and asynchronous:
+        where = RP_MEM_HOST_ASYNC
     _check(load().rp_update_values_packed(h.ptr, _ptr(buffer), where, _stream(stream)), "rp_update_values_packed")
 
 
@@ -380,6 +388,15 @@ def solve(h: Handle, b, x, tol: float = 1e-9, precision: str = "fp64", x_is_gues
     return info.as_dict() if wait else None
 
 
+def solve_info(h: Handle, stream=None) -> dict:
+    """rp_get_solve_info: waits for the stream and returns the SolveInfo of the
+    latest solve launched with ``wait=False``."""
+    info = SolveInfo()
+    st = load().rp_get_solve_info(h.ptr, ctypes.byref(info), _stream(stream))
+    _check(st, "rp_get_solve_info", ok=(RP_OK, RP_NOT_CONVERGED, RP_BREAKDOWN))
+    return info.as_dict()
+
+
 def solve_bicgstab(h: Handle, b, x, tol: float = 1e-9, x_is_guess: bool = False, stream=None,
                    wait: bool = True, raise_on_status: bool = False, precision: str = "fp64"):
     """rp_solve_bicgstab (non-symmetric systems; precision "fp64") or
@@ -430,4 +447,4 @@ class Exports:
                     "rp_solve_adjoint", "rp_profile_iteration", "rp_entry_grad", "rp_face_grad", "rp_destroy", "rp_status_str",
                     "rp_last_error", "rp_spmv_noalloc", "rp_batch_build", "rp_batch_update_solve",
                     "rp_batch_set_config", "rp_batch_autotune", "rp_set_solver_options", "rp_iter_spmv",
-                    "rp_get_sliced_view", "rp_solve_bicgstab", "rp_solve_bicgstab_mixed")
+                    "rp_get_sliced_view", "rp_solve_bicgstab", "rp_solve_bicgstab_mixed", "rp_get_solve_info")

@@ -142,3 +142,13 @@ def test_binding_rejects_unknown_precision(lib):
     b = torch.zeros(4, dtype=torch.float64)
     with pytest.raises(ValueError):
         repart.solve_bicgstab(None, b, b.clone(), precision="fp16")
+
+
+def test_get_solve_info_rejects_null(lib):
+    info = repart.SolveInfo()
+    assert lib.rp_get_solve_info(None, ctypes.byref(info), None) == repart.RP_EINVAL
+    assert lib.rp_get_solve_info(None, None, None) == repart.RP_EINVAL
+
+
+def test_update_rejects_unknown_where(lib):
+    assert lib.rp_update_values_packed(None, None, repart.RP_MEM_HOST_ASYNC, None) == repart.RP_EINVAL

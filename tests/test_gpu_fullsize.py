@@ -5,7 +5,10 @@
   FP64 solves against the oracle's solve (same tolerance, same recurrence).
 * 256^3, k = 128 (the headline workload): the whole map bit-exact; FP64
   iteration counts against the oracle's own counts (tests/golden); the true
-  residual of every precision computed with the oracle's matrix.
+  residual of every precision computed with the oracle's matrix; the FP64
+  solution within 1e-7 of the oracle's (its C / OpenMP restatement, run here
+  on every host core) and every precision's sampled distance to the oracle's
+  1e-13 solution (tests/golden/reference_solutions.json) reported.
 * 128^3 adjoint: dL/db and the face gradient against central finite
   differences (h = 1e-6) on 50 cells and 50 faces, relative error
   |g_fd - g| / max(|g|, 1e-3 max|g|) <= 1e-5.
@@ -20,6 +23,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import pcg_omp as C
 from oracle import repart_oracle as O
 from paper_2510_08536_gb300 import build, repart, synth
 
@@ -87,13 +91,33 @@ def test_headline_workload_256():
     del stg
     A = O.csr_matrix(m.row_ptr, m.col_idx, vals)
     bn = np.linalg.norm(b)
+    # the oracle's own solve of the same system (same recurrence and tolerance), on
+    # every host core; and its stored solutions at 1e-9 and 1e-13, sampled
+    ref = C.pcg(m.row_ptr, m.col_idx, vals, C.jacobi_inverse(m.diag_pos, vals), b, tol=1e-9)
+    # (its dot products are summed in another order than the Python oracle's)
+    assert ref.status == O.OK and abs(ref.iterations - counts[str(seed)]["iterations"]) <= 1
+    g = json.load(open(os.path.join(GOLDEN, "reference_solutions.json")))["mixed_256"]
+    assert g["draw_seed"] == seed
+    idx = np.asarray(g["idx"])
+    np.testing.assert_allclose(ref.x[idx], g["x_ref"], rtol=0, atol=1e-12 * np.abs(g["x_ref"]).max())
+    x_exact = np.asarray(g["x_exact"])
     for precision in ("fp64", "mixed", "mixed_ru"):
         x = torch.zeros(mesh.n_cells, dtype=torch.float64, device=DEV)
         info = repart.solve(h, bd, x, tol=1e-9, precision=precision)
         assert info["status"] == 0, (precision, info)
-        assert np.linalg.norm(b - A @ x.cpu().numpy()) / bn <= 1e-9, precision
+        xs = x.cpu().numpy()
+        assert np.linalg.norm(b - A @ xs) / bn <= 1e-9, precision
+        err_ref = np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x)
+        err_exact = np.linalg.norm(xs[idx] - x_exact) / np.linalg.norm(x_exact)
         if precision == "fp64":
             assert abs(info["iterations"] - counts[str(seed)]["iterations"]) <= 2
+            assert err_ref <= 1e-7, err_ref
+        # at residual 1e-9 the distance to the exact solution is bounded by
+        # kappa * 1e-9 (kappa ~ 1e4 here): no result may be further from it than that
+        # bound, nor much further than the oracle's own 1e-9 solution is
+        assert err_exact <= 1e-5 and err_exact <= 10 * g["ref_vs_exact"] + 1e-9, (precision, err_exact)
+        print(f"256^3 {precision}: |x - x_oracle|/|x_oracle| = {err_ref:.3e}, "
+              f"sampled |x - x_exact|/|x_exact| = {err_exact:.3e} (oracle's own: {g['ref_vs_exact']:.3e})")
     h.close()
 
 
@@ -176,6 +200,36 @@ def test_adjoint_workload_128_finite_differences():
         fdv = fd((up, dn), (rho - hstep * dax, rho + hstep * dax))
         g = gf_np[foff[r] + f]
         assert rel(fdv, g, np.abs(gf_np).max()) <= 1e-5, (r, f, fdv, g)
+    # dL/da_f on 25 processor-interface faces, the coupling the repartitioning merges
+    # (Sec. 3, step 3): a_f sits in the diagonal slots of cell i of rank r and cell j
+    # of rank q, in r's interface entry (i, j) and in q's paired entry (j, i); its
+    # gradient is written at r's interface entry
+    checked = 0
+    while checked < 25:
+        r = int(rng.integers(mesh.k))
+        R = mesh.ranks[r]
+        if R.n_iface == 0:
+            continue
+        e = int(rng.integers(R.n_iface))
+        q, i, j = int(R.iface_nbr_rank[e]), int(R.iface_row[e]), int(R.iface_nbr_col[e])
+        Q = mesh.ranks[q]
+        (e2,) = np.nonzero((Q.iface_row == j) & (Q.iface_nbr_rank == r) & (Q.iface_nbr_col == i))[0]
+        slots = [soff[r] + i, soff[q] + j, soff[r] + R.n_cells + 2 * R.n_faces + e,
+                 soff[q] + Q.n_cells + 2 * Q.n_faces + int(e2)]
+        sign = torch.tensor([1.0, 1.0, -1.0, -1.0], dtype=torch.float64, device=DEV)
+        idx = torch.tensor(slots, device=DEV)
+        up, dn = stg.clone(), stg.clone()
+        up[idx] += hstep * sign
+        dn[idx] -= hstep * sign
+        gi, gj = int(off[r] + i), int(off[q] + j)
+        dax = torch.zeros_like(x)
+        dax[gi] = x[gi] - x[gj]
+        dax[gj] = x[gj] - x[gi]
+        fdv = fd((up, dn), (rho - hstep * dax, rho + hstep * dax))
+        g = gf_np[foff[r] + R.n_faces + e]
+        assert g == gf_np[foff[q] + Q.n_faces + int(e2)]  # both sides carry the same value
+        assert rel(fdv, g, np.abs(gf_np).max()) <= 1e-5, (r, e, fdv, g)
+        checked += 1
     h.close()
 
 

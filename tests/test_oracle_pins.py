@@ -307,6 +307,78 @@ def test_mixed_refinement_reaches_fp64_residual():
     assert np.linalg.norm(b - A @ d.astype(np.float64)) / np.linalg.norm(b) > 1e-9
 
 
+def _system32(mesh, sigma):
+    m, vals, A, dinv, _, _ = _system(mesh, sigma)
+    v32 = O.to_fp32(vals)
+    A32 = O.csr_matrix(m.row_ptr, m.col_idx, v32)
+    return m, vals, A, dinv, A32, np.float32(1.0) / v32[m.diag_pos]
+
+
+def test_pcg_fp32_in_fp64_is_the_fp64_recurrence():
+    """The inner PCG of the restarted refinement run in FP64 from d = 0 is pcg
+    itself: the same iterate after k iterations (a wrong beta, sign or step
+    order would differ)."""
+    mesh = synth.box_mesh(12, 10, 8, 2, 1, 1)
+    m, vals, A, dinv, _, _ = _system(mesh, 1.0)
+    b = synth.uniform_vector(mesh, 0)
+    for k in (1, 2, 7, 20):
+        d, it, st = O.pcg_fp32(A, dinv, b.copy(), rel_tol=0.0, max_iter=k, dtype=np.float64)
+        ref = O.pcg(A, dinv, b, tol=0.0, max_iter=k)
+        assert it == k == ref.iterations and st == O.NOT_CONVERGED
+        assert np.linalg.norm(d - ref.x) / np.linalg.norm(ref.x) <= 1e-12, k
+
+
+def test_pcg_fp32_iterates_match_scipy_cg_in_fp32():
+    """In FP32 the inner PCG follows scipy's preconditioned CG run on the same
+    FP32 matrix, right-hand side and Jacobi diagonal, iterate for iterate, up to
+    FP32 rounding (scipy accumulates its dot products in FP32, the oracle in
+    FP64; the recurrences are the same)."""
+    import scipy.sparse.linalg as sla
+    mesh = synth.box_mesh(12, 10, 8, 2, 1, 1)
+    m, vals, A, dinv, A32, d32 = _system32(mesh, 1.0)
+    b32 = synth.uniform_vector(mesh, 0).astype(np.float32)
+    its = []
+    M = sla.LinearOperator(A32.shape, matvec=lambda r: d32 * r, dtype=np.float32)
+    sla.cg(A32, b32, rtol=1e-30, atol=0.0, maxiter=8, M=M, callback=lambda xk: its.append(xk.copy()))
+    assert len(its) == 8 and its[0].dtype == np.float32
+    for k in range(1, 9):
+        d, it, st = O.pcg_fp32(A32, d32, b32.copy(), rel_tol=0.0, max_iter=k)
+        assert d.dtype == np.float32 and it == k
+        assert np.linalg.norm(d - its[k - 1]) / np.linalg.norm(its[k - 1]) <= 1e-5, k
+
+
+def test_restarted_refinement_with_exact_inner_is_one_pcg_run():
+    """With an FP64 inner solve the first refinement already solves the system:
+    one outer pass, whose iterate is pcg's at the inner stopping point -- half
+    the outer target (the last-pass bound), or inner_tol when the bound is off."""
+    mesh = synth.box_mesh(12, 10, 8, 2, 1, 1)
+    m, vals, A, dinv, _, _ = _system(mesh, 1.0)
+    b = synth.uniform_vector(mesh, 0)
+    for last_pass, ref_tol in ((0.5, 0.5e-9), (0.0, 1e-11)):
+        one = O.mixed_ir(A, A, dinv, b, tol=1e-9, inner_tol=1e-11, dtype=np.float64, last_pass=last_pass)
+        ref = O.pcg(A, dinv, b, tol=ref_tol)
+        assert one.status == O.OK and one.outer_iterations == 1
+        assert one.iterations == ref.iterations
+        assert np.linalg.norm(one.x - ref.x) / np.linalg.norm(ref.x) <= 1e-12
+
+
+def test_restarted_refinement_last_pass_stops_near_target():
+    """The FP32 refinement's last pass stops at half the outer target instead of
+    a further inner_tol reduction: the final FP64 residual sits within a decade
+    below tol, with fewer inner iterations than the uncapped schedule."""
+    mesh = synth.box_mesh(16, 16, 16, 2, 2, 2)
+    m, vals, A, dinv, A32, d32 = _system32(mesh, 1.0)
+    b = synth.uniform_vector(mesh, 0)
+    capped = O.mixed_ir(A, A32, d32, b, tol=1e-9, inner_tol=1e-5)
+    free = O.mixed_ir(A, A32, d32, b, tol=1e-9, inner_tol=1e-5, last_pass=0.0)
+    for r in (capped, free):
+        assert r.status == O.OK
+        assert np.linalg.norm(b - A @ r.x) / np.linalg.norm(b) == pytest.approx(r.true_rel_residual, rel=1e-12)
+    assert 1e-10 <= capped.true_rel_residual <= 1e-9
+    assert free.true_rel_residual < capped.true_rel_residual
+    assert capped.iterations < free.iterations and capped.outer_iterations == free.outer_iterations
+
+
 def test_reliable_refinement_with_exact_inner_is_plain_pcg():
     """With FP64 inner arithmetic every replaced residual equals the recursive
     one up to rounding, so continuing the search direction must reproduce the
@@ -333,7 +405,7 @@ def test_reliable_refinement_with_exact_inner_is_plain_pcg():
         res_ = b - A @ x
         if np.linalg.norm(res_) <= 1e-10 * np.linalg.norm(b):
             break
-        d, it, _st = O.pcg_fp32(A, dinv, res_.astype(f), 1e-1, 10000)
+        d, it, _st = O.pcg_fp32(A, dinv, res_.astype(f), 1e-1, 10000, dtype=f)
         x += d
         total += it
     assert total > ref.iterations + 20
@@ -586,3 +658,49 @@ def test_line_reliable_refinement_fp32_reaches_fp64_residual():
     op32 = O.line_operator(*O.line_part(m.row_ptr, m.col_idx, v32), dtype=np.float32)
     res = O.mixed_reliable(A, A32, op32, b, tol=1e-9, delta=0.1)
     assert res.status == O.OK and res.true_rel_residual <= 1e-9
+
+
+# ---------------------------------------------------------------- C / OpenMP restatement
+
+
+@pytest.mark.parametrize("dims,parts,sigma", [((32, 32, 32), (2, 2, 2), None), ((24, 20, 18), (2, 2, 1), 1.0),
+                                              ((7, 5, 3), (1, 1, 1), 0.5)])
+def test_c_oracle_equals_python_oracle(dims, parts, sigma):
+    """The C / OpenMP restatement (timed on all host cores by the benchmark) gives
+    the Python oracle's update bit for bit and its PCG to rounding: the same
+    iteration count and status, x within 1e-12, on one thread and on all."""
+    from oracle import pcg_omp as C
+    mesh = synth.box_mesh(*dims, *parts)
+    m, vals, A, dinv, _, stg = _system(mesh, sigma)
+    b = synth.uniform_vector(mesh, 0)
+    ref = O.pcg(A, dinv, b, tol=1e-9)
+    for th in (1, 0):
+        v = C.update_values(m.src_of, stg, threads=th)
+        np.testing.assert_array_equal(v, vals)
+        d = C.jacobi_inverse(m.diag_pos, v, threads=th)
+        np.testing.assert_array_equal(d, dinv)
+        r = C.pcg(m.row_ptr, m.col_idx, v, d, b, tol=1e-9, threads=th)
+        assert r.status == ref.status == O.OK and r.iterations == ref.iterations
+        assert np.linalg.norm(r.x - ref.x) / np.linalg.norm(ref.x) <= 1e-12
+        assert r.true_rel_residual == pytest.approx(ref.true_rel_residual, rel=1e-6)
+    assert C.threads(1) == 1 and C.threads(0) >= 1
+
+
+def test_c_oracle_edge_cases():
+    """b = 0 gives x = 0 with no iteration; an iteration cap ends NOT_CONVERGED
+    with the cap's iterate, the Python oracle's; an indefinite matrix breaks down."""
+    from oracle import pcg_omp as C
+    mesh = synth.box_mesh(6, 5, 4, 1, 1, 1)
+    m, vals, A, dinv, _, _ = _system(mesh, 0.5)
+    b = synth.uniform_vector(mesh, 0)
+    r = C.pcg(m.row_ptr, m.col_idx, vals, dinv, np.zeros_like(b))
+    assert r.status == O.OK and r.iterations == 0 and not r.x.any()
+    r = C.pcg(m.row_ptr, m.col_idx, vals, dinv, b, tol=1e-12, max_iter=5)
+    ref = O.pcg(A, dinv, b, tol=1e-12, max_iter=5)
+    assert r.status == ref.status == O.NOT_CONVERGED and r.iterations == 5
+    assert np.linalg.norm(r.x - ref.x) / np.linalg.norm(ref.x) <= 1e-13
+    neg = -vals
+    r = C.pcg(m.row_ptr, m.col_idx, neg, 1.0 / neg[m.diag_pos], b)
+    ref = O.pcg(O.csr_matrix(m.row_ptr, m.col_idx, neg), 1.0 / neg[m.diag_pos], b)
+    # D^-1 A is unchanged but p.Ap < 0 at once
+    assert r.status == ref.status == O.BREAKDOWN and r.iterations == ref.iterations == 0

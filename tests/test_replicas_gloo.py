@@ -1,6 +1,8 @@
 """The N > 1 path of bench.py: independent replicas, one per rank, timed with a
 barrier and the slowest rank's time. Two gloo ranks on the CPU check the
-aggregation the NCCL run uses: value = max over ranks / (steps x ranks)."""
+aggregation the NCCL run uses: under weak scaling every replica solves a whole
+time step per step, so value = the slowest replica's ms per time step, and the
+job's throughput (time steps per second over all ranks) is reported apart."""
 import os
 import socket
 
@@ -40,10 +42,11 @@ def test_two_replicas_take_the_slowest_rank():
         p.join(120)
         assert p.exitcode == 0
     got = sorted(q.get(timeout=10) for _ in range(2))
-    for rank, ms_step, ms_max in got:
+    for rank, ms_step, ms_max, rate in got:
         assert ms_max == 1200.0                 # both ranks see the slowest rank's time
-        assert ms_step == 1200.0 / (4 * 2)      # 8 steps in 1200 ms for the whole job
+        assert ms_step == 1200.0 / 4            # the slowest replica's ms per time step
+        assert rate == pytest.approx(8 / 1.2)   # 8 time steps in 1.2 s for the whole job
 
 
 def test_single_process_is_plain_average():
-    assert bench.replica_ms_per_step(900.0, 3) == (300.0, 900.0)
+    assert bench.replica_ms_per_step(900.0, 3) == (300.0, 900.0, pytest.approx(3 / 0.9))
