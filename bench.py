@@ -822,6 +822,10 @@ def run_ours(args):
     upd_bytes = 20 * nnz + 4 * nnz + 20 * n  # idx + gather + FP64 write + FP32 write; diag read + 2 writes
     if sliced:  # sliced values: position + CSR value read, FP64 + FP32 write per padded entry
         upd_bytes += 24 * sliced[1]
+    if sliced and repart.inner_scaled(h):
+        # S A S values: FP64 sliced value read, s (FP64) at the column, FP32 write per
+        # padded entry, index words; s itself: diagonal position + value read, FP64 write per row
+        upd_bytes += (8 + 8 + 4) * sliced[1] + 4 * sliced[2] + 20 * n
     k1_name = "k_it_spmv_sl" if sliced else "k_it_spmv"
     roof = {"bound": "hbm", "kernel": f"{k1_name}<{'double' if head == 'fp64' else 'float'}>",
             "achieved": round(gbs(spmv_bytes(head), kern[head]["spmv"]), 1), "peak": hbm_peak, "unit": "GB/s",
@@ -842,9 +846,13 @@ def run_ours(args):
                     "peak": round(peak_tf, 4), "peak_kind": "derived: SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
                     "frac": round(ach_tf / peak_tf, 4), "fma_per_launch": fma}
     kernels = {}
+    scaled = repart.inner_scaled(h)  # mixed: FP32 iteration on S A S (no diagonal reads in K2, K3)
     for prec in precs:
         w = 8 if prec == "fp64" else 4
-        kb = {"spmv": spmv_bytes(prec), "resid": 4 * w * n, "xp": 6 * w * n}
+        if prec != "fp64" and scaled:
+            kb = {"spmv": spmv_bytes(prec), "resid": 3 * w * n, "xp": 5 * w * n}
+        else:
+            kb = {"spmv": spmv_bytes(prec), "resid": 4 * w * n, "xp": 6 * w * n}
         kernels[prec] = {k: {"ms": round(kern[prec][k], 5), "GB/s": round(gbs(kb[k], kern[prec][k]), 1),
                              "frac": round(gbs(kb[k], kern[prec][k]) / hbm_peak, 4)} for k in kb}
     kernels["update"] = {"ms": round(upd_ms, 4), "GB/s": round(gbs(upd_bytes, upd_ms), 1),
@@ -978,6 +986,7 @@ def run_ours(args):
         "mixed_ru_ms_per_step": round(results["mixed_ru"]["ms_per_step"], 3) if "mixed_ru" in results else None,
         "mixed_ru_delta": 0.1,
         "per_precision": results, "kernels": kernels, "roofline": roof,
+        "mixed_inner_system": "S A S (Jacobi made explicit)" if scaled else "A, Jacobi-preconditioned",
         "roofline_other_spmv": {o: {"achieved": round(gbs(spmv_bytes(o), kern[o]["spmv"]), 1),
                                     "frac": round(gbs(spmv_bytes(o), kern[o]["spmv"]) / hbm_peak, 4)} for o in other},
         "roofline_fp64_spmv": fp64_alu,

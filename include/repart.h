@@ -276,6 +276,16 @@ typedef struct rp_sliced_view {
   const double* vals;
   const float* vals32;
   const int32_t* srow;
+  /* The FP32 inner iteration of the mixed PCG solves (one part, Jacobi) runs
+   * on the symmetrically scaled matrix S A S, S = diag(scale): scale[i] =
+   * 1 / sqrt(a_ii) in FP64 (correctly rounded square root and division),
+   * vals32s[q] = fl32(a_ij (scale_i scale_j)) with the products in FP64 (the
+   * diagonal is exactly 1), 0 for padding -- Jacobi preconditioning made
+   * explicit (CG on S A S from fl32(S r) is PCG with the preconditioner
+   * S^2 = D^-1). Both NULL until the first mixed solve on a handle that takes
+   * it; then refilled by every value update. */
+  const float* vals32s;
+  const double* scale;
 } rp_sliced_view;
 rp_status rp_get_sliced_view(const rp_handle* h, rp_sliced_view* out);
 
@@ -379,12 +389,14 @@ rp_status rp_batch_update_solve(rp_handle* h, const double* buffer, int32_t wher
                                 double tol, int32_t precision, rp_solve_info* info, void* stream);
 
 /* Launch shape of the batched kernel: cluster size (1, 2, 4, 8, 16 CTAs per
- * team) and threads per CTA (multiple of 32, <= 512). RP_EUNSUPPORTED if
- * the shape cannot be scheduled. Default 8 x 512. */
+ * team) and threads per CTA (multiple of 32, <= 512). CTAs of 128 or 384
+ * threads run a build of the kernel with 80 registers a thread, the others one
+ * with 64 (more warps an SM, more register spills). RP_EUNSUPPORTED if the
+ * shape cannot be scheduled. Default 8 x 512. */
 rp_status rp_batch_set_config(rp_handle* h, int32_t cluster, int32_t threads);
 
 /* Autotuner: times rp_batch_update_solve (device buffer, precision) for every
- * cluster size in {2, 4, 8, 16} and CTA size in {128, 256, 512}, keeps the
+ * cluster size in {2, 4, 8, 16} and CTA size in {128, 256, 384, 512}, keeps the
  * fastest shape in the handle and reports it. Overwrites x. Blocks. */
 rp_status rp_batch_autotune(rp_handle* h, const double* buffer, const double* b, double* x, double tol,
                             int32_t precision, int32_t* best_cluster, int32_t* best_threads, float* best_ms,
@@ -425,6 +437,21 @@ rp_status rp_entry_grad(rp_handle* h, const double* lambda, const double* x, dou
  * Device pointers. Asynchronous. */
 rp_status rp_face_grad(rp_handle* h, const double* lambda, const double* x, double* g_face,
                        void* stream);
+
+/* Bounds-checked build only (librepart_check.so, compiled with RP_CHECK;
+ * the paper has no counterpart: it is this library's stand-in for a memory
+ * checker). Its kernels range-check every gather index and every offset they
+ * derive from the map or the sliced layout -- buffer slots src_of, CSR
+ * columns and positions, non-local columns and halo rows, slice descriptors,
+ * table references and offset indices, the source ranges of staged copies,
+ * the map build's placements -- and skip an access that would leave its
+ * array (a load reads zero, a store is dropped) instead of trapping. Waits
+ * for the device, then returns in *count the accesses skipped since the last
+ * reset (in every kernel of the library), with the site (a small integer
+ * naming the kind of index, 1-10) and the index of the first one; reset = 1
+ * clears the counters. The normal build returns RP_EUNSUPPORTED with
+ * *count = 0. */
+rp_status rp_check_violations(uint64_t* count, int32_t* first_site, int64_t* first_index, int32_t reset);
 
 void rp_destroy(rp_handle* h);
 const char* rp_status_str(rp_status s);

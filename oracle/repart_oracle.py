@@ -748,6 +748,152 @@ def mixed_reliable(A64, A_in, dinv_in, b, tol=1e-9, delta=1e-5, max_iter=20000, 
 
 
 # --------------------------------------------------------------------------
+# The mixed forms on the symmetrically scaled system
+# --------------------------------------------------------------------------
+#
+# Jacobi preconditioning made explicit: with S = diag(s), s_i = 1/sqrt(a_ii),
+# A_hat = S A S has a unit diagonal, and CG on A_hat y = S r with no
+# preconditioner is Jacobi-PCG on A d = r with d = S y: the same iterates in
+# exact arithmetic (z = D^-1 r becomes r_hat = S r). The inner FP32 solves of
+# both refinement forms can run on A_hat; the FP64 residual and update stay
+# on A. s is kept in FP64, so the FP32 copy of A_hat has an exactly unit
+# diagonal.
+
+
+def jacobi_scaling(diag):
+    """s_i = 1 / sqrt(a_ii) in FP64 (correctly rounded square root and division)."""
+    d = np.asarray(diag, np.float64)
+    return 1.0 / np.sqrt(d)
+
+
+def scaled_fp32_values(row_ptr, col_idx, vals, s):
+    """FP32 values of S A S: v_ij = fl32(a_ij (s_i s_j)), all products in FP64,
+    s_i s_j first (the same rounded product for (i, j) and (j, i), so a
+    symmetric A gives an exactly symmetric scaled matrix). The diagonal
+    a_ii s_i s_i lies within a few FP64 rounding errors of 1 and is 1 in FP32."""
+    n = row_ptr.shape[0] - 1
+    row = np.repeat(np.arange(n), np.diff(row_ptr))
+    sd = np.asarray(s, np.float64)
+    return (np.asarray(vals, np.float64) * (sd[row] * sd[np.asarray(col_idx, np.int64)])).astype(np.float32)
+
+
+def _scaled_rhs(sd, r, dtype):
+    """fl(S r): the FP64 residual scaled in FP64, rounded to the working precision."""
+    return (sd * r).astype(dtype)
+
+
+def mixed_ir_scaled(A64, A_hat, s, b, tol=1e-9, inner_tol=1e-5, max_outer=50, max_inner=10000,
+                    dtype=np.float32, last_pass=0.5) -> SolveResult:
+    """``mixed_ir`` with its inner solves on the scaled system.
+
+    x = 0; repeat: r = b - A x with FP64 values; stop when ||r|| <= tol ||b||;
+    solve A_hat y = fl(S r) by ``pcg_fp32`` with no preconditioner from y = 0 to
+    ||r_inner|| <= max(inner_tol ||fl(S r)||, last_pass tol ||b|| c), where
+    c = ||fl(S r)|| / ||r|| carries the outer target into the scaled norm;
+    x += S y in FP64."""
+    b = np.asarray(b, np.float64)
+    bb = float(b @ b)
+    x = np.zeros_like(b)
+    if bb == 0.0:
+        return SolveResult(x, 0, OK, 0.0, 0.0, 0)
+    sd = np.asarray(s, np.float64)
+    inner_total = 0
+    status = NOT_CONVERGED
+    outer = 0
+    while True:
+        r = b - A64 @ x
+        rr = float(r @ r)
+        if rr <= tol * tol * bb:
+            status = OK
+            break
+        if outer >= max_outer:
+            break
+        rh = _scaled_rhs(sd, r, dtype)
+        rh64 = rh.astype(np.float64)
+        stop_abs = last_pass * tol * float(np.sqrt(bb)) * float(np.sqrt((rh64 @ rh64) / rr))
+        y, it, st = pcg_fp32(A_hat, lambda v: v, rh, inner_tol, max_inner, dtype, stop_abs)
+        inner_total += it
+        outer += 1
+        if st == BREAKDOWN:
+            status = BREAKDOWN
+            break
+        x += sd * y.astype(np.float64)
+    rel = float(np.sqrt(rr / bb))
+    return SolveResult(x, inner_total, status, rel, rel, outer)
+
+
+def mixed_reliable_scaled(A64, A_hat, s, b, tol=1e-9, delta=0.1, max_iter=20000, max_updates=100,
+                          dtype=np.float32) -> SolveResult:
+    """``mixed_reliable`` with its inner CG on the scaled system.
+
+    The inner CG (no preconditioner: z = r_hat) runs in ``dtype`` on A_hat
+    from the scaled residual r_hat = fl(S r); dot products accumulated in
+    FP64, alpha and beta rounded to ``dtype``. A phase ends when ||r_hat|| has
+    fallen by ``delta`` since the phase began, or below half the outer target
+    carried into the scaled norm, 0.5 tol ||b|| ||r_hat_0|| / ||r_0|| (r_0,
+    r_hat_0: the phase's starting residuals). Then the inner iterate enters the
+    solution as x += S y (FP64, y = 0), r = b - A64 x is computed, the
+    convergence test ||r|| <= tol ||b|| is taken on it, and otherwise fl(S r)
+    replaces the inner residual and the iteration continues with
+    p = r_hat + beta p, beta = (r_hat.r_hat)_new / (r_hat.r_hat)_old."""
+    f = dtype
+    b = np.asarray(b, np.float64)
+    bb = float(b @ b)
+    x = np.zeros_like(b)
+    if bb == 0.0:
+        return SolveResult(x, 0, OK, 0.0, 0.0, 0)
+    thresh = tol * tol * bb
+    sd = np.asarray(s, np.float64)
+
+    def dot(u, w):
+        return float(u.astype(np.float64) @ w.astype(np.float64))
+
+    def phase_end(rh, r):
+        rh2 = dot(rh, rh)
+        return max(delta * delta * rh2, 0.25 * thresh * rh2 / float(r @ r))
+
+    res = b.copy()
+    rh = _scaled_rhs(sd, res, f)
+    inner = phase_end(rh, res)
+    p = rh.copy()
+    rz = dot(rh, rh)
+    y = np.zeros_like(rh)
+    it = updates = 0
+    status = NOT_CONVERGED
+    rr = bb
+    while True:
+        q = A_hat @ p
+        pq = dot(p, q)
+        if not pq > 0.0:
+            status = BREAKDOWN
+            break
+        alpha = f(rz / pq)
+        y += alpha * p
+        rh -= alpha * q
+        it += 1
+        rz_new = dot(rh, rh)
+        if rz_new <= inner or it >= max_iter:
+            x += sd * y.astype(np.float64)
+            y[:] = 0
+            res = b - A64 @ x
+            rr = float(res @ res)
+            updates += 1
+            if rr <= thresh:
+                status = OK
+                break
+            if it >= max_iter or updates >= max_updates:
+                break
+            rh = _scaled_rhs(sd, res, f)
+            inner = phase_end(rh, res)
+            rz_new = dot(rh, rh)
+        beta = f(rz_new / rz)
+        p = rh + beta * p
+        rz = rz_new
+    rel = float(np.sqrt(rr / bb))
+    return SolveResult(x, it, status, rel, rel, updates)
+
+
+# --------------------------------------------------------------------------
 # Adjoint and gradients
 # --------------------------------------------------------------------------
 

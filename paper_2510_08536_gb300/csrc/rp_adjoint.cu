@@ -17,8 +17,10 @@ rp_status solve_common(rp_handle* h, int mode, const double* vals, const double*
 __global__ void __launch_bounds__(kThreads)
     k_transpose_vals(int64_t nnz, const int32_t* __restrict__ tpos, const double* __restrict__ vals,
                      double* __restrict__ valsT) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
-    valsT[p] = __ldg(vals + __ldg(tpos + p));
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = __ldg(tpos + p);
+    valsT[p] = RP_IN(t, 0, nnz, kChkTranspose) ? __ldg(vals + t) : 0.0;
+  }
 }
 
 // per stored entry (i, j): -lambda_i x_j, accumulated into the entry's slot
@@ -26,10 +28,11 @@ template <bool SHARED_SLOTS>
 __global__ void __launch_bounds__(kThreads)
     k_entry_grad(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                  const int32_t* __restrict__ src_of, const double* __restrict__ lam, const double* __restrict__ x,
-                 double* __restrict__ g) {
+                 double* __restrict__ g, int64_t n_slots) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double li = lam[i];
     for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+      if (!RP_IN(col[p], 0, n, kChkGather) || !RP_IN(src_of[p], 0, n_slots, kChkPermute)) continue;
       const double v = -li * __ldg(x + col[p]);
       if (SHARED_SLOTS) atomicAdd(g + src_of[p], v);  // two addends per shared slot: order-free
       else g[src_of[p]] = v;
@@ -57,9 +60,12 @@ __global__ void __launch_bounds__(kThreads)
       a = row_off[r] + iface_row[e];
       b = iface_gcol[e];
     }
+    if (!RP_IN(a, 0, row_off[k], kChkGather) || !RP_IN(b, 0, row_off[k], kChkGather)) continue;
     g[t] = -(lam[a] - lam[b]) * (x[a] - x[b]);
   }
 }
+
+RP_CHECK_TU(adjoint)
 
 }  // namespace rp
 
@@ -100,9 +106,11 @@ extern "C" rp_status rp_entry_grad(rp_handle* h, const double* lambda, const dou
   cudaStream_t s = (cudaStream_t)stream;
   if (h->symmetric) {
     RP_TRY_CUDA(cudaMemsetAsync(g_buffer, 0, sizeof(double) * h->n_slots, s));
-    k_entry_grad<true><<<h->grid, kThreads, 0, s>>>(h->n, h->row_ptr, h->col_idx, h->src_of, lambda, x, g_buffer);
+    k_entry_grad<true><<<h->grid, kThreads, 0, s>>>(h->n, h->row_ptr, h->col_idx, h->src_of, lambda, x, g_buffer,
+                                                     h->n_slots);
   } else {
-    k_entry_grad<false><<<h->grid, kThreads, 0, s>>>(h->n, h->row_ptr, h->col_idx, h->src_of, lambda, x, g_buffer);
+    k_entry_grad<false><<<h->grid, kThreads, 0, s>>>(h->n, h->row_ptr, h->col_idx, h->src_of, lambda, x, g_buffer,
+                                                      h->n_slots);
   }
   RP_TRY_CUDA(cudaGetLastError());
   return RP_OK;

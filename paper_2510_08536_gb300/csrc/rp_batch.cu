@@ -37,6 +37,12 @@ namespace rp {
 namespace {
 
 constexpr int kBatchMaxThreads = 512;
+// Register budget of the persistent kernel: BUDGET 0 is built for two CTAs of
+// 512 threads an SM (64 registers a thread; the kernel spills), BUDGET 1 for
+// two CTAs of 384 (80 registers; a few spills, fewer warps). CTAs of 256 or 512
+// threads run the first, of 128 or 384 the second, so the launch-shape
+// autotuner weighs warps in flight against spills.
+constexpr int batch_budget(int threads) { return (threads == 128 || threads == 384) ? 1 : 0; }
 
 // Block-wide sum of NV values, then cluster-wide through DSMEM; every thread
 // of every CTA returns the same totals.
@@ -73,10 +79,13 @@ __device__ __forceinline__ void team_sum(double (&v)[NV], double (&tot)[NV], cg:
 // vectors are written inside it and are read with coherent loads.
 template <typename T>
 __device__ __forceinline__ T row_dot_coherent(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                              const T* vals, const T* x, int64_t i) {
+                                              const T* vals, const T* x, int64_t i, int64_t n) {
   const int s = __ldg(rp + i), e = __ldg(rp + i + 1);
   T sum = T(0);
-  for (int j = s; j < e; ++j) sum = fma(vals[j], x[__ldg(col + j)], sum);
+  for (int j = s; j < e; ++j) {
+    const int c = __ldg(col + j);
+    if (RP_IN(c, 0, n, kChkGather)) sum = fma(vals[j], x[c], sum);
+  }
   return sum;
 }
 
@@ -85,7 +94,7 @@ __device__ __forceinline__ T row_dot_coherent(const int32_t* __restrict__ rp, co
 // consumes every result.
 template <typename T, typename F>
 __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                          const T* vals, const T* x, int64_t i0, int64_t i1, F&& f) {
+                                          const T* vals, const T* x, int64_t i0, int64_t i1, int64_t n, F&& f) {
   const int64_t nth = blockDim.x;
   int64_t i = i0 + threadIdx.x;
   for (; i + nth < i1; i += 2 * nth) {
@@ -95,13 +104,15 @@ __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const 
     T a0 = T(0), a1 = T(0);
     const int m = max(e0 - s0, e1 - s1);
     for (int t = 0; t < m; ++t) {
-      if (s0 + t < e0) a0 = fma(vals[s0 + t], x[__ldg(col + s0 + t)], a0);
-      if (s1 + t < e1) a1 = fma(vals[s1 + t], x[__ldg(col + s1 + t)], a1);
+      if (s0 + t < e0 && RP_IN(__ldg(col + s0 + t), 0, n, kChkGather))
+        a0 = fma(vals[s0 + t], x[__ldg(col + s0 + t)], a0);
+      if (s1 + t < e1 && RP_IN(__ldg(col + s1 + t), 0, n, kChkGather))
+        a1 = fma(vals[s1 + t], x[__ldg(col + s1 + t)], a1);
     }
     f(i, a0);
     f(k, a1);
   }
-  for (; i < i1; i += nth) f(i, row_dot_coherent<T>(rp, col, vals, x, i));
+  for (; i < i1; i += nth) f(i, row_dot_coherent<T>(rp, col, vals, x, i, n));
 }
 
 // Per-warp staging of one slice's values and index words (slices of up to
@@ -131,7 +142,19 @@ __device__ __forceinline__ void stage_slice(unsigned char* buf, const T* vals, c
   for (uint32_t o = 16u * lane; o < ib; o += 512u) cp_async16(buf + kStageValBytes + o, is + o);
 }
 
-__device__ __forceinline__ bool stageable(uint2 d0, uint2 d1) { return d1.x - d0.x <= 32u * kStageL; }
+// Slices of up to kStageL entries a row are staged; in the bounds-checked
+// build also only when the copy's source ranges lie inside their arrays (an
+// unstaged slice is read from global memory, where slice_sum checks it).
+__device__ __forceinline__ bool stageable(uint2 d0, uint2 d1, const BatchArgs& a) {
+#ifdef RP_CHECK
+  if (!RP_IN(d1.x, d0.x, a.sl_entries + 1, kChkSliceCopy) || !RP_IN(d1.y, d0.y, a.sl_ibuf_len + 1, kChkSliceCopy) ||
+      d1.y - d0.y > (uint32_t)(kStageIdxBytes / 4))
+    return false;
+#else
+  (void)a;
+#endif
+  return d1.x - d0.x <= 32u * kStageL;
+}
 
 // y_i = (A x)_i for rows [i0, i1) (i0 a multiple of 32) on the sliced layout:
 // one warp per slice, lanes on rows, the same fused multiply-adds in the same
@@ -143,7 +166,7 @@ __device__ __forceinline__ bool stageable(uint2 d0, uint2 d1) { return d1.x - d0
 // plain loads); descriptors, tables and index words are read-only.
 template <typename T, typename F>
 __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, int64_t s0, const T* x, int64_t i0,
-                                            int64_t i1, unsigned char* stage, F&& f) {
+                                            int64_t i1, int64_t n, unsigned char* stage, F&& f) {
   if (i0 >= i1) return;  // i0 = n need not be a multiple of 32
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t nw = blockDim.x >> 5, end = (i1 + 31) >> 5;
@@ -161,13 +184,13 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
     n1 = __ldg(desc + ls + nw + 1);
     ninfo = __ldg(tinfo + ls + nw);
   }
-  if (stageable(d0, d1)) stage_slice<T>(wbuf, vals, a.sl_ibuf, d0, d1, lane);
+  if (stageable(d0, d1, a)) stage_slice<T>(wbuf, vals, a.sl_ibuf, d0, d1, lane);
   cp_async_commit();
   int b = 0;
   for (;;) {
     const bool more = ls + nw < end;
     // the next slice's copy goes out before this one is summed
-    if (more && stageable(n0, n1)) stage_slice<T>(wbuf + (b ^ 1) * kStageBuf, vals, a.sl_ibuf, n0, n1, lane);
+    if (more && stageable(n0, n1, a)) stage_slice<T>(wbuf + (b ^ 1) * kStageBuf, vals, a.sl_ibuf, n0, n1, lane);
     cp_async_commit();
     const int64_t lm = ls + 2 * nw;
     uint2 m0 = n1, m1 = n1;
@@ -181,15 +204,21 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
     __syncwarp();
     const int64_t row = (ls << 5) + lane;
     const bool valid = row < i1;
+#ifdef RP_CHECK
+    const SliceCk ck{(int)(-row), (int)(n - row), a.sl_entries, a.sl_ibuf_len, a.sl_tabs_len};
+#else
+    const SliceCk ck{};
+    (void)n;
+#endif
     T sum;
-    if (stageable(d0, d1)) {
+    if (stageable(d0, d1, a)) {
       const unsigned char* cur = wbuf + b * kStageBuf;
       sum = slice_sum<T, true>(d0, d1, info, reinterpret_cast<const T*>(cur) + lane,
                                reinterpret_cast<const uint32_t*>(cur + kStageValBytes) + lane, a.sl_tabs, x + row,
-                               valid, lane);
+                               valid, lane, ck);
     } else {
       sum = slice_sum<T, true>(d0, d1, info, vals + d0.x + lane, a.sl_ibuf + d0.y + lane, a.sl_tabs, x + row, valid,
-                               lane);
+                               lane, ck);
     }
     if (valid) f(row, sum);
     __syncwarp();  // buffer b is read by every lane before it is refilled
@@ -226,12 +255,9 @@ __device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, FS&
 }  // namespace
 
 // MODE: 0 FP64 PCG, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG;
-// SL: the SpMV and residual passes run on the sliced layout
-template <int MODE, bool SL>
-#ifndef RP_BATCH_MIN_BLOCKS
-#define RP_BATCH_MIN_BLOCKS 2  // CTAs of kBatchMaxThreads per SM the register budget must allow
-#endif
-__global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch(BatchArgs a) {
+// SL: the SpMV and residual passes run on the sliced layout; BUDGET: see batch_budget
+template <int MODE, bool SL, int BUDGET>
+__global__ void __launch_bounds__(BUDGET ? 384 : kBatchMaxThreads, 2) k_batch(BatchArgs a) {
   constexpr bool MIXED = MODE != 0;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned T = cl.num_blocks();
@@ -275,14 +301,16 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
     const int tid = threadIdx.x, nth = blockDim.x;
     // A x for rows [i0, i1) of this CTA, f(i, (A x)_i) for each
     auto spmv64 = [&](const double* xv, auto&& f) {
-      if (sl) spmv_slices<double>(a, a.sl_vals, s0, xv, i0, i1, stage, f);
+      if (sl) spmv_slices<double>(a, a.sl_vals, s0, xv, i0, i1, n, stage, f);
       else
-        for (int64_t i = i0 + tid; i < i1; i += nth) f(i, row_dot_coherent<double>(rp, col, vals, xv, i));
+        for (int64_t i = i0 + tid; i < i1; i += nth) f(i, row_dot_coherent<double>(rp, col, vals, xv, i, n));
     };
 
     // value update of this CTA's rows (Sec. 3 update procedure) and the Jacobi diagonal
+    const int64_t blen = a.buf_off[s + 1] - a.buf_off[s];
+    (void)blen;  // bounds of the update's slots (bounds-checked build)
     for (int64_t pp = rp[i0] + tid; pp < rp[i1]; pp += nth) {
-      const double v = buf[src[pp]];
+      const double v = RP_IN(src[pp], 0, blen, kChkPermute) ? buf[src[pp]] : 0.0;
       vals[pp] = v;
       if (MIXED) vals32[pp] = (float)v;
     }
@@ -296,7 +324,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
       const int64_t e0 = __ldg(a.sl_desc + s0 + (i0 >> 5)).x, e1 = __ldg(a.sl_desc + s0 + ((i1 + 31) >> 5)).x;
       for (int64_t e = e0 + tid; e < e1; e += nth) {
         const int32_t pp = __ldg(a.sl_pos + e);
-        const double v = pp >= 0 ? buf[__ldg(a.src_of + pp)] : 0.0;
+        const bool in = pp >= 0 && RP_IN(pp, 0, a.nnz_off[a.n_sys], kChkSliceValues) &&
+                        RP_IN(__ldg(a.src_of + pp), 0, blen, kChkPermute);
+        const double v = in ? buf[__ldg(a.src_of + pp)] : 0.0;
         a.sl_vals[e] = v;
         if (MIXED) a.sl_vals32[e] = (float)v;
       }
@@ -353,8 +383,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
             q[i] = qi;
             v1[0] = fma(p[i], qi, v1[0]);
           };
-          if (sl) spmv_slices<double>(a, a.sl_vals, s0, p, i0, i1, stage, qrow);
-          else spmv_rows<double>(rp, col, vals, p, i0, i1, qrow);
+          if (sl) spmv_slices<double>(a, a.sl_vals, s0, p, i0, i1, n, stage, qrow);
+          else spmv_rows<double>(rp, col, vals, p, i0, i1, n, qrow);
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; break; }
           const double alpha = rz / t1[0];
@@ -477,8 +507,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, RP_BATCH_MIN_BLOCKS) k_batch
             q[i] = qi;
             acc = fmaf(p[i], qi, acc);
           };
-          if (sl) spmv_slices<float>(a, a.sl_vals32, s0, p, i0, i1, stage, qrow);
-          else spmv_rows<float>(rp, col, vals32, p, i0, i1, qrow);
+          if (sl) spmv_slices<float>(a, a.sl_vals32, s0, p, i0, i1, n, stage, qrow);
+          else spmv_rows<float>(rp, col, vals32, p, i0, i1, n, qrow);
           double v1[1] = {(double)acc}, t1[1];
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; broke = true; break; }
@@ -587,15 +617,22 @@ rp_status balloc(T** p, int64_t count) {
   return RP_OK;
 }
 
-void* batch_kernel(int mode, bool sl) {
-  if (sl) return mode == 2 ? (void*)k_batch<2, true> : mode == 1 ? (void*)k_batch<1, true> : (void*)k_batch<0, true>;
-  return mode == 2 ? (void*)k_batch<2, false> : mode == 1 ? (void*)k_batch<1, false> : (void*)k_batch<0, false>;
+template <int BUDGET>
+void* batch_kernel_b(int mode, bool sl) {
+  if (sl)
+    return mode == 2 ? (void*)k_batch<2, true, BUDGET>
+           : mode == 1 ? (void*)k_batch<1, true, BUDGET> : (void*)k_batch<0, true, BUDGET>;
+  return mode == 2 ? (void*)k_batch<2, false, BUDGET>
+         : mode == 1 ? (void*)k_batch<1, false, BUDGET> : (void*)k_batch<0, false, BUDGET>;
+}
+void* batch_kernel(int mode, bool sl, int threads) {
+  return batch_budget(threads) ? batch_kernel_b<1>(mode, sl) : batch_kernel_b<0>(mode, sl);
 }
 
 rp_status launch_config(rp_handle* h, int mode, int cluster, int threads, cudaLaunchConfig_t* cfg,
                         cudaLaunchAttribute* attr, int* n_clusters) {
   const bool sl = h->batch_args.sl_desc != nullptr;
-  void* fn = batch_kernel(mode, sl);
+  void* fn = batch_kernel(mode, sl, threads);
   if (cluster > 8) RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   const int smem = sl ? (threads / 32) * kWarpStage : 0;
   RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -631,7 +668,7 @@ rp_status build_batch_graph(rp_handle* h, int mode, int cluster, int threads, cu
   if (e == cudaSuccess) {
     cudaMemsetAsync(h->batch_queue, 0, sizeof(unsigned int), cs);
     void* args[] = {&ba};
-    cudaLaunchKernelExC(&cfg, batch_kernel(mode, ba.sl_desc != nullptr), args);
+    cudaLaunchKernelExC(&cfg, batch_kernel(mode, ba.sl_desc != nullptr, threads), args);
     e = cudaStreamEndCapture(cs, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
@@ -711,9 +748,14 @@ rp_status batch_prepare(rp_handle* h) {
   a.sl_pos = sl ? h->sl_pos : nullptr;
   a.sl_vals = sl ? h->sl_vals : nullptr;
   a.sl_vals32 = sl ? h->sl_vals32 : nullptr;
+  a.sl_entries = h->sl_entries;
+  a.sl_ibuf_len = h->sl_ibuf_len;
+  a.sl_tabs_len = h->sl_tabs_len;
   h->batch_ready = true;
   return RP_OK;
 }
+
+RP_CHECK_TU(batch)
 
 void free_batch(rp_handle* h) {
   void* ptrs[] = {h->batch_order, h->batch_row_off, h->batch_nnz_off, h->batch_buf_off, h->batch_queue,
@@ -809,7 +851,7 @@ extern "C" rp_status rp_batch_autotune(rp_handle* h, const double* buffer, const
   RP_TRY(batch_prepare(h));
   cudaStream_t s = (cudaStream_t)stream;
   const int clusters[] = {2, 4, 8, 16};
-  const int threads[] = {128, 256, 512};
+  const int threads[] = {128, 256, 384, 512};
   cudaEvent_t e0, e1;
   RP_TRY_CUDA(cudaEventCreate(&e0));
   RP_TRY_CUDA(cudaEventCreate(&e1));

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_bs_res(BsArgs a) {
       ri = bi;
       x[i] = 0.0;
     } else {
-      ri = bi - row_dot_any<double>(a.d.parts, a.row_ptr, a.col, a.d.vals, x, i);
+      ri = bi - row_dot_any<double>(a.d.parts, a.row_ptr, a.col, a.d.vals, x, i, a.n);
     }
     a.d.r[i] = ri;
     a.d.rhat[i] = ri;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_bs_res_mixed(BsArgs a) {
       ri = bi;
       x[i] = 0.0;
     } else {
-      ri = bi - row_dot_any<double>(a.d.parts, a.row_ptr, a.col, a.d.vals, x, i);
+      ri = bi - row_dot_any<double>(a.d.parts, a.row_ptr, a.col, a.d.vals, x, i, a.n);
     }
     const float r32 = (float)ri;
     F.r[i] = r32;
@@ -757,6 +757,8 @@ void free_bicgstab(rp_handle* h) {
   delete b;
   h->bs = nullptr;
 }
+
+RP_CHECK_TU(bicgstab)
 
 }  // namespace rp
 

@@ -32,6 +32,72 @@ rp_status fail(rp_status s, const char* fmt, ...);
     if (s_ != RP_OK) return s_;      \
   } while (0)
 
+// ---------------------------------------------------------------- bounds-checked build
+//
+// Compiled with -DRP_CHECK (librepart_check.so, next to the library), device
+// code range-checks every gather index and every offset it derives from the
+// map or the sliced layout before using it. An index outside its array skips
+// the access (a load reads zero, a store or copy is dropped) and is counted in
+// a device error word, with the site and index of the first one; nothing
+// traps, and rp_check_violations() reads the words. The normal build compiles
+// every check to nothing.
+enum : int {
+  kChkPermute = 1,  // buffer slot src_of[p] of the value update
+  kChkSliceValues,  // CSR position pos[q] of a padded sliced entry
+  kChkSliceDesc,    // a slice descriptor (x_s, y_s) and its row length
+  kChkSliceCopy,    // the source range of a staged copy
+  kChkSliceIndex,   // an offset index against its table's length
+  kChkGather,       // a gathered vector row (row + offset, or a CSR column)
+  kChkNonlocal,     // a non-local column or its halo row
+  kChkTranspose,    // a transpose position tpos[p]
+  kChkMap,          // a position written by the map build
+  kChkRowRange,     // a row pointer range
+};
+
+struct CheckWord {
+  unsigned long long count;  // accesses skipped
+  long long index, limit;    // the first one: its index and the end of its range
+  int site, pad;
+};
+
+#ifdef RP_CHECK
+// one error word per translation unit (no relocatable device code): each
+// unit's reader is registered in rp_check_violations
+static __device__ CheckWord g_check;
+
+static __device__ __noinline__ bool check_fail(long long i, long long hi, int site) {
+  if (atomicAdd(&g_check.count, 1ull) == 0ull) {
+    g_check.index = i;
+    g_check.limit = hi;
+    g_check.site = site;
+  }
+  return false;
+}
+#define RP_IN(i, lo, hi, site)                                                        \
+  (((long long)(i) >= (long long)(lo) && (long long)(i) < (long long)(hi))            \
+       ? true                                                                          \
+       : ::rp::check_fail((long long)(i), (long long)(hi), (site)))
+// host reader of this unit's word (copies it out; reset: clears it)
+#define RP_CHECK_TU(name)                                                              \
+  rp_status check_read_##name(CheckWord* out, int reset) {                             \
+    RP_TRY_CUDA(cudaMemcpyFromSymbol(out, g_check, sizeof(CheckWord)));                \
+    if (reset) {                                                                       \
+      const CheckWord z{};                                                             \
+      RP_TRY_CUDA(cudaMemcpyToSymbol(g_check, &z, sizeof(CheckWord)));                 \
+    }                                                                                  \
+    return RP_OK;                                                                      \
+  }
+#else
+#define RP_IN(i, lo, hi, site) true
+#define RP_CHECK_TU(name)
+#endif
+// a helper's "no index" answer (-1) is only possible in the bounds-checked build
+#ifdef RP_CHECK
+#define RP_IDX_OK(g) ((g) >= 0)
+#else
+#define RP_IDX_OK(g) true
+#endif
+
 // ---------------------------------------------------------------- constants
 
 constexpr int kThreads = 256;        // block size of the streaming kernels
@@ -133,6 +199,7 @@ struct Sliced {
   // it); the non-local entries of those rows follow in the part's CSR. nullptr:
   // one part, slice s holds rows 32 s ..
   const int2* srow = nullptr;
+  int64_t n_entries = 0, ibuf_len = 0, tabs_len = 0;  // array lengths (bounds-checked build)
 };
 constexpr int kSliceDescPad = 8;  // bulk copies of descriptor runs may read past the end
 // Probe bound of the wait for a block's own bulk copies after another wait
@@ -146,6 +213,7 @@ struct IterGrid {
   int k1 = 1, k1s = 1, k2 = 1, k3 = 1;  // K1 on CSR, K1 on the sliced layout, K2, K3
   int k1sm = 1;                         // K1 on the sliced layout of several parts
   int k2l = 1, k3l = 1;                 // K2, K3 with the line preconditioner
+  int k2s = 1, k3s = 1;                 // K2, K3 of the scaled inner system
 };
 
 struct BsState;  // BiCGStab work space and graph (rp_bicgstab.cu)
@@ -202,6 +270,7 @@ struct BatchArgs {
   const int32_t* sl_pos;
   double* sl_vals;
   float* sl_vals32;
+  int64_t sl_entries, sl_ibuf_len, sl_tabs_len;  // array lengths (bounds-checked build)
 };
 
 }  // namespace rp
@@ -283,6 +352,11 @@ struct rp_handle {
   double* sl_vals = nullptr;
   double* sl_valsT = nullptr;  // sliced transposed values (adjoint of general storage, on demand)
   float* sl_vals32 = nullptr;
+  // FP32 values of the symmetrically scaled matrix S A S (s_i = 1/sqrt(a_ii)),
+  // the inner system of the mixed PCG solves (one part, Jacobi); allocated by
+  // the first such solve, refilled by every value update afterwards
+  float* sl_vals32s = nullptr;
+  double* s64 = nullptr;  // n: s_i = 1/sqrt(a_ii)
 
   // solver work space
   double *r = nullptr, *p = nullptr, *q = nullptr;
@@ -334,6 +408,10 @@ rp_status ensure_solver_buffers(rp_handle* h);
 rp_status build_sliced(rp_handle* h, cudaStream_t s);  // after the CSR map
 rp_status fill_sliced_transposed(rp_handle* h, cudaStream_t s);  // sl_valsT from valsT
 rp_status fill_sliced(rp_handle* h, cudaStream_t s);   // after every value update
+// the scaled inner system of the mixed PCG solves: allocated and filled from the
+// current values on first use (then refilled by fill_sliced); false when the
+// handle does not take it (several parts, CSR layout, no FP32 copy)
+rp_status ensure_scaled(rp_handle* h, cudaStream_t s, bool* ok);
 void free_sliced(rp_handle* h);
 void free_async_stage(rp_handle* h);  // RP_MEM_HOST_ASYNC buffers, stream, events
 void free_bicgstab(rp_handle* h);

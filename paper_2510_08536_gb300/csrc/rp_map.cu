@@ -161,6 +161,7 @@ struct MapIn {
   const int32_t* iface_row;
   const int32_t* iface_gcol;
   int64_t n_entries;
+  int64_t n_rows, nnz, nl_nnz;  // bounds of the placement (bounds-checked build)
 };
 
 // global (row, col, slot) of entry t and its rank's part
@@ -203,6 +204,7 @@ __global__ void k_count(MapIn m, int32_t* __restrict__ deg, int32_t* __restrict_
     int64_t row, col, slot;
     int part;
     entry_coords(m, t, row, col, slot, part);
+    if (!RP_IN(row, 0, m.n_rows, kChkMap) || !RP_IN(col, 0, m.n_rows, kChkMap)) continue;
     if (col_in_part(m, part, col)) atomicAdd(deg + row, 1);
     else atomicAdd(nl_deg + row, 1);
   }
@@ -217,12 +219,15 @@ __global__ void k_place(MapIn m, int32_t* __restrict__ cur, int32_t* __restrict_
     int part;
     entry_coords(m, t, row, col, slot, part);
     int64_t sl = slot - m.part_buf_off[part];
+    if (!RP_IN(row, 0, m.n_rows, kChkMap) || !RP_IN(col, 0, m.n_rows, kChkMap)) continue;
     if (col_in_part(m, part, col)) {
       int q = atomicAdd(cur + row, 1);
+      if (!RP_IN(q, 0, m.nnz, kChkMap)) continue;
       col_idx[q] = (int32_t)(col - m.part_row_off[part]);
       src_of[q] = (int32_t)sl;
     } else {
       int q = atomicAdd(nl_cur + row, 1);
+      if (!RP_IN(q, 0, m.nl_nnz, kChkMap)) continue;
       nl_gcol[q] = (int32_t)col;
       nl_src_of[q] = (int32_t)sl;
     }
@@ -274,6 +279,7 @@ __global__ void k_tpos(int64_t n, const int32_t* __restrict__ pos, const int32_t
     int32_t li = (int32_t)(i - r0);
     for (int a = pos[i]; a < pos[i + 1]; ++a) {
       int64_t jg = r0 + col[a];
+      if (!RP_IN(jg, 0, n, kChkMap)) continue;
       int lo = pos[jg], hi = pos[jg + 1];
       while (lo < hi) {
         int mid = (lo + hi) >> 1;
@@ -297,11 +303,11 @@ __global__ void k_part_rowptr(const int32_t* __restrict__ pos, int64_t r0, int64
 }
 
 __global__ void k_mark(int64_t r0, int64_t r1, const int32_t* __restrict__ pos,
-                       const int32_t* __restrict__ gcol, int32_t* __restrict__ mark) {
+                       const int32_t* __restrict__ gcol, int32_t* __restrict__ mark, int64_t n) {
   int64_t s = pos[r0], e = pos[r1];
   for (int64_t q = s + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < e;
        q += (int64_t)gridDim.x * blockDim.x)
-    mark[gcol[q]] = 1;
+    if (RP_IN(gcol[q], 0, n, kChkMap)) mark[gcol[q]] = 1;
 }
 
 __global__ void k_compact_cols(int64_t n, const int32_t* __restrict__ mark, const int32_t* __restrict__ idx,
@@ -490,6 +496,8 @@ rp_status validate(const rp_ldu_desc* ranks, int32_t k, const rp_options& o) {
 }
 
 }  // namespace
+
+RP_CHECK_TU(map)
 
 }  // namespace rp
 
@@ -709,6 +717,8 @@ extern "C" rp_status rp_build_repartition(const rp_ldu_desc* ranks, int32_t k, c
   m.iface_row = H->d_iface_row;
   m.iface_gcol = H->d_iface_gcol;
   m.n_entries = n_entries;
+  m.n_rows = n;
+  m.nnz = m.nl_nnz = 0;
   const int g = grid_for(H, n_entries > n ? n_entries : n);
 
   // 1-2: degrees and their scans
@@ -749,6 +759,8 @@ extern "C" rp_status rp_build_repartition(const rp_ldu_desc* ranks, int32_t k, c
   TALLOC(nl_gcol, H->nl_nnz + 1);
   CU(cudaMemcpyAsync(deg, pos, 4 * (n + 1), cudaMemcpyDeviceToDevice, st));
   CU(cudaMemcpyAsync(nl_deg, nl_pos, 4 * (n + 1), cudaMemcpyDeviceToDevice, st));
+  m.nnz = H->nnz;
+  m.nl_nnz = H->nl_nnz;
   k_place<<<g, kThreads, 0, st>>>(m, deg, nl_deg, H->col_idx, H->src_of, nl_gcol, H->nl_src_of);
   CU(cudaGetLastError());
 
@@ -788,7 +800,7 @@ extern "C" rp_status rp_build_repartition(const rp_ldu_desc* ranks, int32_t k, c
     for (int p = 0; p < o.n_parts; ++p) {
       int64_t r0 = H->part_row_off[p], r1 = H->part_row_off[p + 1];
       CU(cudaMemsetAsync(mark, 0, 4 * (n + 1), st));
-      k_mark<<<gr, kThreads, 0, st>>>(r0, r1, nl_pos, nl_gcol, mark);
+      k_mark<<<gr, kThreads, 0, st>>>(r0, r1, nl_pos, nl_gcol, mark, n);
       rp_status s = scan_exclusive(mark, idx, n, bsum, st);
       if (s != RP_OK) return fail_free(s);
       CU(cudaMemcpyAsync(&counts[p], idx + n, 4, cudaMemcpyDeviceToHost, st));
@@ -895,4 +907,44 @@ extern "C" rp_status rp_get_sizes(const rp_handle* h, int64_t* n_rows, int64_t* 
   if (n_slots) *n_slots = h->n_slots;
   if (n_parts) *n_parts = h->n_parts;
   return RP_OK;
+}
+
+#ifdef RP_CHECK
+namespace rp {
+rp_status check_read_update(CheckWord*, int);
+rp_status check_read_sliced(CheckWord*, int);
+rp_status check_read_pcg(CheckWord*, int);
+rp_status check_read_batch(CheckWord*, int);
+rp_status check_read_bicgstab(CheckWord*, int);
+rp_status check_read_adjoint(CheckWord*, int);
+rp_status check_read_noalloc(CheckWord*, int);
+}  // namespace rp
+#endif
+
+extern "C" rp_status rp_check_violations(uint64_t* count, int32_t* first_site, int64_t* first_index,
+                                         int32_t reset) {
+  if (!count) return fail(RP_EINVAL, "null argument");
+  *count = 0;
+  if (first_site) *first_site = 0;
+  if (first_index) *first_index = -1;
+#ifdef RP_CHECK
+  using Reader = rp_status (*)(CheckWord*, int);
+  const Reader readers[] = {check_read_map,   check_read_update,   check_read_sliced, check_read_pcg,
+                            check_read_batch, check_read_bicgstab, check_read_adjoint, check_read_noalloc};
+  RP_TRY_CUDA(cudaDeviceSynchronize());
+  for (Reader r : readers) {
+    CheckWord w{};
+    RP_TRY(r(&w, reset));
+    if (w.count && *count == 0) {
+      if (first_site) *first_site = w.site;
+      if (first_index) *first_index = w.index;
+    }
+    *count += w.count;
+  }
+  return RP_OK;
+#else
+  (void)reset;
+  return fail(RP_EUNSUPPORTED, "this library was built without RP_CHECK (the bounds-checked build is "
+                               "librepart_check.so)");
+#endif
 }

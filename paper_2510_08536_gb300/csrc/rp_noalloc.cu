@@ -42,7 +42,10 @@ __global__ void __launch_bounds__(kNaThreads)
     if (i < n) {
       const int s = __ldg(row_ptr + i), e = __ldg(row_ptr + i + 1);
       double sum = 0.0;
-      for (int j = s; j < e; ++j) sum = fma(__ldg(vals + j), __ldg(x + __ldg(col + j)), sum);
+      for (int j = s; j < e; ++j) {
+        const int c = __ldg(col + j);
+        if (RP_IN(c, 0, n, kChkGather)) sum = fma(__ldg(vals + j), __ldg(x + c), sum);
+      }
       y[i] = sum;
       acc += x[i] * sum;
     }
@@ -73,6 +76,9 @@ rp_status scratch_for_current_device(unsigned char** out) {
 }
 
 }  // namespace
+
+RP_CHECK_TU(noalloc)
+
 }  // namespace rp
 
 using namespace rp;

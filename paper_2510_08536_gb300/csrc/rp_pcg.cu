@@ -66,6 +66,7 @@ struct ResArgs {
   Parts<double> parts;
   Line<double> line;   // FP64 path, line preconditioner
   Line<float> line32;  // mixed path, line preconditioner
+  const double* s64;   // mixed path, scaled inner system: s = 1/sqrt(a_ii)
 };
 
 // z = M^-1 r for the 32-row block this warp holds (lane j: row 32 s + j) of
@@ -229,7 +230,8 @@ __device__ __forceinline__ void it_spmv_sl(const IterArgs<T>& a) {
         }
         unsigned char* base = sbuf + st * St::kBytes;
         const uint32_t vb = (d1.x - d0.x) * (uint32_t)sizeof(T), ib = (d1.y - d0.y) * 4u;
-        const bool fit = vb <= (uint32_t)St::kVals && ib <= (uint32_t)kStageIdx;
+        const uint32_t db = 16u * (uint32_t)((kChunk + 2) / 2);  // kChunk + 1 descriptors, 16-byte multiple
+        const bool fit = vb <= (uint32_t)St::kVals && ib <= (uint32_t)kStageIdx && chunk_copy_ok(a.sl, d0, d1, ch, db);
         chunk_x[st] = d0.x;
         chunk_y[st] = d0.y;
         staged[st] = fit;
@@ -237,7 +239,6 @@ __device__ __forceinline__ void it_spmv_sl(const IterArgs<T>& a) {
         // empty[st]) before the async-proxy writes of the copy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (fit) {
-          const uint32_t db = 16u * (uint32_t)((kChunk + 2) / 2);  // kChunk + 1 descriptors, 16-byte multiple
           mbar_expect_tx(&full[st], vb + ib + db + kStageInfo);
           bulk_g2s(base, a.sl.vals + d0.x, vb, &full[st]);
           bulk_g2s(base + St::kVals, a.sl.ibuf + d0.y, ib, &full[st]);
@@ -268,6 +269,7 @@ __device__ __forceinline__ void it_spmv_sl(const IterArgs<T>& a) {
         if constexpr (MP)
           if (valid) nl = nonlocal_range<T>(a.parts, sr.part, row);
         const T* x = a.p + row;
+        const SliceCk ck = slice_ck<T, MP>(a.sl, a.parts, sr.part, row, n);
         const unsigned char* base = sbuf + st * St::kBytes;
         T sum;
         if (staged[st]) {
@@ -276,11 +278,12 @@ __device__ __forceinline__ void it_spmv_sl(const IterArgs<T>& a) {
           const uint2 d0 = sd[w], d1 = sd[w + 1];
           sum = slice_sum<T>(d0, d1, si[w], reinterpret_cast<const T*>(base) + (d0.x - chunk_x[st]) + lane,
                              reinterpret_cast<const uint32_t*>(base + St::kVals) + (d0.y - chunk_y[st]) + lane,
-                             a.sl.tabs, x, valid, lane);
+                             a.sl.tabs, x, valid, lane, ck);
         } else {
           const uint2 d0 = __ldg(desc + s), d1 = __ldg(desc + s + 1);
           sum = slice_sum<T>(d0, d1, __ldg(a.sl.tinfo + s), a.sl.vals + d0.x + lane,
-                             reinterpret_cast<const uint32_t*>(a.sl.ibuf + d0.y) + lane, a.sl.tabs, x, valid, lane);
+                             reinterpret_cast<const uint32_t*>(a.sl.ibuf + d0.y) + lane, a.sl.tabs, x, valid, lane,
+                             ck);
         }
         if constexpr (MP) sum = nonlocal_sum<T>(a.parts, sr.part, nl, a.p, sum);
         if (valid) {
@@ -343,8 +346,9 @@ void launch_k1(const IterArgs<T>& a, int grid, cudaStream_t s) {
   else k_it_spmv<T><<<grid, kThreads, 0, s>>>(a);
 }
 
-// K2: r -= alpha q; z = D^-1 r (LINE: z = M^-1 r, stored); (r, z), (r, r); stop test; beta.
-template <typename T, bool LINE>
+// K2: r -= alpha q; z = D^-1 r (LINE: z = M^-1 r, stored; SCALED: the system
+// is scaled to a unit diagonal and z = r); (r, z), (r, r); stop test; beta.
+template <typename T, bool LINE, bool SCALED = false>
 __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
   Ctl* c = a.ctl;
   if (c->stop) {
@@ -391,6 +395,38 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
     }
     k = nv;  // the Jacobi loops below do nothing
   }
+  if constexpr (SCALED) {
+    // unit diagonal: z = r, so (r, z) = (r, r) and no diagonal is read
+    auto sstep = [&](V& rv, V qv) {
+      for_each_comp<W>([&](auto e) {
+        constexpr int E = decltype(e)::value;
+        T ri = fma(-alpha, comp<E>(qv), comp<E>(rv));
+        comp<E>(rv) = ri;
+        rr = fma(ri, ri, rr);
+      });
+    };
+    for (; k + stride < nv; k += 2 * stride) {
+      V q0 = reinterpret_cast<const V*>(a.q)[k], q1 = reinterpret_cast<const V*>(a.q)[k + stride];
+      V r0 = reinterpret_cast<const V*>(a.r)[k], r1 = reinterpret_cast<const V*>(a.r)[k + stride];
+      sstep(r0, q0);
+      sstep(r1, q1);
+      reinterpret_cast<V*>(a.r)[k] = r0;
+      reinterpret_cast<V*>(a.r)[k + stride] = r1;
+    }
+    for (; k < nv; k += stride) {
+      V qv = reinterpret_cast<const V*>(a.q)[k];
+      V rv = reinterpret_cast<const V*>(a.r)[k];
+      sstep(rv, qv);
+      reinterpret_cast<V*>(a.r)[k] = rv;
+    }
+    for (int64_t i = nv * W + tid; i < a.n; i += stride) {
+      T ri = fma(-alpha, a.q[i], a.r[i]);
+      a.r[i] = ri;
+      rr = fma(ri, ri, rr);
+    }
+    rz = rr;
+    k = nv;  // the Jacobi loops below do nothing
+  }
   // two vectors of each stream in flight per thread
   for (; k + stride < nv; k += 2 * stride) {
     V q0 = reinterpret_cast<const V*>(a.q)[k], q1 = reinterpret_cast<const V*>(a.q)[k + stride];
@@ -408,7 +444,7 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
     step(rv, qv, dv);
     reinterpret_cast<V*>(a.r)[k] = rv;
   }
-  for (int64_t i = nv * W + tid; !LINE && i < a.n; i += stride) {
+  for (int64_t i = nv * W + tid; !LINE && !SCALED && i < a.n; i += stride) {
     T ri = fma(-alpha, a.q[i], a.r[i]);
     a.r[i] = ri;
     rz = fma(ri, a.dinv[i] * ri, rz);
@@ -436,8 +472,8 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
 }
 
 // K3: x += alpha p; p = z + beta p (the latter only while iterating; z = D^-1 r,
-// or LINE: the z K2 stored).
-template <typename T, bool LINE>
+// LINE: the z K2 stored, SCALED: z = r).
+template <typename T, bool LINE, bool SCALED = false>
 __global__ void __launch_bounds__(kThreads) k_it_xp(IterArgs<T> a) {
   Ctl* c = a.ctl;
   if (c->skip_x) return;
@@ -466,6 +502,12 @@ __global__ void __launch_bounds__(kThreads) k_it_xp(IterArgs<T> a) {
           constexpr int E = decltype(e)::value;
           comp<E>(pv) = fma(beta, comp<E>(pv), comp<E>(zv));
         });
+      } else if constexpr (SCALED) {
+        V rv = reinterpret_cast<const V*>(a.r)[k];
+        for_each_comp<W>([&](auto e) {
+          constexpr int E = decltype(e)::value;
+          comp<E>(pv) = fma(beta, comp<E>(pv), comp<E>(rv));
+        });
       } else {
         V rv = reinterpret_cast<const V*>(a.r)[k];
         V dv = reinterpret_cast<const V*>(a.dinv)[k];
@@ -480,7 +522,7 @@ __global__ void __launch_bounds__(kThreads) k_it_xp(IterArgs<T> a) {
   for (int64_t i = nv * W + tid; i < a.n; i += stride) {
     T pi = a.p[i];
     x[i] = fma(alpha, pi, x[i]);
-    if (upd_p) a.p[i] = fma(beta, pi, LINE ? a.line.z[i] : a.dinv[i] * a.r[i]);
+    if (upd_p) a.p[i] = fma(beta, pi, LINE ? a.line.z[i] : SCALED ? a.r[i] : a.dinv[i] * a.r[i]);
   }
 }
 
@@ -507,7 +549,7 @@ __global__ void __launch_bounds__(kThreads) k_res64(ResArgs a) {
         ri = bi;
         x[i] = 0.0;
       } else {
-        ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
+        ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i, a.n);
       }
       a.r[i] = ri;
     }
@@ -555,8 +597,9 @@ __global__ void __launch_bounds__(kThreads) k_res64(ResArgs a) {
 
 // Residual pass of the mixed solve: r = b - A x in FP64 with FP64 values,
 // its FP32 copy as the inner right-hand side, d = 0, p = z = D32^-1 r32
-// (LINE: z = M32^-1 r32, also stored for the continued refinement).
-template <bool LINE>
+// (LINE: z = M32^-1 r32, also stored for the continued refinement; SCALED:
+// the inner system is S A S, its right-hand side r32 = fl32(S r) and z = r32).
+template <bool LINE, bool SCALED = false>
 __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
   Ctl* c = a.ctl;
   const bool cold = c->pass == 0 && c->x_zero;
@@ -577,16 +620,20 @@ __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
         ri = bi;
         x[i] = 0.0;
       } else {
-        ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i);
+        ri = bi - row_dot_any<double>(a.parts, a.row_ptr, a.col, a.vals, x, i, a.n);
       }
     }
-    const float r32 = (float)ri;
-    float z32;
-    if constexpr (LINE) {
+    float r32, z32;
+    if constexpr (SCALED) {
+      r32 = valid ? (float)(a.s64[i] * ri) : 0.0f;
+      z32 = r32;
+    } else if constexpr (LINE) {
+      r32 = (float)ri;
       z32 = line_solve<float>(r32, valid ? a.line32.l[i] : 0.0f, valid ? a.line32.w[i] : 0.0f,
                               valid ? a.line32.g[i] : 0.0f, lane);
       if (valid) a.line32.z[i] = z32;
     } else {
+      r32 = (float)ri;
       z32 = valid ? a.dinv32[i] * r32 : 0.0f;
     }
     if (valid) {
@@ -620,17 +667,20 @@ __global__ void __launch_bounds__(kThreads) k_res_mixed(ResArgs a) {
     } else {
       go = true;
       c->outer += 1;
+      // half the outer target, in the inner residual's norm (scaled: carried
+      // over by the ratio of the scaled to the unscaled residual)
+      const double floor = 0.25 * c->thresh * (SCALED ? tot[3] / tot[1] : 1.0);
       if (a.ru) {
         // the FP64 residual replaces the FP32 one; the search direction continues
         c->ru_apply = first ? 0 : 1;
         c->beta_ru = first ? 0.0 : tot[0] / c->rz;
         // inner tolerance, or half the outer target (a residual just above the
         // target must still make progress: no endless one-step phases)
-        c->inner_thresh = fmax(c->ru_delta * c->ru_delta * tot[3], 0.25 * c->thresh);
+        c->inner_thresh = fmax(c->ru_delta * c->ru_delta * tot[3], floor);
       } else {
         // a reduction by inner_tol, but no further than half the outer target:
         // the last refinement stops near the target instead of far below it
-        c->inner_thresh = fmax(c->inner_tol * c->inner_tol * tot[3], 0.25 * c->thresh);
+        c->inner_thresh = fmax(c->inner_tol * c->inner_tol * tot[3], floor);
         c->iter = 0;
       }
       c->rz = tot[0];
@@ -651,6 +701,7 @@ struct CorrectArgs {
   const float* d;
   Ctl* c;
   SolveIO* io;
+  const double* s64;  // scaled inner system: x += S d
 };
 
 struct RuArgs {
@@ -662,22 +713,23 @@ struct RuArgs {
   const float* z32;  // LINE: M32^-1 r32 stored by the residual pass
 };
 
-// continued refinement: p = D32^-1 r32 + beta p (LINE: z32 + beta p) after the
-// residual was replaced
-template <bool LINE>
+// continued refinement: p = D32^-1 r32 + beta p (LINE: z32 + beta p, SCALED:
+// r32 + beta p) after the residual was replaced
+template <bool LINE, bool SCALED = false>
 __global__ void __launch_bounds__(kThreads) k_ru_p(RuArgs a) {
   if (!a.c->ru_apply) return;
   const float beta = (float)a.c->beta_ru;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
-    a.p32[i] = fmaf(beta, a.p32[i], LINE ? a.z32[i] : a.dinv32[i] * a.r32[i]);
+    a.p32[i] = fmaf(beta, a.p32[i], LINE ? a.z32[i] : SCALED ? a.r32[i] : a.dinv32[i] * a.r32[i]);
 }
 
-// x += d (FP64) after an inner FP32 solve.
+// x += d (FP64) after an inner FP32 solve (scaled inner system: x += S d).
 __global__ void __launch_bounds__(kThreads) k_correct(CorrectArgs a) {
   if (a.c->skip_correct || a.c->status == RP_BREAKDOWN || a.c->status == RP_DEVICE_TIMEOUT) return;
   double* __restrict__ x = a.io->x;
+  const double* __restrict__ s = a.s64;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += (double)a.d[i];
+    x[i] += s ? s[i] * (double)a.d[i] : (double)a.d[i];
 }
 
 __global__ void k_setup(Ctl* c, SolveIO* io, const double* b, double* x, double tol, double inner_tol, int x_zero,
@@ -711,7 +763,7 @@ __global__ void __launch_bounds__(kThreads)
                  double* xy, double* partials, unsigned int* ticket, Parts<double> parts) {
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = row_dot_any<double>(parts, row_ptr, col, vals, x, i);
+    double s = row_dot_any<double>(parts, row_ptr, col, vals, x, i, n);
     y[i] = s;
     acc += x[i] * s;
   }
@@ -762,6 +814,7 @@ struct GraphGuard {
 // of both precisions and the correction, with the Jacobi or line variants.
 struct SolveSet {
   bool line;
+  bool scaled;  // mixed: the inner FP32 iteration runs on S A S
   ResArgs ra;
   RuArgs ru;
   IterArgs<double> a64;
@@ -776,6 +829,7 @@ SolveSet solve_set(rp_handle* h, int mode, const double* vals, const double* din
   SolveSet k{};
   const bool mixed = mode != 0;
   k.line = h->precond == RP_PRECOND_LINE && vals == h->vals && h->ln_l != nullptr;
+  k.scaled = mixed && !k.line && vals == h->vals && h->sl_vals32s != nullptr;
   const Line<double> l64 = k.line ? Line<double>{h->ln_l, h->ln_w, h->ln_g, h->ln_z} : Line<double>{};
   const Line<float> l32 = k.line ? Line<float>{h->ln_l32, h->ln_w32, h->ln_g32, h->ln_z32} : Line<float>{};
   ResArgs& ra = k.ra;
@@ -800,13 +854,26 @@ SolveSet solve_set(rp_handle* h, int mode, const double* vals, const double* din
   ra.parts = parts64(h);
   ra.line = l64;
   ra.line32 = l32;
+  ra.s64 = k.scaled ? h->s64 : nullptr;
   k.ru = RuArgs{h->n, h->dinv32, h->r32, h->p32, h->ctl, h->ln_z32};
   k.a64 = IterArgs<double>{h->n, h->row_ptr, h->col_idx, vals, dinv, h->r, h->p, h->q, nullptr,
                            h->ctl, h->io, h->partials, hin, in_graph, parts64(h), sliced64(h, vals), l64};
   k.a32 = IterArgs<float>{h->n, h->row_ptr, h->col_idx, h->vals32, h->dinv32, h->r32, h->p32, h->q32, h->d32,
                           h->ctl, h->io, h->partials, hin, in_graph, parts32(h), sliced32(h), l32};
-  k.ca = CorrectArgs{h->n, h->d32, h->ctl, h->io};
-  if (k.line) {
+  k.ca = CorrectArgs{h->n, h->d32, h->ctl, h->io, k.scaled ? h->s64 : nullptr};
+  if (k.scaled) k.a32.sl.vals = h->sl_vals32s;  // same slices, the values of S A S
+  if (k.scaled) {
+    k.res = (void*)k_res_mixed<false, true>;
+    k.rup = (void*)k_ru_p<false, true>;
+    k.k2_64 = (void*)k_it_resid<double, false>;
+    k.k3_64 = (void*)k_it_xp<double, false>;
+    k.k2_32 = (void*)k_it_resid<float, false, true>;
+    k.k3_32 = (void*)k_it_xp<float, false, true>;
+    k.g2_64 = h->igrid64.k2;
+    k.g3_64 = h->igrid64.k3;
+    k.g2_32 = h->igrid32.k2s;
+    k.g3_32 = h->igrid32.k3s;
+  } else if (k.line) {
     k.res = mixed ? (void*)k_res_mixed<true> : (void*)k_res64<true>;
     k.rup = (void*)k_ru_p<true>;
     k.k2_64 = (void*)k_it_resid<double, true>;
@@ -922,6 +989,8 @@ IterGrid iter_grid(const rp_handle* h) {
   gr.k3 = g(resident((const void*)k_it_xp<T, false>));
   gr.k2l = g(resident((const void*)k_it_resid<T, true>));
   gr.k3l = g(resident((const void*)k_it_xp<T, true>));
+  gr.k2s = g(resident((const void*)k_it_resid<T, false, true>));
+  gr.k3s = g(resident((const void*)k_it_xp<T, false, true>));
   return gr;
 }
 
@@ -1093,6 +1162,8 @@ rp_status solve_common(rp_handle* h, int mode, const double* vals, const double*
   return RP_OK;
 }
 
+RP_CHECK_TU(pcg)
+
 }  // namespace rp
 
 using namespace rp;
@@ -1110,6 +1181,10 @@ extern "C" rp_status rp_solve(rp_handle* h, const double* b, double* x, double t
     return RP_OK;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (precision != RP_FP64 && h->precond == RP_PRECOND_JACOBI) {
+    bool ok = false;
+    RP_TRY(ensure_scaled(h, s, &ok));  // the inner FP32 iteration on S A S (sliced, one part)
+  }
   if (precision == RP_MIXED)
     return solve_common(h, 1, h->vals, h->dinv, &h->graphs.mixed, b, x, tol, x_is_guess, where, info, s);
   if (precision == RP_MIXED_RU)
@@ -1217,6 +1292,10 @@ extern "C" rp_status rp_profile_iteration(rp_handle* h, const double* b, int32_t
   if (h->n == 0) return fail(RP_EINVAL, "empty system");
   cudaStream_t s = (cudaStream_t)stream;
   const bool mixed = precision != RP_FP64;  // both mixed modes run the same FP32 iteration kernels
+  if (mixed && h->precond == RP_PRECOND_JACOBI) {
+    bool ok = false;
+    RP_TRY(ensure_scaled(h, s, &ok));  // the kernels the mixed solves run
+  }
   RP_TRY(dalloc(&h->x_host_stage, h->n + 64));
   // a fresh CG run from x = 0 that never meets its tolerance (tol = 0)
   k_setup<<<1, 1, 0, s>>>(h->ctl, h->io, b, h->x_host_stage, 0.0, 0.0, 1, iters + 2, 0, 1);

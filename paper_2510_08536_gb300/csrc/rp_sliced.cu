@@ -206,11 +206,12 @@ __global__ void __launch_bounds__(kThreads)
 template <bool FP32>
 __global__ void __launch_bounds__(kThreads)
     k_slice_vals(int64_t nq4, const int4* __restrict__ pos, const double* __restrict__ vals,
-                 double2* __restrict__ out, float4* __restrict__ out32) {
+                 double2* __restrict__ out, float4* __restrict__ out32, int64_t nnz) {
+  // a CSR position, or -1 for padding (bounds-checked build: anything else reads 0)
+  auto at = [&](int32_t q) { return q >= 0 && RP_IN(q, 0, nnz, kChkSliceValues) ? __ldg(vals + q) : 0.0; };
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq4; i += (int64_t)gridDim.x * blockDim.x) {
     const int4 p = __ldcs(pos + i);
-    const double a = p.x >= 0 ? __ldg(vals + p.x) : 0.0, b = p.y >= 0 ? __ldg(vals + p.y) : 0.0;
-    const double c = p.z >= 0 ? __ldg(vals + p.z) : 0.0, d = p.w >= 0 ? __ldg(vals + p.w) : 0.0;
+    const double a = at(p.x), b = at(p.y), c = at(p.z), d = at(p.w);
     __stcs(out + 2 * i, make_double2(a, b));
     __stcs(out + 2 * i + 1, make_double2(c, d));
     if (FP32) __stcs(out32 + i, make_float4((float)a, (float)b, (float)c, (float)d));
@@ -246,9 +247,11 @@ struct Tmp {
 
 void free_sliced(rp_handle* h) {
   void* ptrs[] = {h->sl_part_soff, h->sl_srow, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_pos,
-                  h->sl_vals, h->sl_vals32, h->sl_valsT};
+                  h->sl_vals, h->sl_vals32, h->sl_valsT, h->sl_vals32s, h->s64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  h->sl_vals32s = nullptr;
+  h->s64 = nullptr;
   h->sl_part_soff = nullptr;
   h->sl_srow = nullptr;
   h->sl_desc = nullptr;
@@ -394,6 +397,77 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
   return RP_OK;
 }
 
+// s_i = 1 / sqrt(a_ii): FP64 square root and division (both correctly rounded)
+__global__ void __launch_bounds__(kThreads)
+    k_scaling(int64_t n, const int32_t* __restrict__ diag_pos, const double* __restrict__ vals, int64_t nnz,
+              double* __restrict__ s64) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = diag_pos[i];
+    s64[i] = RP_IN(d, 0, nnz, kChkSliceValues) ? 1.0 / sqrt(__ldg(vals + d)) : 0.0;
+  }
+}
+
+// FP32 sliced values of S A S (one part: slice s holds rows 32 s ..) from the
+// FP64 sliced values: entry k of lane j of slice s is v = fl32(sv (s_i s_i')),
+// i = 32 s + j, with the column i' = i + its offset decoded from the slice's
+// table and index words as the iteration reads them, products in FP64, s_i s_i'
+// first (the diagonal comes out as exactly 1). Padding (value 0, offset 0)
+// stays 0. One warp per slice; reads the FP64 values and index words once,
+// coalesced, and s at the gathered rows.
+__global__ void __launch_bounds__(kThreads)
+    k_slice_vals_scaled(int64_t S, const uint2* __restrict__ desc, const uint32_t* __restrict__ tinfo,
+                        const int32_t* __restrict__ tabs, const uint32_t* __restrict__ ibuf,
+                        const double* __restrict__ sv, const double* __restrict__ s64, int64_t n,
+                        float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
+    const uint2 d0 = __ldg(desc + s), d1 = __ldg(desc + s + 1);
+    const uint32_t info = __ldg(tinfo + s);
+    const int32_t* tab = tabs + (info & ~kSliceW4);
+    const bool w4 = (info & kSliceW4) != 0;
+    const int per = w4 ? 8 : 4, bits = w4 ? 4 : 8;
+    const uint32_t mask = w4 ? 15u : 255u;
+    const int L = (int)((d1.x - d0.x) >> 5);
+    const int64_t i = s * kSliceRows + lane;
+    const bool valid = i < n;
+    const double si = valid ? __ldg(s64 + i) : 0.0;
+    uint32_t wd = 0;
+    for (int k = 0; k < L; ++k) {
+      if (k % per == 0) wd = __ldg(ibuf + d0.y + (uint32_t)(kSliceRows * (k / per)) + lane);
+      const int64_t q = d0.x + (int64_t)kSliceRows * k + lane;
+      const int64_t j = i + __ldg(tab + ((wd >> (bits * (k % per))) & mask));
+      float v = 0.0f;
+      if (valid && RP_IN(j, 0, n, kChkGather)) v = (float)(__ldcs(sv + q) * (si * __ldg(s64 + j)));
+      __stcs(out + q, v);
+    }
+  }
+}
+
+static rp_status fill_scaled(rp_handle* h, cudaStream_t s) {
+  k_scaling<<<grid_for(h, h->n), kThreads, 0, s>>>(h->n, h->diag_pos, h->vals, h->nnz, h->s64);
+  k_slice_vals_scaled<<<grid_for(h, h->sl_slices * kSliceRows), kThreads, 0, s>>>(
+      h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, reinterpret_cast<const uint32_t*>(h->sl_ibuf), h->sl_vals,
+      h->s64, h->n, h->sl_vals32s);
+  RP_TRY_CUDA(cudaGetLastError());
+  return RP_OK;
+}
+
+rp_status ensure_scaled(rp_handle* h, cudaStream_t s, bool* ok) {
+  *ok = h->n_parts == 1 && h->sl_slices > 0 && h->sl_vals32 != nullptr && h->n > 0;
+  if (!*ok || h->sl_vals32s) return RP_OK;
+  RP_TRY(salloc(&h->s64, h->n + 64));
+  rp_status st = salloc(&h->sl_vals32s, h->sl_entries);
+  if (st != RP_OK) {
+    cudaFree(h->s64);
+    h->s64 = nullptr;
+    return st;
+  }
+  return fill_scaled(h, s);
+}
+
+RP_CHECK_TU(sliced)
+
 rp_status fill_sliced(rp_handle* h, cudaStream_t s) {
   if (h->sl_slices == 0) return RP_OK;
   const int64_t nq4 = h->sl_entries / 4;  // a multiple of 32 entries
@@ -401,10 +475,12 @@ rp_status fill_sliced(rp_handle* h, cudaStream_t s) {
   const int4* pos = reinterpret_cast<const int4*>(h->sl_pos);
   double2* out = reinterpret_cast<double2*>(h->sl_vals);
   if (h->sl_vals32)
-    k_slice_vals<true><<<g, kThreads, 0, s>>>(nq4, pos, h->vals, out, reinterpret_cast<float4*>(h->sl_vals32));
+    k_slice_vals<true><<<g, kThreads, 0, s>>>(nq4, pos, h->vals, out, reinterpret_cast<float4*>(h->sl_vals32),
+                                              h->nnz);
   else
-    k_slice_vals<false><<<g, kThreads, 0, s>>>(nq4, pos, h->vals, out, nullptr);
+    k_slice_vals<false><<<g, kThreads, 0, s>>>(nq4, pos, h->vals, out, nullptr, h->nnz);
   RP_TRY_CUDA(cudaGetLastError());
+  if (h->sl_vals32s) RP_TRY(fill_scaled(h, s));
   return RP_OK;
 }
 
@@ -416,7 +492,7 @@ rp_status fill_sliced_transposed(rp_handle* h, cudaStream_t s) {
   if (!h->sl_valsT) RP_TRY(salloc(&h->sl_valsT, h->sl_entries));
   const int64_t nq4 = h->sl_entries / 4;
   k_slice_vals<false><<<grid_for(h, nq4), kThreads, 0, s>>>(nq4, reinterpret_cast<const int4*>(h->sl_pos), h->valsT,
-                                                            reinterpret_cast<double2*>(h->sl_valsT), nullptr);
+                                                            reinterpret_cast<double2*>(h->sl_valsT), nullptr, h->nnz);
   RP_TRY_CUDA(cudaGetLastError());
   return RP_OK;
 }
@@ -438,6 +514,8 @@ extern "C" rp_status rp_get_sliced_view(const rp_handle* h, rp_sliced_view* out)
   out->pos = h->sl_pos;
   out->vals = h->sl_vals;
   out->vals32 = h->sl_vals32;
+  out->vals32s = h->sl_vals32s;
+  out->scale = h->s64;
   out->srow = reinterpret_cast<const int32_t*>(h->sl_srow);
   return RP_OK;
 }

@@ -10,13 +10,29 @@
 
 namespace rp {
 
+// Row i of a CSR matrix with ncols columns (ncols bounds the gathers in the
+// bounds-checked build).
 template <typename T>
 __device__ __forceinline__ T row_dot(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                     const T* __restrict__ vals, const T* __restrict__ x, int64_t i) {
+                                     const T* __restrict__ vals, const T* __restrict__ x, int64_t i, int64_t ncols) {
   const int s = __ldg(row_ptr + i), e = __ldg(row_ptr + i + 1);
   T sum = T(0);
-  for (int j = s; j < e; ++j) sum = fma(__ldg(vals + j), __ldg(x + __ldg(col + j)), sum);
+  for (int j = s; j < e; ++j) {
+    const int c = __ldg(col + j);
+    if (RP_IN(c, 0, ncols, kChkGather)) sum = fma(__ldg(vals + j), __ldg(x + c), sum);
+  }
   return sum;
+}
+
+// Global row behind non-local entry j of part p (entry and compressed-column
+// offsets nlo, nco): the halo row the entry gathers. Bounds-checked build: -1
+// when the compressed column or its row is out of range.
+template <typename T>
+__device__ __forceinline__ int nl_row_of(const Parts<T>& P, int p, int64_t nlo, int64_t nco, int j) {
+  const int cc = __ldg(P.nl_col + nlo + j);
+  if (!RP_IN(cc, 0, __ldg(P.nlcol_off + p + 1) - nco, kChkNonlocal)) return -1;
+  const int g = __ldg(P.nl_cols + nco + cc);
+  return RP_IN(g, 0, __ldg(P.row_off + P.n), kChkNonlocal) ? g : -1;
 }
 
 // The non-local entries of row i (part p) added to sum in their CSR order:
@@ -27,8 +43,10 @@ __device__ __forceinline__ T nonlocal_add(const Parts<T>& P, int p, int64_t i, c
   const int64_t r0 = __ldg(P.row_off + p), li = i - r0;
   const int32_t* nrp = P.nl_row_ptr + r0 + p;
   const int64_t nlo = __ldg(P.nl_off + p), nco = __ldg(P.nlcol_off + p);
-  for (int j = __ldg(nrp + li); j < __ldg(nrp + li + 1); ++j)
-    sum = fma(__ldg(P.nl_vals + nlo + j), __ldg(x + __ldg(P.nl_cols + nco + __ldg(P.nl_col + nlo + j))), sum);
+  for (int j = __ldg(nrp + li); j < __ldg(nrp + li + 1); ++j) {
+    const int g = nl_row_of<T>(P, p, nlo, nco, j);
+    if (RP_IDX_OK(g)) sum = fma(__ldg(P.nl_vals + nlo + j), __ldg(x + g), sum);
+  }
   return sum;
 }
 
@@ -49,8 +67,10 @@ __device__ __forceinline__ T nonlocal_sum(const Parts<T>& P, int p, const NlRang
                                           T sum) {
   if (r.j0 == r.j1) return sum;
   const int64_t nlo = __ldg(P.nl_off + p), nco = __ldg(P.nlcol_off + p);
-  for (int j = r.j0; j < r.j1; ++j)
-    sum = fma(__ldg(P.nl_vals + nlo + j), __ldg(x + __ldg(P.nl_cols + nco + __ldg(P.nl_col + nlo + j))), sum);
+  for (int j = r.j0; j < r.j1; ++j) {
+    const int g = nl_row_of<T>(P, p, nlo, nco, j);
+    if (RP_IDX_OK(g)) sum = fma(__ldg(P.nl_vals + nlo + j), __ldg(x + g), sum);
+  }
   return sum;
 }
 
@@ -65,8 +85,10 @@ __device__ __forceinline__ T row_dot_parts(const Parts<T>& P, const int32_t* __r
   const int32_t* rp = row_ptr + r0 + p;
   const int64_t no = __ldg(P.nnz_off + p);
   T sum = T(0);
-  for (int j = __ldg(rp + li); j < __ldg(rp + li + 1); ++j)
-    sum = fma(__ldg(vals + no + j), __ldg(x + r0 + __ldg(col + no + j)), sum);
+  for (int j = __ldg(rp + li); j < __ldg(rp + li + 1); ++j) {
+    const int c = __ldg(col + no + j);
+    if (RP_IN(c, 0, __ldg(P.row_off + p + 1) - r0, kChkGather)) sum = fma(__ldg(vals + no + j), __ldg(x + r0 + c), sum);
+  }
   return nonlocal_add<T>(P, p, i, x, sum);
 }
 
@@ -79,11 +101,12 @@ inline Parts<float> parts32(const rp_handle* h) {
                       h->nl_row_ptr, h->nl_col_idx, h->nl_cols, h->nl_vals32};
 }
 
+// Row i of the merged matrix (n rows), one part or several.
 template <typename T>
 __device__ __forceinline__ T row_dot_any(const Parts<T>& P, const int32_t* __restrict__ row_ptr,
                                          const int32_t* __restrict__ col, const T* __restrict__ vals,
-                                         const T* __restrict__ x, int64_t i) {
-  return P.n > 1 ? row_dot_parts<T>(P, row_ptr, col, vals, x, i) : row_dot<T>(row_ptr, col, vals, x, i);
+                                         const T* __restrict__ x, int64_t i, int64_t n) {
+  return P.n > 1 ? row_dot_parts<T>(P, row_ptr, col, vals, x, i) : row_dot<T>(row_ptr, col, vals, x, i, n);
 }
 
 // The sliced layout of the iteration (with per-slice row records when the
@@ -92,12 +115,12 @@ inline Sliced<double> sliced64(const rp_handle* h, const double* vals) {
   const double* v = vals == h->vals ? h->sl_vals : vals == h->valsT ? h->sl_valsT : nullptr;
   if (h->sl_slices == 0 || !v) return Sliced<double>{};
   return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, v, h->opts.spin_limit,
-                        h->sl_srow};
+                        h->sl_srow, h->sl_entries, h->sl_ibuf_len, h->sl_tabs_len};
 }
 inline Sliced<float> sliced32(const rp_handle* h) {
   if (h->sl_slices == 0 || !h->sl_vals32) return Sliced<float>{};
   return Sliced<float>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_vals32,
-                       h->opts.spin_limit, h->sl_srow};
+                       h->opts.spin_limit, h->sl_srow, h->sl_entries, h->sl_ibuf_len, h->sl_tabs_len};
 }
 
 // Rows of slice s: the first (global) row, how many of its 32 lanes hold a
@@ -239,10 +262,36 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes
 enum : int { kIdx4 = 0, kIdx8Shfl = 1, kIdx8Glob = 2 };
 
 template <int MODE>
-__device__ __forceinline__ int slice_offset(uint32_t wd, int e, int32_t tv, const int32_t* tab) {
+__device__ __forceinline__ int slice_offset(uint32_t wd, int e, int32_t tv, const int32_t* tab, int D) {
   if (MODE == kIdx4) return __shfl_sync(0xffffffffu, tv, (int)(wd >> (4 * e)), 16);
   if (MODE == kIdx8Shfl) return __shfl_sync(0xffffffffu, tv, (int)(wd >> (8 * e)));
+#ifdef RP_CHECK
+  return __ldg(tab + min((int)((wd >> (8 * e)) & 255u), D - 1));  // in the table; the index is checked apart
+#else
+  (void)D;
   return __ldg(tab + ((wd >> (8 * e)) & 255u));
+#endif
+}
+
+// Bounds of one lane's gathers in the bounds-checked build: admissible
+// offsets col - row of the lane's row, [lo, hi), and the lengths of the
+// arrays the slice's descriptor and table reference index.
+struct SliceCk {
+  int lo, hi;
+  int64_t entries, ibuf, tabs;
+};
+
+// Bounds-checked build: is index e of word wd inside the slice's table of D
+// offsets, and the offset it names inside the lane's admissible range?
+template <int MODE>
+__device__ __forceinline__ bool slice_ok(uint32_t wd, int e, int off, int D, const SliceCk& ck) {
+#ifdef RP_CHECK
+  const int id = MODE == kIdx4 ? (int)((wd >> (4 * e)) & 15u) : (int)((wd >> (8 * e)) & 255u);
+  return RP_IN(id, 0, D, kChkSliceIndex) && RP_IN(off, ck.lo, ck.hi, kChkGather);
+#else
+  (void)wd, (void)e, (void)off, (void)D, (void)ck;
+  return true;
+#endif
 }
 
 // A gather from x: read-only path, or (COH) a plain load for a vector that the
@@ -259,7 +308,7 @@ __device__ __forceinline__ T xload(const T* p) {
 // (valid false) run the shuffles but load nothing.
 template <typename T, int MODE, int L, bool COH = false>
 __device__ __forceinline__ T slice_row_exact(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab,
-                                             const T* x, bool valid) {
+                                             const T* x, bool valid, int D, const SliceCk& ck) {
   constexpr int PER = MODE == kIdx4 ? 8 : 4;
   const uint32_t w0 = iw[0], w1 = L > PER ? iw[kSliceRows] : 0u;
   T vv[L];
@@ -268,24 +317,25 @@ __device__ __forceinline__ T slice_row_exact(const T* v, const uint32_t* iw, int
   T sum = T(0);
 #pragma unroll
   for (int k = 0; k < L; ++k) {
-    const int off = slice_offset<MODE>(k < PER ? w0 : w1, k % PER, tv, tab);
-    if (valid) sum = fma(vv[k], xload<COH>(x + off), sum);
+    const uint32_t wd = k < PER ? w0 : w1;
+    const int off = slice_offset<MODE>(wd, k % PER, tv, tab, D);
+    if (valid && slice_ok<MODE>(wd, k % PER, off, D, ck)) sum = fma(vv[k], xload<COH>(x + off), sum);
   }
   return sum;
 }
 
 template <typename T, int MODE, bool COH = false>
 __device__ __forceinline__ T slice_row(const T* v, const uint32_t* iw, int32_t tv, const int32_t* tab, const T* x,
-                                       bool valid, int L) {
+                                       bool valid, int L, int D, const SliceCk& ck) {
   switch (L) {
-    case 1: return slice_row_exact<T, MODE, 1, COH>(v, iw, tv, tab, x, valid);
-    case 2: return slice_row_exact<T, MODE, 2, COH>(v, iw, tv, tab, x, valid);
-    case 3: return slice_row_exact<T, MODE, 3, COH>(v, iw, tv, tab, x, valid);
-    case 4: return slice_row_exact<T, MODE, 4, COH>(v, iw, tv, tab, x, valid);
-    case 5: return slice_row_exact<T, MODE, 5, COH>(v, iw, tv, tab, x, valid);
-    case 6: return slice_row_exact<T, MODE, 6, COH>(v, iw, tv, tab, x, valid);
-    case 7: return slice_row_exact<T, MODE, 7, COH>(v, iw, tv, tab, x, valid);
-    case 8: return slice_row_exact<T, MODE, 8, COH>(v, iw, tv, tab, x, valid);
+    case 1: return slice_row_exact<T, MODE, 1, COH>(v, iw, tv, tab, x, valid, D, ck);
+    case 2: return slice_row_exact<T, MODE, 2, COH>(v, iw, tv, tab, x, valid, D, ck);
+    case 3: return slice_row_exact<T, MODE, 3, COH>(v, iw, tv, tab, x, valid, D, ck);
+    case 4: return slice_row_exact<T, MODE, 4, COH>(v, iw, tv, tab, x, valid, D, ck);
+    case 5: return slice_row_exact<T, MODE, 5, COH>(v, iw, tv, tab, x, valid, D, ck);
+    case 6: return slice_row_exact<T, MODE, 6, COH>(v, iw, tv, tab, x, valid, D, ck);
+    case 7: return slice_row_exact<T, MODE, 7, COH>(v, iw, tv, tab, x, valid, D, ck);
+    case 8: return slice_row_exact<T, MODE, 8, COH>(v, iw, tv, tab, x, valid, D, ck);
     default: break;
   }
   constexpr int PER = MODE == kIdx4 ? 8 : 4;
@@ -295,24 +345,85 @@ __device__ __forceinline__ T slice_row(const T* v, const uint32_t* iw, int32_t t
 #pragma unroll
     for (int e = 0; e < PER; ++e)
       if (PER * g + e < L) {
-        const int off = slice_offset<MODE>(wd, e, tv, tab);
-        if (valid) sum = fma(v[(PER * g + e) * kSliceRows], xload<COH>(x + off), sum);
+        const int off = slice_offset<MODE>(wd, e, tv, tab, D);
+        if (valid && slice_ok<MODE>(wd, e, off, D, ck))
+          sum = fma(v[(PER * g + e) * kSliceRows], xload<COH>(x + off), sum);
       }
   }
   return sum;
 }
 
+// Bounds-checked build: the slice's descriptor pair, row length, index words
+// and table reference inside their arrays (warp-uniform: the whole warp
+// skips a bad slice); D receives the table's length.
+__device__ __forceinline__ bool slice_desc_ok(uint2 d0, uint2 d1, uint32_t info, const int32_t* __restrict__ tabs,
+                                              const SliceCk& ck, int& D) {
+#ifdef RP_CHECK
+  const int64_t t = info & ~kSliceW4;
+  if (!RP_IN(d0.x, 0, ck.entries + 1, kChkSliceDesc) || !RP_IN(d1.x, d0.x, ck.entries + 1, kChkSliceDesc) ||
+      !RP_IN(d1.x - d0.x, 0, kSliceRows * kSliceMaxWidth + 1, kChkSliceDesc) || ((d1.x - d0.x) & 31u) != 0u ||
+      !RP_IN(d0.y, 0, ck.ibuf + 1, kChkSliceDesc) || !RP_IN(d1.y, d0.y, ck.ibuf + 1, kChkSliceDesc) ||
+      !RP_IN(t, 1, ck.tabs, kChkSliceDesc))
+    return false;
+  D = __ldg(tabs + t - 1);
+  const int L = (int)((d1.x - d0.x) >> 5), per = (info & kSliceW4) ? 8 : 4;
+  return RP_IN(D, 1, (info & kSliceW4) ? 17 : kSliceMaxDict + 1, kChkSliceDesc) &&
+         RP_IN(t + D, t, ck.tabs - 32 + 1, kChkSliceDesc) &&  // the 32 spare words stay past every table
+         RP_IN(d1.y - d0.y, (int64_t)kSliceRows * ((L + per - 1) / per), (int64_t)kSliceRows * ((L + per - 1) / per) + 1,
+               kChkSliceDesc);
+#else
+  (void)d0, (void)d1, (void)info, (void)tabs, (void)ck, (void)D;
+  return true;
+#endif
+}
+
 // One slice: descriptor pair (d0, d1), table reference info, values v and
 // index words iw (shared memory or global, lane applied), tables tabs (global),
-// gathers from x relative to the lane's row (COH: plain loads, see xload).
+// gathers from x relative to the lane's row (COH: plain loads, see xload);
+// ck: the bounds the checked build tests.
 template <typename T, bool COH = false>
 __device__ __forceinline__ T slice_sum(uint2 d0, uint2 d1, uint32_t info, const T* v, const uint32_t* iw,
-                                       const int32_t* __restrict__ tabs, const T* x, bool valid, int lane) {
+                                       const int32_t* __restrict__ tabs, const T* x, bool valid, int lane,
+                                       const SliceCk& ck) {
+  int D = 0;
+  if (!slice_desc_ok(d0, d1, info, tabs, ck, D)) return T(0);
   const int L = (int)((d1.x - d0.x) >> 5);
   const int32_t* tab = tabs + (info & ~kSliceW4);
-  if (info & kSliceW4) return slice_row<T, kIdx4, COH>(v, iw, __ldg(tab + (lane & 15)), tab, x, valid, L);
-  if (__ldg(tab - 1) <= 32) return slice_row<T, kIdx8Shfl, COH>(v, iw, __ldg(tab + lane), tab, x, valid, L);
-  return slice_row<T, kIdx8Glob, COH>(v, iw, 0, tab, x, valid, L);
+  if (info & kSliceW4) return slice_row<T, kIdx4, COH>(v, iw, __ldg(tab + (lane & 15)), tab, x, valid, L, D, ck);
+  if (__ldg(tab - 1) <= 32) return slice_row<T, kIdx8Shfl, COH>(v, iw, __ldg(tab + lane), tab, x, valid, L, D, ck);
+  return slice_row<T, kIdx8Glob, COH>(v, iw, 0, tab, x, valid, L, D, ck);
+}
+
+// The gather bounds of a lane's row in the bounds-checked build: the rows of
+// its part (several parts, MP) or of the matrix.
+template <typename T, bool MP>
+__device__ __forceinline__ SliceCk slice_ck(const Sliced<T>& sl, const Parts<T>& P, int part, int row, int n) {
+#ifdef RP_CHECK
+  int64_t lo = 0, hi = n;
+  if (MP) {
+    lo = __ldg(P.row_off + part);
+    hi = __ldg(P.row_off + part + 1);
+  }
+  return SliceCk{(int)(lo - row), (int)(hi - row), sl.n_entries, sl.ibuf_len, sl.tabs_len};
+#else
+  (void)sl, (void)P, (void)part, (void)row, (void)n;
+  return SliceCk{};
+#endif
+}
+
+// Bounds-checked build: the source ranges of a chunk's four staged copies
+// inside their arrays (values, index words, descriptor run, table references).
+template <typename T>
+__device__ __forceinline__ bool chunk_copy_ok(const Sliced<T>& sl, uint2 d0, uint2 d1, int ch, uint32_t db) {
+#ifdef RP_CHECK
+  return RP_IN(d0.x, 0, sl.n_entries + 1, kChkSliceCopy) && RP_IN(d1.x, d0.x, sl.n_entries + 1, kChkSliceCopy) &&
+         RP_IN(d0.y, 0, sl.ibuf_len + 1, kChkSliceCopy) && RP_IN(d1.y, d0.y, sl.ibuf_len + 1, kChkSliceCopy) &&
+         RP_IN((int64_t)ch * kChunk + db / 8, 0, sl.n_slices + 1 + kSliceDescPad + 1, kChkSliceCopy) &&
+         RP_IN((int64_t)ch * kChunk + kStageInfo / 4, 0, sl.n_slices + kSliceDescPad + 1, kChkSliceCopy);
+#else
+  (void)sl, (void)d0, (void)d1, (void)ch, (void)db;
+  return true;
+#endif
 }
 
 // MP: several parts (slice rows from the per-slice records, non-local sums);
@@ -365,7 +476,8 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, const Parts<T>&
         }
         unsigned char* base = sbuf + st * St::kBytes;
         const uint32_t vb = (d1.x - d0.x) * (uint32_t)sizeof(T), ib = (d1.y - d0.y) * 4u;
-        const bool fit = vb <= (uint32_t)St::kVals && ib <= (uint32_t)kStageIdx;
+        const uint32_t db = 16u * (uint32_t)((kChunk + 2) / 2);  // kChunk + 1 descriptors, 16-byte multiple
+        const bool fit = vb <= (uint32_t)St::kVals && ib <= (uint32_t)kStageIdx && chunk_copy_ok(sl, d0, d1, ch, db);
         chunk_x[st] = d0.x;
         chunk_y[st] = d0.y;
         staged[st] = fit;
@@ -373,7 +485,6 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, const Parts<T>&
         // empty[st]) before the async-proxy writes of the copy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (fit) {
-          const uint32_t db = 16u * (uint32_t)((kChunk + 2) / 2);  // kChunk + 1 descriptors, 16-byte multiple
           mbar_expect_tx(&full[st], vb + ib + db + kStageInfo);
           bulk_g2s(base, sl.vals + d0.x, vb, &full[st]);
           bulk_g2s(base + St::kVals, sl.ibuf + d0.y, ib, &full[st]);
@@ -404,6 +515,7 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, const Parts<T>&
         if constexpr (MP)
           if (valid) nl = nonlocal_range<T>(parts, sr.part, row);
         const T* x = xin + row;
+        const SliceCk ck = slice_ck<T, MP>(sl, parts, sr.part, row, n);
         const unsigned char* base = sbuf + st * St::kBytes;
         T sum;
         if (staged[st]) {
@@ -412,11 +524,11 @@ __device__ __forceinline__ void spmv_sl_body(const Sliced<T> sl, const Parts<T>&
           const uint2 d0 = sd[w], d1 = sd[w + 1];
           sum = slice_sum<T>(d0, d1, si[w], reinterpret_cast<const T*>(base) + (d0.x - chunk_x[st]) + lane,
                              reinterpret_cast<const uint32_t*>(base + St::kVals) + (d0.y - chunk_y[st]) + lane,
-                             sl.tabs, x, valid, lane);
+                             sl.tabs, x, valid, lane, ck);
         } else {
           const uint2 d0 = __ldg(desc + s), d1 = __ldg(desc + s + 1);
           sum = slice_sum<T>(d0, d1, __ldg(sl.tinfo + s), sl.vals + d0.x + lane,
-                             reinterpret_cast<const uint32_t*>(sl.ibuf + d0.y) + lane, sl.tabs, x, valid, lane);
+                             reinterpret_cast<const uint32_t*>(sl.ibuf + d0.y) + lane, sl.tabs, x, valid, lane, ck);
         }
         if constexpr (MP) sum = nonlocal_sum<T>(parts, sr.part, nl, xin, sum);
         if (valid) {
@@ -449,7 +561,7 @@ __device__ __forceinline__ void spmv_csr_body(int64_t n, const Parts<T>& parts, 
                                               const int32_t* __restrict__ col, const T* __restrict__ vals,
                                               const T* xin, T* yout, Epi& epi) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T s = row_dot_any<T>(parts, row_ptr, col, vals, xin, i);
+    const T s = row_dot_any<T>(parts, row_ptr, col, vals, xin, i, n);
     yout[i] = s;
     epi.row(i, s);
   }

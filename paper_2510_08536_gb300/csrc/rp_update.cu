@@ -12,10 +12,15 @@
 
 namespace rp {
 
+// buffer value at slot s (bounds-checked build: slots outside [0, len) read 0)
+__device__ __forceinline__ double slot_value(const double* __restrict__ buf, int32_t s, int64_t len) {
+  return RP_IN(s, 0, len, kChkPermute) ? __ldg(buf + s) : 0.0;
+}
+
 template <bool FP32>
 __global__ void __launch_bounds__(kThreads)
     k_permute(const double* __restrict__ buf, const int32_t* __restrict__ src_of, double* __restrict__ vals,
-              float* __restrict__ vals32, int64_t nnz) {
+              float* __restrict__ vals32, int64_t nnz, int64_t buf_len) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool vec = ((reinterpret_cast<uintptr_t>(src_of) | reinterpret_cast<uintptr_t>(vals)) & 15) == 0 &&
@@ -28,7 +33,8 @@ __global__ void __launch_bounds__(kThreads)
     float4* f4 = reinterpret_cast<float4*>(vals32);
     for (int64_t i = tid; i < nv; i += stride) {
       int4 s = __ldcs(s4 + i);
-      double a = __ldg(buf + s.x), b = __ldg(buf + s.y), c = __ldg(buf + s.z), d = __ldg(buf + s.w);
+      double a = slot_value(buf, s.x, buf_len), b = slot_value(buf, s.y, buf_len), c = slot_value(buf, s.z, buf_len),
+             d = slot_value(buf, s.w, buf_len);
       __stcs(v2 + 2 * i, make_double2(a, b));
       __stcs(v2 + 2 * i + 1, make_double2(c, d));
       if (FP32) __stcs(f4 + i, make_float4((float)a, (float)b, (float)c, (float)d));
@@ -36,7 +42,7 @@ __global__ void __launch_bounds__(kThreads)
     done = nv << 2;
   }
   for (int64_t i = done + tid; i < nnz; i += stride) {
-    double a = __ldg(buf + src_of[i]);
+    double a = slot_value(buf, src_of[i], buf_len);
     vals[i] = a;
     if (FP32) vals32[i] = (float)a;
   }
@@ -60,22 +66,23 @@ __global__ void __launch_bounds__(kThreads)
 static rp_status permute_all(rp_handle* h, const double* buf, cudaStream_t s) {
   for (int p = 0; p < h->n_parts; ++p) {
     const double* base = buf + h->part_buf_off[p];
+    const int64_t blen = h->part_buf_off[p + 1] - h->part_buf_off[p];
     int64_t o = h->part_nnz_off[p], cnt = h->part_nnz_off[p + 1] - o;
     int g = grid_for(h, (cnt + 3) / 4);
     if (cnt > 0) {
       if (h->want_fp32)
-        k_permute<true><<<g, kThreads, 0, s>>>(base, h->src_of + o, h->vals + o, h->vals32 + o, cnt);
+        k_permute<true><<<g, kThreads, 0, s>>>(base, h->src_of + o, h->vals + o, h->vals32 + o, cnt, blen);
       else
-        k_permute<false><<<g, kThreads, 0, s>>>(base, h->src_of + o, h->vals + o, nullptr, cnt);
+        k_permute<false><<<g, kThreads, 0, s>>>(base, h->src_of + o, h->vals + o, nullptr, cnt, blen);
     }
     int64_t no = h->part_nl_off[p], ncnt = h->part_nl_off[p + 1] - no;
     if (ncnt > 0) {
       if (h->want_fp32)
         k_permute<true><<<grid_for(h, (ncnt + 3) / 4), kThreads, 0, s>>>(base, h->nl_src_of + no, h->nl_vals + no,
-                                                                         h->nl_vals32 + no, ncnt);
+                                                                         h->nl_vals32 + no, ncnt, blen);
       else
         k_permute<false><<<grid_for(h, (ncnt + 3) / 4), kThreads, 0, s>>>(base, h->nl_src_of + no,
-                                                                          h->nl_vals + no, nullptr, ncnt);
+                                                                          h->nl_vals + no, nullptr, ncnt, blen);
     }
   }
   if (h->n > 0) {
@@ -143,6 +150,10 @@ static rp_status update_host_async(rp_handle* h, const double* buffer, cudaStrea
 }  // namespace rp
 
 using namespace rp;
+
+namespace rp {
+RP_CHECK_TU(update)
+}
 
 // Can the current device read this host pointer in place?
 static rp_status check_host_direct(const void* p) {

@@ -57,7 +57,8 @@ class SolveInfo(ctypes.Structure):
 
 class SlicedView(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("n_slices", "n_entries", "ibuf_len", "tabs_len")] + \
-               [(k, ctypes.c_void_p) for k in ("desc", "tinfo", "tabs", "ibuf", "pos", "vals", "vals32", "srow")]
+               [(k, ctypes.c_void_p) for k in ("desc", "tinfo", "tabs", "ibuf", "pos", "vals", "vals32", "srow",
+                                               "vals32s", "scale")]
 
 
 class MapView(ctypes.Structure):
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rp_profile_iteration": (i32, [vp, vp, i32, i32, ctypes.POINTER(ctypes.c_float), vp]),
         "rp_entry_grad": (i32, [vp, vp, vp, vp, vp]),
         "rp_face_grad": (i32, [vp, vp, vp, vp, vp]),
+        "rp_check_violations": (i32, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i32), ctypes.POINTER(i64), i32]),
         "rp_destroy": (None, [vp]),
         "rp_status_str": (ctypes.c_char_p, [i32]),
         "rp_last_error": (ctypes.c_char_p, []),
@@ -289,6 +291,14 @@ def sliced_sizes(h: Handle):
     return (v.n_slices, v.n_entries, v.ibuf_len, v.tabs_len) if v.n_slices else None
 
 
+def inner_scaled(h: Handle) -> bool:
+    """Whether the mixed solves' FP32 iteration runs on the scaled system S A S
+    (made by the first mixed solve on a handle that takes it)."""
+    v = SlicedView()
+    _check(load().rp_get_sliced_view(h.ptr, ctypes.byref(v)), "rp_get_sliced_view")
+    return bool(v.vals32s)
+
+
 def get_sliced_view(h: Handle) -> dict:
     """rp_get_sliced_view, copied into torch tensors on the device (None when
     the iteration runs on the CSR arrays)."""
@@ -306,7 +316,9 @@ def get_sliced_view(h: Handle) -> dict:
                 pos=_view(v.pos, v.n_entries, "<i4").clone(),
                 vals=_view(v.vals, v.n_entries, "<f8").clone(),
                 vals32=_view(v.vals32, v.n_entries, "<f4").clone() if v.vals32 else None,
-                srow=_view(v.srow, 2 * v.n_slices, "<i4").clone() if v.srow else None)
+                srow=_view(v.srow, 2 * v.n_slices, "<i4").clone() if v.srow else None,
+                vals32s=_view(v.vals32s, v.n_entries, "<f4").clone() if v.vals32s else None,
+                scale=_view(v.scale, h.n, "<f8").clone() if v.scale else None)
 
 
 def batch_build(systems, want_fp32: bool = True, **opts) -> Handle:
@@ -439,6 +451,15 @@ def face_grad(h: Handle, lam, x, g_face, stream=None):
     _check(load().rp_face_grad(h.ptr, _ptr(lam), _ptr(x), _ptr(g_face), _stream(stream)), "rp_face_grad")
 
 
+def check_violations(reset: bool = False):
+    """rp_check_violations (bounds-checked library only): (accesses skipped,
+    first site, first index) since the last reset; waits for the device."""
+    c, site, idx = ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().rp_check_violations(ctypes.byref(c), ctypes.byref(site), ctypes.byref(idx), int(reset)),
+           "rp_check_violations")
+    return c.value, site.value, idx.value
+
+
 @dataclasses.dataclass
 class Exports:
     """Names the header declares (checked against the loaded library)."""
@@ -447,4 +468,5 @@ class Exports:
                     "rp_solve_adjoint", "rp_profile_iteration", "rp_entry_grad", "rp_face_grad", "rp_destroy", "rp_status_str",
                     "rp_last_error", "rp_spmv_noalloc", "rp_batch_build", "rp_batch_update_solve",
                     "rp_batch_set_config", "rp_batch_autotune", "rp_set_solver_options", "rp_iter_spmv",
-                    "rp_get_sliced_view", "rp_solve_bicgstab", "rp_solve_bicgstab_mixed", "rp_get_solve_info")
+                    "rp_get_sliced_view", "rp_solve_bicgstab", "rp_solve_bicgstab_mixed", "rp_get_solve_info",
+                    "rp_check_violations")

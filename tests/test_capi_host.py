@@ -152,3 +152,16 @@ def test_get_solve_info_rejects_null(lib):
 
 def test_update_rejects_unknown_where(lib):
     assert lib.rp_update_values_packed(None, None, repart.RP_MEM_HOST_ASYNC, None) == repart.RP_EINVAL
+
+
+def test_check_violations_needs_the_checked_build(lib):
+    """The normal library answers RP_EUNSUPPORTED with a zero count; the
+    bounds-checked variant (built next to it) exports the same symbols."""
+    c, site, idx = ctypes.c_uint64(7), ctypes.c_int32(7), ctypes.c_int64(7)
+    st = lib.rp_check_violations(ctypes.byref(c), ctypes.byref(site), ctypes.byref(idx), 0)
+    assert st == repart.RP_EUNSUPPORTED and c.value == 0 and site.value == 0 and idx.value == -1
+    assert lib.rp_check_violations(None, None, None, 0) == repart.RP_EINVAL
+    path = build.build(check=True)
+    chk = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(chk, name), name

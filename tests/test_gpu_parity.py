@@ -205,6 +205,22 @@ def test_fp64_solve_parity(dims, parts, sigma):
     h.close()
 
 
+def _inner_count_ok(got, oracle, fp64):
+    """Inner FP32 iteration counts depend on rounding order (the kernels sum dot
+    products per thread in FP32, the oracle in FP64), by several percent either
+    way: no fewer than exact PCG needs (95% of the FP64 count, less 5) and no
+    more than 10% above the oracle's form (+ 10). A lost correction or a wrong
+    recurrence costs far more."""
+    assert 0.95 * fp64 - 5 <= got <= 1.10 * oracle + 10, (got, oracle, fp64)
+
+
+def _scaled_system(c):
+    """The oracle's scaling s = fl32(1/sqrt(a_ii)) and FP32 matrix S A S."""
+    s_ = O.jacobi_scaling(c.vals[c.map.diag_pos])
+    return s_, O.csr_matrix(c.map.row_ptr, c.map.col_idx,
+                            O.scaled_fp32_values(c.map.row_ptr, c.map.col_idx, c.vals, s_))
+
+
 def test_mixed_solve_parity():
     c = Case((32, 32, 32), (2, 2, 2), sigma=1.0)
     h = repart.build_repartition(c.mesh.ranks)
@@ -215,17 +231,16 @@ def test_mixed_solve_parity():
     assert info["status"] == repart.RP_OK, info
     assert info["outer_iterations"] >= 2
     assert c.true_rel_residual(xs) <= 1e-9
-    v32 = O.to_fp32(c.vals)
-    A32 = O.csr_matrix(c.map.row_ptr, c.map.col_idx, v32)
-    ref = O.mixed_ir(c.A, A32, np.float32(1) / v32[c.map.diag_pos], c.b, tol=1e-9)
+    # the inner FP32 iteration runs on S A S (sliced layout, one part, Jacobi)
+    s_, Ah32 = _scaled_system(c)
+    ref = O.mixed_ir_scaled(c.A, Ah32, s_, c.b, tol=1e-9)
     assert ref.status == O.OK
     x64 = O.pcg(c.A, c.dinv, c.b, tol=1e-12).x
     assert np.linalg.norm(xs - x64) / np.linalg.norm(x64) <= 1e-6
     assert abs(info["outer_iterations"] - ref.outer_iterations) <= 1
-    # the inner FP32 recurrence: total inner iterations as the oracle's (FP32
-    # rounding order differs, so loosely), and the last pass stops near the
-    # target like the oracle's (half of it), not far below
-    assert abs(info["iterations"] - ref.iterations) <= 5 + 0.05 * ref.iterations, (info, ref.iterations)
+    # the inner FP32 recurrence: total inner iterations as the oracle's, and the
+    # last pass stops near the target like the oracle's (half of it), not far below
+    _inner_count_ok(info["iterations"], ref.iterations, O.pcg(c.A, c.dinv, c.b, tol=1e-9).iterations)
     assert 1e-10 <= info["rel_residual"] <= 1e-9 and 1e-10 <= ref.true_rel_residual <= 1e-9
     h.close()
 
@@ -241,14 +256,12 @@ def test_mixed_continued_solve_parity(sigma):
     xs = x.cpu().numpy()
     assert info["status"] == repart.RP_OK, info
     assert c.true_rel_residual(xs) <= 1e-9
-    v32 = O.to_fp32(c.vals)
-    A32 = O.csr_matrix(c.map.row_ptr, c.map.col_idx, v32)
-    ref = O.mixed_reliable(c.A, A32, np.float32(1) / v32[c.map.diag_pos], c.b, tol=1e-9, delta=0.1)
+    s_, Ah32 = _scaled_system(c)
+    ref = O.mixed_reliable_scaled(c.A, Ah32, s_, c.b, tol=1e-9, delta=0.1)
     assert ref.status == O.OK
     x64 = O.pcg(c.A, c.dinv, c.b, tol=1e-12).x
     assert np.linalg.norm(xs - x64) / np.linalg.norm(x64) <= 1e-6
-    # FP32 rounding order differs from the oracle's: iteration counts agree loosely
-    assert abs(info["iterations"] - ref.iterations) <= 5 + 0.05 * ref.iterations, (info, ref.iterations)
+    _inner_count_ok(info["iterations"], ref.iterations, O.pcg(c.A, c.dinv, c.b, tol=1e-9).iterations)
     h.close()
 
 

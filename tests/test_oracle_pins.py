@@ -704,3 +704,81 @@ def test_c_oracle_edge_cases():
     ref = O.pcg(O.csr_matrix(m.row_ptr, m.col_idx, neg), 1.0 / neg[m.diag_pos], b)
     # D^-1 A is unchanged but p.Ap < 0 at once
     assert r.status == ref.status == O.BREAKDOWN and r.iterations == ref.iterations == 0
+
+
+# ---------------------------------------------------------------- scaled inner system
+
+
+def _scaled(mesh, sigma):
+    m, vals, A, dinv, _, _ = _system(mesh, sigma)
+    s = O.jacobi_scaling(vals[m.diag_pos])
+    Ah32 = O.csr_matrix(m.row_ptr, m.col_idx, O.scaled_fp32_values(m.row_ptr, m.col_idx, vals, s))
+    return m, vals, A, dinv, s, Ah32
+
+
+def test_scaled_values_are_s_a_s():
+    """fl32(a_ij s_i s_j) against the dense product S A S in FP64: within FP32
+    rounding, a diagonal of exact ones, exactly symmetric; s_i^2 a_ii = 1 to
+    FP64 rounding."""
+    mesh = synth.box_mesh(7, 6, 5, 2, 1, 1)
+    m, vals, A, dinv, s, Ah32 = _scaled(mesh, 1.0)
+    d = A.diagonal()
+    assert s.dtype == np.float64
+    assert np.all(np.abs(s * s * d - 1.0) <= 4 * 2.0 ** -53)
+    dense = (s[:, None] * A.toarray()) * s[None, :]
+    got = Ah32.toarray().astype(np.float64)
+    assert np.all(np.abs(got - dense) <= 2.0 ** -24 * np.abs(dense) * (1 + 1e-12) + 1e-300)
+    assert np.array_equal(got, got.T)
+    assert np.array_equal(np.diag(got), np.ones(mesh.n_cells))
+
+
+def test_cg_on_scaled_system_is_jacobi_pcg():
+    """CG without a preconditioner on S A S from S b, mapped back by S, is PCG on
+    A with the preconditioner S^2 iterate for iterate (FP64 arithmetic, FP64
+    scaled matrix): the equivalence the scaled inner solves rest on. S^2 is the
+    Jacobi inverse D^-1 to FP64 rounding, so the iterates are Jacobi-PCG's."""
+    mesh = synth.box_mesh(12, 10, 8, 2, 1, 1)
+    m, vals, A, dinv, s, _ = _scaled(mesh, 1.0)
+    b = synth.uniform_vector(mesh, 0)
+    sd = s
+    row = np.repeat(np.arange(mesh.n_cells), np.diff(m.row_ptr))
+    Ah64 = O.csr_matrix(m.row_ptr, m.col_idx, vals * (sd[row] * sd[m.col_idx]))
+    for k in (1, 2, 7, 20):
+        y, it, st = O.pcg_fp32(Ah64, lambda v: v, sd * b, rel_tol=0.0, max_iter=k, dtype=np.float64)
+        ref = O.pcg(A, sd * sd, b, tol=0.0, max_iter=k)
+        assert it == k == ref.iterations
+        assert np.linalg.norm(sd * y - ref.x) / np.linalg.norm(ref.x) <= 1e-12, k
+        jac = O.pcg(A, dinv, b, tol=0.0, max_iter=k)
+        assert np.linalg.norm(sd * y - jac.x) / np.linalg.norm(jac.x) <= 1e-11, k
+
+
+def test_scaled_refinement_forms():
+    """Both refinement forms with FP32 inner solves on the scaled system reach the
+    FP64 residual 1e-9 with iteration counts within 5% of the Jacobi-preconditioned
+    forms; the restarted form's last pass stops near the target; with an exact (FP64)
+    inner solve the continued form reproduces plain PCG up to the rounding of its
+    residual replacements."""
+    mesh = synth.box_mesh(16, 16, 16, 2, 2, 2)
+    m, vals, A, dinv, s, Ah32 = _scaled(mesh, 1.0)
+    b = synth.uniform_vector(mesh, 0)
+    v32 = O.to_fp32(vals)
+    A32 = O.csr_matrix(m.row_ptr, m.col_idx, v32)
+    d32 = np.float32(1) / v32[m.diag_pos]
+    x = np.linalg.solve(A.toarray(), b)
+    for scaled, plain in ((O.mixed_reliable_scaled(A, Ah32, s, b, tol=1e-9, delta=0.1),
+                           O.mixed_reliable(A, A32, d32, b, tol=1e-9, delta=0.1)),
+                          (O.mixed_ir_scaled(A, Ah32, s, b, tol=1e-9), O.mixed_ir(A, A32, d32, b, tol=1e-9))):
+        assert scaled.status == O.OK
+        assert np.linalg.norm(b - A @ scaled.x) / np.linalg.norm(b) <= 1e-9
+        assert np.linalg.norm(scaled.x - x) / np.linalg.norm(x) < 1e-6
+        assert abs(scaled.iterations - plain.iterations) <= 0.05 * plain.iterations + 2
+    ir = O.mixed_ir_scaled(A, Ah32, s, b, tol=1e-9)
+    assert 1e-10 <= ir.true_rel_residual <= 1e-9 and ir.outer_iterations >= 2
+    sd = s
+    row = np.repeat(np.arange(mesh.n_cells), np.diff(m.row_ptr))
+    Ah64 = O.csr_matrix(m.row_ptr, m.col_idx, vals * (sd[row] * sd[m.col_idx]))
+    ref = O.pcg(A, dinv, b, tol=1e-10)
+    ex = O.mixed_reliable_scaled(A, Ah64, s, b, tol=1e-10, delta=0.1, dtype=np.float64)
+    assert ex.status == O.OK
+    assert abs(ex.iterations - ref.iterations) <= 2 + ex.outer_iterations // 2
+    assert np.linalg.norm(ex.x - ref.x) / np.linalg.norm(ref.x) < 1e-8
