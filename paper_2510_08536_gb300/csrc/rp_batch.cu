@@ -36,13 +36,11 @@ namespace rp {
 
 namespace {
 
+// Built for two CTAs of 512 threads an SM: 64 registers a thread (the kernel
+// spills some). A build with 80 registers (two CTAs of 384, fewer spills, 24
+// warps an SM) measured slower in every launch shape (continued refinement,
+// 256 systems: 219-417 ms against 201 ms): warps in flight matter more here.
 constexpr int kBatchMaxThreads = 512;
-// Register budget of the persistent kernel: BUDGET 0 is built for two CTAs of
-// 512 threads an SM (64 registers a thread; the kernel spills), BUDGET 1 for
-// two CTAs of 384 (80 registers; a few spills, fewer warps). CTAs of 256 or 512
-// threads run the first, of 128 or 384 the second, so the launch-shape
-// autotuner weighs warps in flight against spills.
-constexpr int batch_budget(int threads) { return (threads == 128 || threads == 384) ? 1 : 0; }
 
 // Block-wide sum of NV values, then cluster-wide through DSMEM; every thread
 // of every CTA returns the same totals.
@@ -255,9 +253,9 @@ __device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, FS&
 }  // namespace
 
 // MODE: 0 FP64 PCG, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG;
-// SL: the SpMV and residual passes run on the sliced layout; BUDGET: see batch_budget
-template <int MODE, bool SL, int BUDGET>
-__global__ void __launch_bounds__(BUDGET ? 384 : kBatchMaxThreads, 2) k_batch(BatchArgs a) {
+// SL: the SpMV and residual passes run on the sliced layout
+template <int MODE, bool SL>
+__global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
   constexpr bool MIXED = MODE != 0;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned T = cl.num_blocks();
@@ -617,22 +615,15 @@ rp_status balloc(T** p, int64_t count) {
   return RP_OK;
 }
 
-template <int BUDGET>
-void* batch_kernel_b(int mode, bool sl) {
-  if (sl)
-    return mode == 2 ? (void*)k_batch<2, true, BUDGET>
-           : mode == 1 ? (void*)k_batch<1, true, BUDGET> : (void*)k_batch<0, true, BUDGET>;
-  return mode == 2 ? (void*)k_batch<2, false, BUDGET>
-         : mode == 1 ? (void*)k_batch<1, false, BUDGET> : (void*)k_batch<0, false, BUDGET>;
-}
-void* batch_kernel(int mode, bool sl, int threads) {
-  return batch_budget(threads) ? batch_kernel_b<1>(mode, sl) : batch_kernel_b<0>(mode, sl);
+void* batch_kernel(int mode, bool sl) {
+  if (sl) return mode == 2 ? (void*)k_batch<2, true> : mode == 1 ? (void*)k_batch<1, true> : (void*)k_batch<0, true>;
+  return mode == 2 ? (void*)k_batch<2, false> : mode == 1 ? (void*)k_batch<1, false> : (void*)k_batch<0, false>;
 }
 
 rp_status launch_config(rp_handle* h, int mode, int cluster, int threads, cudaLaunchConfig_t* cfg,
                         cudaLaunchAttribute* attr, int* n_clusters) {
   const bool sl = h->batch_args.sl_desc != nullptr;
-  void* fn = batch_kernel(mode, sl, threads);
+  void* fn = batch_kernel(mode, sl);
   if (cluster > 8) RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   const int smem = sl ? (threads / 32) * kWarpStage : 0;
   RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -668,7 +659,7 @@ rp_status build_batch_graph(rp_handle* h, int mode, int cluster, int threads, cu
   if (e == cudaSuccess) {
     cudaMemsetAsync(h->batch_queue, 0, sizeof(unsigned int), cs);
     void* args[] = {&ba};
-    cudaLaunchKernelExC(&cfg, batch_kernel(mode, ba.sl_desc != nullptr, threads), args);
+    cudaLaunchKernelExC(&cfg, batch_kernel(mode, ba.sl_desc != nullptr), args);
     e = cudaStreamEndCapture(cs, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
@@ -851,7 +842,7 @@ extern "C" rp_status rp_batch_autotune(rp_handle* h, const double* buffer, const
   RP_TRY(batch_prepare(h));
   cudaStream_t s = (cudaStream_t)stream;
   const int clusters[] = {2, 4, 8, 16};
-  const int threads[] = {128, 256, 384, 512};
+  const int threads[] = {128, 256, 512};
   cudaEvent_t e0, e1;
   RP_TRY_CUDA(cudaEventCreate(&e0));
   RP_TRY_CUDA(cudaEventCreate(&e1));
