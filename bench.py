@@ -431,10 +431,13 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
         iters = [sum(i["iterations"] for i in infos) for infos in infos_all]
         # algorithmic bytes of one step: update (24 B/entry + 20 B/row, plus the sliced
         # values: position, source index, buffer value, FP64 (and FP32) value per padded
-        # entry), every iteration (FP64: SpMV + 80 B/row; FP32: SpMV + 40 B/row), every
-        # FP64 residual pass; SpMV on CSR: values, columns, row pointers, x, y; sliced:
-        # padded values, index words, descriptors and table references, x, y
+        # entry), every iteration (FP64: SpMV + 80 B/row; FP32: SpMV + 40 B/row, 32 on the
+        # scaled system S A S that the mixed forms run on the sliced layout: no diagonal
+        # reads; its FP32 values add a column and s_j per padded entry and s per row to the
+        # update), every FP64 residual pass; SpMV on CSR: values, columns, row pointers, x,
+        # y; sliced: padded values, index words, descriptors and table references, x, y
         w = 8 if prec == "fp64" else 4
+        scaled_b = prec != "fp64" and sl_sizes is not None
         moved = 0.0
         for infos in infos_all:
             for s, inf in enumerate(infos):
@@ -443,12 +446,12 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
                     E, I, S = sl_sizes[s]
                     spmv = w * E + 4 * I + 12 * S + 2 * w * nn
                     res = 8 * E + 4 * I + 12 * S + 40 * nn
-                    upd = 24 * nz + 20 * nn + (24 + (w == 4) * 4) * E
+                    upd = 24 * nz + 20 * nn + (24 + (w == 4) * 4) * E + (12 * E + 8 * nn if scaled_b else 0)
                 else:
                     spmv = (w + 4) * nz + 4 * (nn + 1) + 2 * w * nn
                     res = 12 * nz + 4 * (nn + 1) + 40 * nn
                     upd = 24 * nz + 20 * nn
-                moved += upd + inf["iterations"] * (spmv + 10 * w * nn) + inf["passes"] * res
+                moved += upd + inf["iterations"] * (spmv + (8 if scaled_b else 10) * w * nn) + inf["passes"] * res
         gbps = moved / len(infos_all) / (ms * 1e-3) / 1e9
         out[prec] = {"ms_per_step": round(ms, 3), "not_converged_systems": bad,
                      "iterations_sum_mean": statistics.mean(iters),

@@ -378,7 +378,11 @@ rp_status rp_batch_build(const rp_ldu_desc* systems, int32_t count, const rp_opt
 /* One batched time step: the value update of every system from `buffer`
  * (all systems' continuous buffers concatenated; where = host or device)
  * and the solve of every system to its own ||b_s - A_s x_s|| <= tol ||b_s||
- * from x_s = 0 (precision RP_FP64 or RP_MIXED), all in ONE persistent kernel
+ * from x_s = 0 (precision RP_FP64, RP_MIXED or RP_MIXED_RU; on the sliced
+ * layout the mixed forms' FP32 iteration runs on the symmetrically scaled
+ * system S A S, s_i = 1/sqrt(a_ii) in FP64, FP32 values fl32(a_ij (s_i s_j)),
+ * which the kernel writes into the sliced view's vals32), all in ONE
+ * persistent kernel
  * launched from a CUDA graph (instantiated on first use per precision).
  * b and x are device pointers (n_rows doubles, system order). Thread-block
  * clusters act as teams that take systems largest first from a device work

@@ -289,6 +289,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
     float* vals32 = MIXED ? a.vals32 + no : nullptr;
     double* dinv = a.dinv + ro;
     float* dinv32 = MIXED ? a.dinv32 + ro : nullptr;
+    // mixed on the sliced layout: the inner iteration runs on S A S (Jacobi made
+    // explicit, unit diagonal: no diagonal reads in the FP32 vector passes)
+    constexpr bool SCALED = MIXED && SL;
+    double* s64 = SCALED ? a.s64 + ro : nullptr;
     const double* b = ball + ro;
     double* x = xall + ro;
     constexpr bool sl = SL;
@@ -316,8 +320,33 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
       const double d = buf[i];  // diagonal block leads the system's buffer
       dinv[i] = 1.0 / d;
       if (MIXED) dinv32[i] = 1.0f / (float)d;
+      if (SCALED) s64[i] = 1.0 / sqrt(d);
     }
-    if (sl && i0 < i1) {
+    if constexpr (SCALED) {
+      cl.sync();  // s of every row of the system before the scaled values use it
+      // this CTA's slices, one warp per slice: FP64 values from the buffer and the
+      // FP32 values of S A S, fl32(a_ij (s_i s_j)) (products in FP64); padding 0
+      const int lane = tid & 31;
+      const int64_t nw = nth >> 5, ls1 = (i1 + 31) >> 5;
+      for (int64_t ls = (i0 >> 5) + (tid >> 5); i0 < i1 && ls < ls1; ls += nw) {
+        const uint2 d0 = __ldg(a.sl_desc + s0 + ls), d1 = __ldg(a.sl_desc + s0 + ls + 1);
+        const int64_t i = (ls << 5) + lane;
+        const double si = i < n ? s64[i] : 0.0;
+        for (uint32_t e = d0.x + lane; e < d1.x; e += 32) {
+          const int32_t pp = __ldg(a.sl_pos + e);
+          double v = 0.0;
+          float v32 = 0.0f;
+          if (pp >= 0 && RP_IN(pp, 0, a.nnz_off[a.n_sys], kChkSliceValues) &&
+              RP_IN(__ldg(a.src_of + pp), 0, blen, kChkPermute)) {
+            v = buf[__ldg(a.src_of + pp)];
+            const int32_t j = __ldg(a.col + pp);
+            if (RP_IN(j, 0, n, kChkGather)) v32 = (float)(v * (si * s64[j]));
+          }
+          a.sl_vals[e] = v;
+          a.sl_vals32[e] = v32;
+        }
+      }
+    } else if (sl && i0 < i1) {
       // this CTA's slices, padding included (zero values)
       const int64_t e0 = __ldg(a.sl_desc + s0 + (i0 >> 5)).x, e1 = __ldg(a.sl_desc + s0 + ((i1 + 31) >> 5)).x;
       for (int64_t e = e0 + tid; e < e1; e += nth) {
@@ -454,10 +483,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
         double v4[4] = {0.0, 0.0, 0.0, 0.0}, t4[4];
         float rzf = 0.f, rr32f = 0.f;
         auto res_row = [&](int64_t i, double ri) {
-          const float r32 = (float)ri;
+          const float r32 = SCALED ? (float)(s64[i] * ri) : (float)ri;
           r[i] = r32;
           d[i] = 0.f;
-          const float z32 = dinv32[i] * r32;
+          const float z32 = SCALED ? r32 : dinv32[i] * r32;
           if (!RU || passes == 0) p[i] = z32;
           rzf = fmaf(r32, z32, rzf);
           rr32f = fmaf(r32, r32, rr32f);
@@ -491,11 +520,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
         if (RU && !first) {
           // the FP64 residual replaced the FP32 one: continue the search direction
           const float beta = (float)(t4[0] / rz);
-          for (int64_t i = i0 + tid; i < i1; i += nth) p[i] = fmaf(beta, p[i], dinv32[i] * r[i]);
+          for (int64_t i = i0 + tid; i < i1; i += nth) p[i] = fmaf(beta, p[i], SCALED ? r[i] : dinv32[i] * r[i]);
         }
         rz = t4[0];
+        // a reduction by ru_delta (inner_tol), or half the outer target in the inner
+        // residual's norm (scaled: carried over by the ratio of the two residuals)
         const double ithresh = fmax((RU ? a.ru_delta * a.ru_delta : a.inner_tol * a.inner_tol) * t4[3],
-                                    0.25 * thresh);
+                                    0.25 * thresh * (SCALED ? t4[3] / t4[1] : 1.0));
         int it = 0;
         bool broke = false;
         for (;;) {
@@ -514,26 +545,27 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           float a0 = 0.f, a1 = 0.f;
           auto rstep = [&](float& rv, float qv, float dv) {
             rv = fmaf(-alpha, qv, rv);
-            a0 = fmaf(rv, dv * rv, a0);
+            if (!SCALED) a0 = fmaf(rv, dv * rv, a0);
             a1 = fmaf(rv, rv, a1);
           };
           rows_vec<4>(
               ro, i0, i1,
               [&](int64_t i) {
                 float ri = r[i];
-                rstep(ri, q[i], dinv32[i]);
+                rstep(ri, q[i], SCALED ? 1.0f : dinv32[i]);
                 r[i] = ri;
               },
               [&](int64_t v) {
                 const float4 qv = reinterpret_cast<const float4*>(a.q32)[v];
                 float4 rv = reinterpret_cast<const float4*>(a.r32)[v];
-                const float4 dv = reinterpret_cast<const float4*>(a.dinv32)[v];
+                const float4 dv = SCALED ? make_float4(1.f, 1.f, 1.f, 1.f) : reinterpret_cast<const float4*>(a.dinv32)[v];
                 rstep(rv.x, qv.x, dv.x);
                 rstep(rv.y, qv.y, dv.y);
                 rstep(rv.z, qv.z, dv.z);
                 rstep(rv.w, qv.w, dv.w);
                 reinterpret_cast<float4*>(a.r32)[v] = rv;
               });
+          if (SCALED) a0 = a1;  // z = r: (r, z) = (r, r)
           double v2[2] = {(double)a0, (double)a1}, t2[2];
           team_sum<2>(v2, t2, cl, spart, swarp, parity);
           ++it;
@@ -548,7 +580,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
               [&](int64_t i) {
                 const float pi = p[i];
                 d[i] = fmaf(alpha, pi, d[i]);
-                if (!stop) p[i] = fmaf(beta, pi, dinv32[i] * r[i]);
+                if (!stop) p[i] = fmaf(beta, pi, SCALED ? r[i] : dinv32[i] * r[i]);
               },
               [&](int64_t v) {
                 float4 pv = reinterpret_cast<const float4*>(a.p32)[v];
@@ -560,7 +592,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
                 reinterpret_cast<float4*>(a.d32)[v] = dd;
                 if (!stop) {
                   const float4 rv = reinterpret_cast<const float4*>(a.r32)[v];
-                  const float4 iv = reinterpret_cast<const float4*>(a.dinv32)[v];
+                  const float4 iv = SCALED ? make_float4(1.f, 1.f, 1.f, 1.f) : reinterpret_cast<const float4*>(a.dinv32)[v];
                   pv.x = fmaf(beta, pv.x, iv.x * rv.x);
                   pv.y = fmaf(beta, pv.y, iv.y * rv.y);
                   pv.z = fmaf(beta, pv.z, iv.z * rv.z);
@@ -574,7 +606,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
         // row by row, so every thread of the CTA must have finished its writes
         __syncthreads();
         if (!broke) {
-          for (int64_t i = i0 + tid; i < i1; i += nth) x[i] += (double)d[i];
+          for (int64_t i = i0 + tid; i < i1; i += nth) x[i] += SCALED ? s64[i] * (double)d[i] : (double)d[i];
         }
         cl.sync();  // x visible before the next residual pass
       }
@@ -739,6 +771,8 @@ rp_status batch_prepare(rp_handle* h) {
   a.sl_pos = sl ? h->sl_pos : nullptr;
   a.sl_vals = sl ? h->sl_vals : nullptr;
   a.sl_vals32 = sl ? h->sl_vals32 : nullptr;
+  if (sl && h->want_fp32) RP_TRY(balloc(&h->batch_s64, h->n + 64));
+  a.s64 = h->batch_s64;
   a.sl_entries = h->sl_entries;
   a.sl_ibuf_len = h->sl_ibuf_len;
   a.sl_tabs_len = h->sl_tabs_len;
@@ -750,7 +784,7 @@ RP_CHECK_TU(batch)
 
 void free_batch(rp_handle* h) {
   void* ptrs[] = {h->batch_order, h->batch_row_off, h->batch_nnz_off, h->batch_buf_off, h->batch_queue,
-                  h->batch_info, h->batch_io};
+                  h->batch_info, h->batch_io, h->batch_s64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& g : h->batch_graphs)

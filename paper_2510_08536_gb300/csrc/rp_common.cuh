@@ -271,6 +271,9 @@ struct BatchArgs {
   double* sl_vals;
   float* sl_vals32;
   int64_t sl_entries, sl_ibuf_len, sl_tabs_len;  // array lengths (bounds-checked build)
+  // mixed forms on the sliced layout: the inner FP32 iteration runs on S A S,
+  // s_i = 1/sqrt(a_ii) (FP64), written by the kernel's update
+  double* s64;
 };
 
 }  // namespace rp
@@ -391,6 +394,7 @@ struct rp_handle {
   rp_solve_info* batch_info = nullptr;
   rp::BatchIO* batch_io = nullptr;
   rp::BatchArgs batch_args{};
+  double* batch_s64 = nullptr;  // s_i = 1/sqrt(a_ii) of the batched mixed forms
   cudaGraphExec_t batch_graphs[3] = {nullptr, nullptr, nullptr};
 };
 

@@ -393,7 +393,6 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
       rz = fma(ri, zi, rz);
       rr = fma(ri, ri, rr);
     }
-    k = nv;  // the Jacobi loops below do nothing
   }
   if constexpr (SCALED) {
     // unit diagonal: z = r, so (r, z) = (r, r) and no diagonal is read
@@ -425,30 +424,31 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
       rr = fma(ri, ri, rr);
     }
     rz = rr;
-    k = nv;  // the Jacobi loops below do nothing
   }
-  // two vectors of each stream in flight per thread
-  for (; k + stride < nv; k += 2 * stride) {
-    V q0 = reinterpret_cast<const V*>(a.q)[k], q1 = reinterpret_cast<const V*>(a.q)[k + stride];
-    V r0 = reinterpret_cast<const V*>(a.r)[k], r1 = reinterpret_cast<const V*>(a.r)[k + stride];
-    V d0 = reinterpret_cast<const V*>(a.dinv)[k], d1 = reinterpret_cast<const V*>(a.dinv)[k + stride];
-    step(r0, q0, d0);
-    step(r1, q1, d1);
-    reinterpret_cast<V*>(a.r)[k] = r0;
-    reinterpret_cast<V*>(a.r)[k + stride] = r1;
-  }
-  for (; k < nv; k += stride) {
-    V qv = reinterpret_cast<const V*>(a.q)[k];
-    V rv = reinterpret_cast<const V*>(a.r)[k];
-    V dv = reinterpret_cast<const V*>(a.dinv)[k];
-    step(rv, qv, dv);
-    reinterpret_cast<V*>(a.r)[k] = rv;
-  }
-  for (int64_t i = nv * W + tid; !LINE && !SCALED && i < a.n; i += stride) {
-    T ri = fma(-alpha, a.q[i], a.r[i]);
-    a.r[i] = ri;
-    rz = fma(ri, a.dinv[i] * ri, rz);
-    rr = fma(ri, ri, rr);
+  if constexpr (!LINE && !SCALED) {
+    // two vectors of each stream in flight per thread
+    for (; k + stride < nv; k += 2 * stride) {
+      V q0 = reinterpret_cast<const V*>(a.q)[k], q1 = reinterpret_cast<const V*>(a.q)[k + stride];
+      V r0 = reinterpret_cast<const V*>(a.r)[k], r1 = reinterpret_cast<const V*>(a.r)[k + stride];
+      V d0 = reinterpret_cast<const V*>(a.dinv)[k], d1 = reinterpret_cast<const V*>(a.dinv)[k + stride];
+      step(r0, q0, d0);
+      step(r1, q1, d1);
+      reinterpret_cast<V*>(a.r)[k] = r0;
+      reinterpret_cast<V*>(a.r)[k + stride] = r1;
+    }
+    for (; k < nv; k += stride) {
+      V qv = reinterpret_cast<const V*>(a.q)[k];
+      V rv = reinterpret_cast<const V*>(a.r)[k];
+      V dv = reinterpret_cast<const V*>(a.dinv)[k];
+      step(rv, qv, dv);
+      reinterpret_cast<V*>(a.r)[k] = rv;
+    }
+    for (int64_t i = nv * W + tid; i < a.n; i += stride) {
+      T ri = fma(-alpha, a.q[i], a.r[i]);
+      a.r[i] = ri;
+      rz = fma(ri, a.dinv[i] * ri, rz);
+      rr = fma(ri, ri, rr);
+    }
   }
   double v[2] = {(double)rz, (double)rr}, tot[2];
   if (reduce_last_block<2>(v, a.partials, &c->ticket, tot) && threadIdx.x == 0) {

@@ -72,7 +72,9 @@ def test_batch_maps_and_values_bit_exact(batch):
 
 def test_batch_sliced_layout_per_system(batch):
     """Every system gets its own 32-row slices (part-local rows and columns,
-    global CSR positions); the kernel writes their values from the buffer."""
+    global CSR positions); the kernel writes their values from the buffer: the
+    FP64 values, and for its mixed forms the FP32 values of the scaled system
+    S A S, fl32(a_ij (s_i s_j)) with s_i = 1/sqrt(a_ii), bit for bit the oracle's."""
     B, stg, b, refs = batch
     h = repart.batch_build(B.systems)
     x = torch.zeros(B.n_rows, dtype=torch.float64, device=DEV)
@@ -95,7 +97,10 @@ def test_batch_sliced_layout_per_system(batch):
         lp = local[e0:e1]
         want = np.where(lp >= 0, ref["vals"][np.maximum(lp, 0)], 0.0)
         np.testing.assert_array_equal(vals[e0:e1], want, err_msg=str(s))
-        np.testing.assert_array_equal(vals32[e0:e1], want.astype(np.float32), err_msg=str(s))
+        s_ = O.jacobi_scaling(ref["vals"][ref["map"].diag_pos])
+        w32 = O.scaled_fp32_values(ref["map"].row_ptr, ref["map"].col_idx, ref["vals"], s_)
+        want32 = np.where(lp >= 0, w32[np.maximum(lp, 0)], np.float32(0))
+        np.testing.assert_array_equal(vals32[e0:e1], want32, err_msg=str(s))
         nnz0 += ref["vals"].size
     h.close()
 
@@ -127,15 +132,22 @@ def test_batch_solves_match_oracle(batch, precision, layout):
             assert np.linalg.norm(xi - ref["exact"]) / np.linalg.norm(ref["exact"]) <= 1e-6
             assert inf["outer_iterations"] >= 1
             # FP32 rounding order differs from the oracle's, but the iteration count must
-            # stay close: a lost refinement correction would show up here
-            v32 = O.to_fp32(ref["vals"])
-            A32 = O.csr_matrix(ref["map"].row_ptr, ref["map"].col_idx, v32)
-            d32 = np.float32(1) / v32[ref["map"].diag_pos]
-            if precision == "mixed":
-                o = O.mixed_ir(ref["A"], A32, d32, ref["b"], tol=1e-9, inner_tol=1e-5)
+            # stay close: a lost refinement correction would show up here. On the sliced
+            # layout the inner iteration runs on S A S, on CSR Jacobi-preconditioned on A.
+            m = ref["map"]
+            if layout == "sliced":
+                s_ = O.jacobi_scaling(ref["vals"][m.diag_pos])
+                Ah = O.csr_matrix(m.row_ptr, m.col_idx, O.scaled_fp32_values(m.row_ptr, m.col_idx, ref["vals"], s_))
+                o = (O.mixed_ir_scaled(ref["A"], Ah, s_, ref["b"], tol=1e-9) if precision == "mixed" else
+                     O.mixed_reliable_scaled(ref["A"], Ah, s_, ref["b"], tol=1e-9, delta=0.1))
             else:
-                o = O.mixed_reliable(ref["A"], A32, d32, ref["b"], tol=1e-9, delta=0.1)
-            assert inf["iterations"] <= 1.25 * o.iterations + 10, (s, inf, o.iterations)
+                v32 = O.to_fp32(ref["vals"])
+                A32 = O.csr_matrix(m.row_ptr, m.col_idx, v32)
+                d32 = np.float32(1) / v32[m.diag_pos]
+                o = (O.mixed_ir(ref["A"], A32, d32, ref["b"], tol=1e-9, inner_tol=1e-5) if precision == "mixed" else
+                     O.mixed_reliable(ref["A"], A32, d32, ref["b"], tol=1e-9, delta=0.1))
+            assert 0.95 * ref["fp64"].iterations - 5 <= inf["iterations"] <= 1.10 * o.iterations + 10, \
+                (s, inf, o.iterations, ref["fp64"].iterations)
     h.close()
 
 
