@@ -392,14 +392,15 @@ rp_status rp_batch_build(const rp_ldu_desc* systems, int32_t count, const rp_opt
 rp_status rp_batch_update_solve(rp_handle* h, const double* buffer, int32_t where, const double* b, double* x,
                                 double tol, int32_t precision, rp_solve_info* info, void* stream);
 
-/* Launch shape of the batched kernel: cluster size (1, 2, 4, 8, 16 CTAs per
- * team) and threads per CTA (multiple of 32, <= 512). RP_EUNSUPPORTED if
- * the shape cannot be scheduled. Default 8 x 512. */
+/* Launch shape of the batched kernel: cluster size (1 to 16 CTAs per team;
+ * above 8 a non-portable cluster size) and threads per CTA (multiple of 32,
+ * <= 512). RP_EINVAL outside those ranges, RP_EUNSUPPORTED if the shape
+ * cannot be scheduled. Default 5 x 512. */
 rp_status rp_batch_set_config(rp_handle* h, int32_t cluster, int32_t threads);
 
 /* Autotuner: times rp_batch_update_solve (device buffer, precision) for every
- * cluster size in {2, 4, 8, 16} and CTA size in {128, 256, 512}, keeps the
- * fastest shape in the handle and reports it. Overwrites x. Blocks. */
+ * cluster size in {2, 3, 4, 5, 6, 8, 16} and CTA size in {256, 512}, keeps
+ * the fastest shape in the handle and reports it. Overwrites x. Blocks. */
 rp_status rp_batch_autotune(rp_handle* h, const double* buffer, const double* b, double* x, double tol,
                             int32_t precision, int32_t* best_cluster, int32_t* best_threads, float* best_ms,
                             void* stream);

@@ -63,13 +63,14 @@ __device__ __forceinline__ void team_sum(double (&v)[NV], double (&tot)[NV], cg:
     }
   }
   cl.sync();
+  // lane r reads CTA r's partials (all T remote loads in flight at once), then
+  // an xor butterfly over the warp: every step adds the same two operands in
+  // both lanes of a pair (addition commutes exactly), so every thread of every
+  // CTA ends with the same bits
   const unsigned T = cl.num_blocks();
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double t = 0.0;
-    for (unsigned r = 0; r < T; ++r) t += *cl.map_shared_rank(&spart[parity][i], r);
-    tot[i] = t;
-  }
+  for (int i = 0; i < NV; ++i)
+    tot[i] = warp_sum((unsigned)lane < T ? *cl.map_shared_rank(&spart[parity][i], (unsigned)lane) : 0.0);
   parity ^= 1;
 }
 
@@ -88,11 +89,12 @@ __device__ __forceinline__ T row_dot_coherent(const int32_t* __restrict__ rp, co
 }
 
 // y_i = (A x)_i for rows [i0, i1) of this CTA, two independent rows per thread
-// in flight (rows i and i + blockDim, so each warp stays coalesced); f(i, y_i)
-// consumes every result.
+// in flight (rows i and i + blockDim, so each warp stays coalesced); f(i, y_i,
+// pre_i) consumes every result (pre: a vector the consumer reads at row i).
 template <typename T, typename F>
 __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                          const T* vals, const T* x, int64_t i0, int64_t i1, int64_t n, F&& f) {
+                                          const T* vals, const T* x, const T* pre, int64_t i0, int64_t i1,
+                                          int64_t n, F&& f) {
   const int64_t nth = blockDim.x;
   int64_t i = i0 + threadIdx.x;
   for (; i + nth < i1; i += 2 * nth) {
@@ -107,10 +109,10 @@ __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const 
       if (s1 + t < e1 && RP_IN(__ldg(col + s1 + t), 0, n, kChkGather))
         a1 = fma(vals[s1 + t], x[__ldg(col + s1 + t)], a1);
     }
-    f(i, a0);
-    f(k, a1);
+    f(i, a0, pre[i]);
+    f(k, a1, pre[k]);
   }
-  for (; i < i1; i += nth) f(i, row_dot_coherent<T>(rp, col, vals, x, i, n));
+  for (; i < i1; i += nth) f(i, row_dot_coherent<T>(rp, col, vals, x, i, n), pre[i]);
 }
 
 // Per-warp staging of one slice's values and index words (slices of up to
@@ -159,12 +161,14 @@ __device__ __forceinline__ bool stageable(uint2 d0, uint2 d1, const BatchArgs& a
 // order as the CSR row sums. The warp's next slice is copied (cp.async, L2
 // only) into its other staging buffer while the current one is summed, so the
 // value and index loads of one slice overlap the gathers of the previous one;
-// descriptors are loaded two slices ahead. Values and x are written inside the
-// kernel (the values before a block barrier, read back through L2; x with
-// plain loads); descriptors, tables and index words are read-only.
+// descriptors are loaded two slices ahead. f(i, y_i, pre_i) consumes every
+// result; pre_i (a vector the consumer reads at row i) is loaded before the
+// slice's gathers, so its latency hides behind theirs. Values and x are written
+// inside the kernel (the values before a block barrier, read back through L2;
+// x and pre with plain loads); descriptors, tables and index words are read-only.
 template <typename T, typename F>
-__device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, int64_t s0, const T* x, int64_t i0,
-                                            int64_t i1, int64_t n, unsigned char* stage, F&& f) {
+__device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, int64_t s0, const T* x, const T* pre,
+                                            int64_t i0, int64_t i1, int64_t n, unsigned char* stage, F&& f) {
   if (i0 >= i1) return;  // i0 = n need not be a multiple of 32
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t nw = blockDim.x >> 5, end = (i1 + 31) >> 5;
@@ -202,6 +206,7 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
     __syncwarp();
     const int64_t row = (ls << 5) + lane;
     const bool valid = row < i1;
+    const T prow = valid ? pre[row] : T(0);
 #ifdef RP_CHECK
     const SliceCk ck{(int)(-row), (int)(n - row), a.sl_entries, a.sl_ibuf_len, a.sl_tabs_len};
 #else
@@ -218,7 +223,7 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
       sum = slice_sum<T, true>(d0, d1, info, vals + d0.x + lane, a.sl_ibuf + d0.y + lane, a.sl_tabs, x + row, valid,
                                lane, ck);
     }
-    if (valid) f(row, sum);
+    if (valid) f(row, sum, prow);
     __syncwarp();  // buffer b is read by every lane before it is refilled
     if (!more) break;
     ls += nw;
@@ -233,11 +238,13 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
   cp_async_wait<0>();
 }
 
-// Visit rows [i0, i1) of a system whose first row has global index ro: fv(v)
-// for every W-wide vector v (global vector index, 16-byte aligned) inside the
-// range, fs(i) for the ragged rows at either end.
-template <int W, typename FS, typename FV>
-__device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, FS&& fs, FV&& fv) {
+// Visit rows [i0, i1) of a system whose first row has global index ro:
+// st(v, ld(v)) for every W-wide vector v (global vector index, 16-byte
+// aligned) inside the range, fs(i) for the ragged rows at either end. (Two
+// vectors a trip, both loads before either store, measured slower: the extra
+// registers spill.)
+template <int W, typename FS, typename FL, typename FT>
+__device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, FS&& fs, FL&& ld, FT&& st) {
   const int64_t nth = blockDim.x, tid = threadIdx.x;
   const int64_t g0 = ro + i0, g1 = ro + i1;
   const int64_t v0 = (g0 + W - 1) / W, v1 = g1 / W;
@@ -246,9 +253,14 @@ __device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, FS&
     return;
   }
   for (int64_t g = g0 + tid; g < v0 * W; g += nth) fs(g - ro);
-  for (int64_t v = v0 + tid; v < v1; v += nth) fv(v);
+  for (int64_t v = v0 + tid; v < v1; v += nth) st(v, ld(v));
   for (int64_t g = v1 * W + tid; g < g1; g += nth) fs(g - ro);
 }
+
+// operands of one vector of the passes below
+struct V2x3 { double2 a, b, c; };
+struct V2x4 { double2 a, b, c, d; };
+struct F4x3 { float4 a, b, c; };
 
 }  // namespace
 
@@ -302,10 +314,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
     const int64_t i0 = min((int64_t)me * chunk, n), i1 = min(i0 + chunk, n);
     const int tid = threadIdx.x, nth = blockDim.x;
     // A x for rows [i0, i1) of this CTA, f(i, (A x)_i) for each
-    auto spmv64 = [&](const double* xv, auto&& f) {
-      if (sl) spmv_slices<double>(a, a.sl_vals, s0, xv, i0, i1, n, stage, f);
+    auto spmv64 = [&](const double* xv, const double* pre, auto&& f) {
+      if (sl) spmv_slices<double>(a, a.sl_vals, s0, xv, pre, i0, i1, n, stage, f);
       else
-        for (int64_t i = i0 + tid; i < i1; i += nth) f(i, row_dot_coherent<double>(rp, col, vals, xv, i, n));
+        for (int64_t i = i0 + tid; i < i1; i += nth) f(i, row_dot_coherent<double>(rp, col, vals, xv, i, n), pre[i]);
     };
 
     // value update of this CTA's rows (Sec. 3 update procedure) and the Jacobi diagonal
@@ -386,7 +398,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
             res_row(i, ri);
           }
         } else {
-          spmv64(x, [&](int64_t i, double axi) { res_row(i, b[i] - axi); });
+          spmv64(x, b, [&](int64_t i, double axi, double bi) { res_row(i, bi - axi); });
         }
         team_sum<3>(v3, t3, cl, spart, swarp, parity);
         if (passes == 0) {
@@ -406,12 +418,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
         for (;;) {
           cl.sync();  // p of every row visible to the team
           double v1[1] = {0.0}, t1[1];
-          auto qrow = [&](int64_t i, double qi) {
+          auto qrow = [&](int64_t i, double qi, double pi) {
             q[i] = qi;
-            v1[0] = fma(p[i], qi, v1[0]);
+            v1[0] = fma(pi, qi, v1[0]);
           };
-          if (sl) spmv_slices<double>(a, a.sl_vals, s0, p, i0, i1, n, stage, qrow);
-          else spmv_rows<double>(rp, col, vals, p, i0, i1, n, qrow);
+          if (sl) spmv_slices<double>(a, a.sl_vals, s0, p, p, i0, i1, n, stage, qrow);
+          else spmv_rows<double>(rp, col, vals, p, p, i0, i1, n, qrow);
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; break; }
           const double alpha = rz / t1[0];
@@ -425,9 +437,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
                 v2[1] = fma(ri, ri, v2[1]);
               },
               [&](int64_t v) {
-                const double2 qv = reinterpret_cast<const double2*>(a.q)[v];
-                double2 rv = reinterpret_cast<const double2*>(a.r)[v];
-                const double2 dv = reinterpret_cast<const double2*>(a.dinv)[v];
+                return V2x3{reinterpret_cast<const double2*>(a.q)[v], reinterpret_cast<const double2*>(a.r)[v],
+                            reinterpret_cast<const double2*>(a.dinv)[v]};
+              },
+              [&](int64_t v, const V2x3& o) {
+                const double2 qv = o.a, dv = o.c;
+                double2 rv = o.b;
                 rv.x = fma(-alpha, qv.x, rv.x);
                 rv.y = fma(-alpha, qv.y, rv.y);
                 reinterpret_cast<double2*>(a.r)[v] = rv;
@@ -450,20 +465,30 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
             if (!stop) p[i] = fma(beta, pi, dinv[i] * r[i]);
           };
           if (xvec) {
-            rows_vec<2>(ro, i0, i1, upd, [&](int64_t v) {
-              double2 pv = reinterpret_cast<const double2*>(a.p)[v];
-              double2 xv = reinterpret_cast<const double2*>(xall)[v];
-              xv.x = fma(alpha, pv.x, xv.x);
-              xv.y = fma(alpha, pv.y, xv.y);
-              reinterpret_cast<double2*>(xall)[v] = xv;
-              if (!stop) {
-                const double2 rv = reinterpret_cast<const double2*>(a.r)[v];
-                const double2 dv = reinterpret_cast<const double2*>(a.dinv)[v];
-                pv.x = fma(beta, pv.x, dv.x * rv.x);
-                pv.y = fma(beta, pv.y, dv.y * rv.y);
-                reinterpret_cast<double2*>(a.p)[v] = pv;
-              }
-            });
+            rows_vec<2>(
+                ro, i0, i1, upd,
+                [&](int64_t v) {
+                  V2x4 o;
+                  o.a = reinterpret_cast<const double2*>(a.p)[v];
+                  o.b = reinterpret_cast<const double2*>(xall)[v];
+                  if (!stop) {
+                    o.c = reinterpret_cast<const double2*>(a.r)[v];
+                    o.d = reinterpret_cast<const double2*>(a.dinv)[v];
+                  }
+                  return o;
+                },
+                [&](int64_t v, const V2x4& o) {
+                  double2 pv = o.a, xv = o.b;
+                  xv.x = fma(alpha, pv.x, xv.x);
+                  xv.y = fma(alpha, pv.y, xv.y);
+                  reinterpret_cast<double2*>(xall)[v] = xv;
+                  if (!stop) {
+                    const double2 rv = o.c, dv = o.d;
+                    pv.x = fma(beta, pv.x, dv.x * rv.x);
+                    pv.y = fma(beta, pv.y, dv.y * rv.y);
+                    reinterpret_cast<double2*>(a.p)[v] = pv;
+                  }
+                });
           } else {
             for (int64_t i = i0 + tid; i < i1; i += nth) upd(i);
           }
@@ -500,7 +525,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
             res_row(i, ri);
           }
         } else {
-          spmv64(x, [&](int64_t i, double axi) { res_row(i, b[i] - axi); });
+          spmv64(x, b, [&](int64_t i, double axi, double bi) { res_row(i, bi - axi); });
         }
         v4[0] = rzf;
         v4[3] = rr32f;
@@ -532,12 +557,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
         for (;;) {
           cl.sync();
           float acc = 0.f;
-          auto qrow = [&](int64_t i, float qi) {
+          auto qrow = [&](int64_t i, float qi, float pi) {
             q[i] = qi;
-            acc = fmaf(p[i], qi, acc);
+            acc = fmaf(pi, qi, acc);
           };
-          if (sl) spmv_slices<float>(a, a.sl_vals32, s0, p, i0, i1, n, stage, qrow);
-          else spmv_rows<float>(rp, col, vals32, p, i0, i1, n, qrow);
+          if (sl) spmv_slices<float>(a, a.sl_vals32, s0, p, p, i0, i1, n, stage, qrow);
+          else spmv_rows<float>(rp, col, vals32, p, p, i0, i1, n, qrow);
           double v1[1] = {(double)acc}, t1[1];
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; broke = true; break; }
@@ -556,9 +581,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
                 r[i] = ri;
               },
               [&](int64_t v) {
-                const float4 qv = reinterpret_cast<const float4*>(a.q32)[v];
-                float4 rv = reinterpret_cast<const float4*>(a.r32)[v];
-                const float4 dv = SCALED ? make_float4(1.f, 1.f, 1.f, 1.f) : reinterpret_cast<const float4*>(a.dinv32)[v];
+                F4x3 o;
+                o.a = reinterpret_cast<const float4*>(a.q32)[v];
+                o.b = reinterpret_cast<const float4*>(a.r32)[v];
+                o.c = SCALED ? make_float4(1.f, 1.f, 1.f, 1.f) : reinterpret_cast<const float4*>(a.dinv32)[v];
+                return o;
+              },
+              [&](int64_t v, const F4x3& o) {
+                const float4 qv = o.a, dv = o.c;
+                float4 rv = o.b;
                 rstep(rv.x, qv.x, dv.x);
                 rstep(rv.y, qv.y, dv.y);
                 rstep(rv.z, qv.z, dv.z);
@@ -583,15 +614,22 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
                 if (!stop) p[i] = fmaf(beta, pi, SCALED ? r[i] : dinv32[i] * r[i]);
               },
               [&](int64_t v) {
-                float4 pv = reinterpret_cast<const float4*>(a.p32)[v];
-                float4 dd = reinterpret_cast<const float4*>(a.d32)[v];
+                F4x3 o;
+                o.a = reinterpret_cast<const float4*>(a.p32)[v];
+                o.b = reinterpret_cast<const float4*>(a.d32)[v];
+                if (!stop) o.c = reinterpret_cast<const float4*>(a.r32)[v];
+                return o;
+              },
+              [&](int64_t v, const F4x3& o) {
+                float4 pv = o.a;
+                float4 dd = o.b;
                 dd.x = fmaf(alpha, pv.x, dd.x);
                 dd.y = fmaf(alpha, pv.y, dd.y);
                 dd.z = fmaf(alpha, pv.z, dd.z);
                 dd.w = fmaf(alpha, pv.w, dd.w);
                 reinterpret_cast<float4*>(a.d32)[v] = dd;
                 if (!stop) {
-                  const float4 rv = reinterpret_cast<const float4*>(a.r32)[v];
+                  const float4 rv = o.c;
                   const float4 iv = SCALED ? make_float4(1.f, 1.f, 1.f, 1.f) : reinterpret_cast<const float4*>(a.dinv32)[v];
                   pv.x = fmaf(beta, pv.x, iv.x * rv.x);
                   pv.y = fmaf(beta, pv.y, iv.y * rv.y);
@@ -849,8 +887,7 @@ extern "C" rp_status rp_batch_update_solve(rp_handle* h, const double* buffer, i
 
 extern "C" rp_status rp_batch_set_config(rp_handle* h, int32_t cluster, int32_t threads) {
   if (!h) return fail(RP_EINVAL, "null handle");
-  if (cluster < 1 || cluster > 16 || (cluster & (cluster - 1)))
-    return fail(RP_EINVAL, "cluster size must be 1, 2, 4, 8 or 16");
+  if (cluster < 1 || cluster > 16) return fail(RP_EINVAL, "cluster size must be in [1, 16]");
   if (threads < 64 || threads > kBatchMaxThreads || threads % 32)
     return fail(RP_EINVAL, "threads must be a multiple of 32 in [64, %d]", kBatchMaxThreads);
   RP_TRY(batch_prepare(h));
@@ -875,8 +912,11 @@ extern "C" rp_status rp_batch_autotune(rp_handle* h, const double* buffer, const
   if (!h || !buffer || !b || !x) return fail(RP_EINVAL, "null argument");
   RP_TRY(batch_prepare(h));
   cudaStream_t s = (cudaStream_t)stream;
-  const int clusters[] = {2, 4, 8, 16};
-  const int threads[] = {128, 256, 512};
+  // team counts between these shapes matter: with the largest systems first,
+  // too many small teams leave the largest system's team running alone at
+  // the end, too few large teams pay more barrier latency per iteration
+  const int clusters[] = {2, 3, 4, 5, 6, 8, 16};
+  const int threads[] = {256, 512};
   cudaEvent_t e0, e1;
   RP_TRY_CUDA(cudaEventCreate(&e0));
   RP_TRY_CUDA(cudaEventCreate(&e1));

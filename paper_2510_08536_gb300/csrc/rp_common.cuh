@@ -387,7 +387,7 @@ struct rp_handle {
 
   // batched form (one system per part)
   bool batch_ready = false;
-  int batch_cluster = 8, batch_threads = 512;  // autotuned by rp_batch_autotune
+  int batch_cluster = 5, batch_threads = 512;  // autotuned by rp_batch_autotune
   int32_t* batch_order = nullptr;
   int64_t *batch_row_off = nullptr, *batch_nnz_off = nullptr, *batch_buf_off = nullptr;
   unsigned int* batch_queue = nullptr;
