@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--only-batch", action="store_true",
                     help="run only the batched form (default launch shape, no loop baseline): profiling runs")
     ap.add_argument("--batch-systems", type=int, default=256)
+    ap.add_argument("--batch-shape", default=None,
+                    help="CLUSTERxTHREADS launch shape of the batched kernel instead of the autotuner's choice")
     ap.add_argument("--no-bicgstab", action="store_true",
                     help="skip the non-symmetric (momentum) solve and the adjoint measurement")
     ap.add_argument("--no-line", action="store_true", help="skip the line-preconditioner measurement")
@@ -411,7 +413,11 @@ def run_batch(args, dev, steps, warmup, loop_steps=1):
         del view
     out["layout"] = "sliced" if sl_sizes else "csr"
     hbm_peak, _ = load_peaks()
-    if not args.only_batch:
+    if args.batch_shape:
+        c, t = (int(v) for v in args.batch_shape.lower().split("x"))
+        repart.batch_set_config(h, c, t)
+        out["shape"] = {"cluster": c, "threads": t}
+    elif not args.only_batch:
         c, t, ms = repart.batch_autotune(h, stg[0], b, x, tol=1e-9, precision="fp64")
         out["autotuned"] = {"cluster": c, "threads": t, "tuning_ms": round(ms, 2)}
     stream = torch.cuda.current_stream()
