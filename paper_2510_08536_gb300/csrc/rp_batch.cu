@@ -238,13 +238,33 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
   cp_async_wait<0>();
 }
 
-// Visit rows [i0, i1) of a system whose first row has global index ro:
-// st(v, ld(v)) for every W-wide vector v (global vector index, 16-byte
-// aligned) inside the range, fs(i) for the ragged rows at either end. (Two
-// vectors a trip, both loads before either store, measured slower: the extra
-// registers spill.)
-template <int W, typename FS, typename FL, typename FT>
-__device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, FS&& fs, FL&& ld, FT&& st) {
+// Base pointers of the NOP operand vectors of a vector pass, as 16-byte vectors.
+template <int NOP>
+struct VecOps {
+  const uint4* p[NOP];
+};
+__device__ __forceinline__ const uint4* vec16(const void* p) { return reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ float4 as_f4(uint4 u) {
+  return make_float4(__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z), __uint_as_float(u.w));
+}
+__device__ __forceinline__ double2 as_d2(uint4 u) {
+  return make_double2(__hiloint2double((int)u.y, (int)u.x), __hiloint2double((int)u.w, (int)u.z));
+}
+
+// Visit rows [i0, i1) of a system whose first row has global index ro: for
+// every W-wide vector v (global vector index, 16-byte aligned) inside the range
+// st(v, s, k) with operand j of v at s[j k] (NOP operands from ops), fs(i) for the
+// ragged rows at either end. STAGED (the sliced layout's per-warp staging area,
+// free between SpMVs): every lane copies the operands of its next vector into
+// its own slots with cp.async (L2, coherent after the cluster barriers) while
+// it computes the current one from shared memory, so two vectors' loads are in
+// flight without holding either in registers (each lane reads only what it
+// copied: no warp barrier). Otherwise the operands are loaded straight into
+// registers, one vector a trip.
+template <int W, int NOP, bool STAGED, typename FS, typename FT>
+__device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, const VecOps<NOP>& ops,
+                                         unsigned char* stage, FS&& fs, FT&& st) {
+  static_assert(2 * NOP * 32 * 16 <= kWarpStage, "operand slots exceed the warp's staging area");
   const int64_t nth = blockDim.x, tid = threadIdx.x;
   const int64_t g0 = ro + i0, g1 = ro + i1;
   const int64_t v0 = (g0 + W - 1) / W, v1 = g1 / W;
@@ -253,14 +273,35 @@ __device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, FS&
     return;
   }
   for (int64_t g = g0 + tid; g < v0 * W; g += nth) fs(g - ro);
-  for (int64_t v = v0 + tid; v < v1; v += nth) st(v, ld(v));
+  if constexpr (STAGED) {
+    uint4* slot = reinterpret_cast<uint4*>(stage + (tid >> 5) * kWarpStage) + (tid & 31);  // [buffer][operand][lane]
+    auto issue = [&](int64_t v, int b) {
+#pragma unroll
+      for (int j = 0; j < NOP; ++j) cp_async16(slot + (b * NOP + j) * 32, ops.p[j] + v);
+    };
+    int64_t v = v0 + tid;
+    if (v < v1) issue(v, 0);
+    cp_async_commit();
+    int b = 0;
+    for (; v < v1; v += nth) {
+      if (v + nth < v1) issue(v + nth, b ^ 1);
+      cp_async_commit();
+      cp_async_wait<1>();  // this vector's copies
+      st(v, slot + b * NOP * 32, 32);
+      b ^= 1;
+    }
+    cp_async_wait<0>();
+  } else {
+    (void)stage;
+    for (int64_t v = v0 + tid; v < v1; v += nth) {
+      uint4 o[NOP];
+#pragma unroll
+      for (int j = 0; j < NOP; ++j) o[j] = ops.p[j][v];
+      st(v, o, 1);
+    }
+  }
   for (int64_t g = v1 * W + tid; g < g1; g += nth) fs(g - ro);
 }
-
-// operands of one vector of the passes below
-struct V2x3 { double2 a, b, c; };
-struct V2x4 { double2 a, b, c, d; };
-struct F4x3 { float4 a, b, c; };
 
 }  // namespace
 
@@ -428,21 +469,17 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; break; }
           const double alpha = rz / t1[0];
           double v2[2] = {0.0, 0.0}, t2[2];
-          rows_vec<2>(
-              ro, i0, i1,
+          rows_vec<2, 3, SL>(
+              ro, i0, i1, VecOps<3>{{vec16(a.q), vec16(a.r), vec16(a.dinv)}}, stage,
               [&](int64_t i) {
                 const double ri = fma(-alpha, q[i], r[i]);
                 r[i] = ri;
                 v2[0] = fma(ri, dinv[i] * ri, v2[0]);
                 v2[1] = fma(ri, ri, v2[1]);
               },
-              [&](int64_t v) {
-                return V2x3{reinterpret_cast<const double2*>(a.q)[v], reinterpret_cast<const double2*>(a.r)[v],
-                            reinterpret_cast<const double2*>(a.dinv)[v]};
-              },
-              [&](int64_t v, const V2x3& o) {
-                const double2 qv = o.a, dv = o.c;
-                double2 rv = o.b;
+              [&](int64_t v, const uint4* o, int k) {
+                const double2 qv = as_d2(o[0]), dv = as_d2(o[2 * k]);
+                double2 rv = as_d2(o[k]);
                 rv.x = fma(-alpha, qv.x, rv.x);
                 rv.y = fma(-alpha, qv.y, rv.y);
                 reinterpret_cast<double2*>(a.r)[v] = rv;
@@ -465,25 +502,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
             if (!stop) p[i] = fma(beta, pi, dinv[i] * r[i]);
           };
           if (xvec) {
-            rows_vec<2>(
-                ro, i0, i1, upd,
-                [&](int64_t v) {
-                  V2x4 o;
-                  o.a = reinterpret_cast<const double2*>(a.p)[v];
-                  o.b = reinterpret_cast<const double2*>(xall)[v];
-                  if (!stop) {
-                    o.c = reinterpret_cast<const double2*>(a.r)[v];
-                    o.d = reinterpret_cast<const double2*>(a.dinv)[v];
-                  }
-                  return o;
-                },
-                [&](int64_t v, const V2x4& o) {
-                  double2 pv = o.a, xv = o.b;
+            rows_vec<2, 4, SL>(
+                ro, i0, i1, VecOps<4>{{vec16(a.p), vec16(xall), vec16(a.r), vec16(a.dinv)}}, stage, upd,
+                [&](int64_t v, const uint4* o, int k) {
+                  double2 pv = as_d2(o[0]), xv = as_d2(o[k]);
                   xv.x = fma(alpha, pv.x, xv.x);
                   xv.y = fma(alpha, pv.y, xv.y);
                   reinterpret_cast<double2*>(xall)[v] = xv;
                   if (!stop) {
-                    const double2 rv = o.c, dv = o.d;
+                    const double2 rv = as_d2(o[2 * k]), dv = as_d2(o[3 * k]);
                     pv.x = fma(beta, pv.x, dv.x * rv.x);
                     pv.y = fma(beta, pv.y, dv.y * rv.y);
                     reinterpret_cast<double2*>(a.p)[v] = pv;
@@ -573,23 +600,21 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
             if (!SCALED) a0 = fmaf(rv, dv * rv, a0);
             a1 = fmaf(rv, rv, a1);
           };
-          rows_vec<4>(
-              ro, i0, i1,
+          VecOps<SCALED ? 2 : 3> rops;
+          rops.p[0] = vec16(a.q32);
+          rops.p[1] = vec16(a.r32);
+          if constexpr (!SCALED) rops.p[2] = vec16(a.dinv32);
+          rows_vec<4, SCALED ? 2 : 3, SL>(
+              ro, i0, i1, rops, stage,
               [&](int64_t i) {
                 float ri = r[i];
                 rstep(ri, q[i], SCALED ? 1.0f : dinv32[i]);
                 r[i] = ri;
               },
-              [&](int64_t v) {
-                F4x3 o;
-                o.a = reinterpret_cast<const float4*>(a.q32)[v];
-                o.b = reinterpret_cast<const float4*>(a.r32)[v];
-                o.c = SCALED ? make_float4(1.f, 1.f, 1.f, 1.f) : reinterpret_cast<const float4*>(a.dinv32)[v];
-                return o;
-              },
-              [&](int64_t v, const F4x3& o) {
-                const float4 qv = o.a, dv = o.c;
-                float4 rv = o.b;
+              [&](int64_t v, const uint4* o, int k) {
+                const float4 qv = as_f4(o[0]);
+                const float4 dv = SCALED ? make_float4(1.f, 1.f, 1.f, 1.f) : as_f4(o[(SCALED ? 0 : 2) * k]);
+                float4 rv = as_f4(o[k]);
                 rstep(rv.x, qv.x, dv.x);
                 rstep(rv.y, qv.y, dv.y);
                 rstep(rv.z, qv.z, dv.z);
@@ -606,31 +631,29 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           if (t2[1] <= ithresh || (RU ? iters : it) >= a.max_iter) stop = true;
           else if (!(t2[0] > 0.0) || !isfinite(t2[0])) { stop = true; status = RP_BREAKDOWN; broke = true; }
           else { beta = (float)(t2[0] / rz); rz = t2[0]; }
-          rows_vec<4>(
-              ro, i0, i1,
+          VecOps<SCALED ? 3 : 4> xops;
+          xops.p[0] = vec16(a.p32);
+          xops.p[1] = vec16(a.d32);
+          xops.p[2] = vec16(a.r32);
+          if constexpr (!SCALED) xops.p[3] = vec16(a.dinv32);
+          rows_vec<4, SCALED ? 3 : 4, SL>(
+              ro, i0, i1, xops, stage,
               [&](int64_t i) {
                 const float pi = p[i];
                 d[i] = fmaf(alpha, pi, d[i]);
                 if (!stop) p[i] = fmaf(beta, pi, SCALED ? r[i] : dinv32[i] * r[i]);
               },
-              [&](int64_t v) {
-                F4x3 o;
-                o.a = reinterpret_cast<const float4*>(a.p32)[v];
-                o.b = reinterpret_cast<const float4*>(a.d32)[v];
-                if (!stop) o.c = reinterpret_cast<const float4*>(a.r32)[v];
-                return o;
-              },
-              [&](int64_t v, const F4x3& o) {
-                float4 pv = o.a;
-                float4 dd = o.b;
+              [&](int64_t v, const uint4* o, int k) {
+                float4 pv = as_f4(o[0]);
+                float4 dd = as_f4(o[k]);
                 dd.x = fmaf(alpha, pv.x, dd.x);
                 dd.y = fmaf(alpha, pv.y, dd.y);
                 dd.z = fmaf(alpha, pv.z, dd.z);
                 dd.w = fmaf(alpha, pv.w, dd.w);
                 reinterpret_cast<float4*>(a.d32)[v] = dd;
                 if (!stop) {
-                  const float4 rv = o.c;
-                  const float4 iv = SCALED ? make_float4(1.f, 1.f, 1.f, 1.f) : reinterpret_cast<const float4*>(a.dinv32)[v];
+                  const float4 rv = as_f4(o[2 * k]);
+                  const float4 iv = SCALED ? make_float4(1.f, 1.f, 1.f, 1.f) : as_f4(o[(SCALED ? 0 : 3) * k]);
                   pv.x = fmaf(beta, pv.x, iv.x * rv.x);
                   pv.y = fmaf(beta, pv.y, iv.y * rv.y);
                   pv.z = fmaf(beta, pv.z, iv.z * rv.z);
