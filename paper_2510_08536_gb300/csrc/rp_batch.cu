@@ -274,21 +274,27 @@ __device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, con
   }
   for (int64_t g = g0 + tid; g < v0 * W; g += nth) fs(g - ro);
   if constexpr (STAGED) {
+    // D vectors in flight a lane: three where the slots fit, else two
+    constexpr int D = 3 * NOP * 32 * 16 <= kWarpStage ? 3 : 2;
     uint4* slot = reinterpret_cast<uint4*>(stage + (tid >> 5) * kWarpStage) + (tid & 31);  // [buffer][operand][lane]
     auto issue = [&](int64_t v, int b) {
 #pragma unroll
       for (int j = 0; j < NOP; ++j) cp_async16(slot + (b * NOP + j) * 32, ops.p[j] + v);
     };
     int64_t v = v0 + tid;
-    if (v < v1) issue(v, 0);
-    cp_async_commit();
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) {
+      if (v + j * nth < v1) issue(v + j * nth, j);
+      cp_async_commit();
+    }
     int b = 0;
     for (; v < v1; v += nth) {
-      if (v + nth < v1) issue(v + nth, b ^ 1);
+      // into the buffer the previous trip read (its values are already used)
+      if (v + (D - 1) * nth < v1) issue(v + (D - 1) * nth, b == 0 ? D - 1 : b - 1);
       cp_async_commit();
-      cp_async_wait<1>();  // this vector's copies
+      cp_async_wait<D - 1>();  // this vector's copies
       st(v, slot + b * NOP * 32, 32);
-      b ^= 1;
+      b = b + 1 == D ? 0 : b + 1;
     }
     cp_async_wait<0>();
   } else {
