@@ -394,6 +394,36 @@ __device__ __forceinline__ T slice_sum(uint2 d0, uint2 d1, uint32_t info, const 
   return slice_row<T, kIdx8Glob, COH>(v, iw, 0, tab, x, valid, L, D, ck);
 }
 
+// The table entry a lane holds for a slice: entry lane & 15 of a 4-bit table,
+// entry lane of an 8-bit one (the tables area keeps 32 spare words past its
+// last table, so the read stays inside it). For callers that load it a slice
+// ahead; in the bounds-checked build a reference outside the area loads
+// nothing (slice_desc_ok reports it when the slice is summed).
+__device__ __forceinline__ int32_t slice_tab_entry(uint32_t info, const int32_t* __restrict__ tabs, int lane,
+                                                   int64_t tabs_len) {
+  const int64_t t = info & ~kSliceW4;
+#ifdef RP_CHECK
+  if (t < 1 || t + 32 > tabs_len) return 0;
+#else
+  (void)tabs_len;
+#endif
+  return __ldg(tabs + t + ((info & kSliceW4) ? (lane & 15) : lane));
+}
+
+// slice_sum with the lane's table entry tv already loaded (slice_tab_entry).
+template <typename T, bool COH = false>
+__device__ __forceinline__ T slice_sum_tv(uint2 d0, uint2 d1, uint32_t info, int32_t tv, const T* v,
+                                          const uint32_t* iw, const int32_t* __restrict__ tabs, const T* x,
+                                          bool valid, const SliceCk& ck) {
+  int D = 0;
+  if (!slice_desc_ok(d0, d1, info, tabs, ck, D)) return T(0);
+  const int L = (int)((d1.x - d0.x) >> 5);
+  const int32_t* tab = tabs + (info & ~kSliceW4);
+  if (info & kSliceW4) return slice_row<T, kIdx4, COH>(v, iw, tv, tab, x, valid, L, D, ck);
+  if (__ldg(tab - 1) <= 32) return slice_row<T, kIdx8Shfl, COH>(v, iw, tv, tab, x, valid, L, D, ck);
+  return slice_row<T, kIdx8Glob, COH>(v, iw, 0, tab, x, valid, L, D, ck);
+}
+
 // The gather bounds of a lane's row in the bounds-checked build: the rows of
 // its part (several parts, MP) or of the matrix.
 template <typename T, bool MP>
