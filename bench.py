@@ -710,6 +710,7 @@ def run_ours(args):
     build_ms = 1e3 * (time.perf_counter() - tb)
     nnz, n_slots = h.nnz, h.n_slots
     sliced = repart.sliced_sizes(h)  # (slices, padded entries, table + index words) or None
+    uniform4 = repart.sliced_uniform4(h)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -836,7 +837,8 @@ def run_ours(args):
         # padded entry, index words; s itself: diagonal position + value read, FP64 write per row
         upd_bytes += (8 + 8 + 4) * sliced[1] + 4 * sliced[2] + 20 * n
     k1_name = "k_it_spmv_sl" if sliced else "k_it_spmv"
-    roof = {"bound": "hbm", "kernel": f"{k1_name}<{'double' if head == 'fp64' else 'float'}>",
+    u4 = ", true" if sliced and uniform4 else ""  # the uniform-slice instance
+    roof = {"bound": "hbm", "kernel": f"{k1_name}<{'double' if head == 'fp64' else 'float'}{u4}>",
             "achieved": round(gbs(spmv_bytes(head), kern[head]["spmv"]), 1), "peak": hbm_peak, "unit": "GB/s",
             "peak_kind": peak_kind}
     roof["frac"] = round(roof["achieved"] / hbm_peak, 4)
@@ -851,7 +853,7 @@ def run_ours(args):
         sm_mhz = clocks.get("fp64", {}).get("sm_max_mhz") or MAX_SM_MHZ
         peak_tf = fp64_peak_tflops(dev, sm_mhz)
         ach_tf = 2 * fma / (kern["fp64"]["spmv"] * 1e-3) / 1e12
-        fp64_alu = {"bound": "alu", "kernel": f"{k1_name}<double>", "achieved": round(ach_tf, 4), "unit": "TFLOP/s",
+        fp64_alu = {"bound": "alu", "kernel": f"{k1_name}<double{u4}>", "achieved": round(ach_tf, 4), "unit": "TFLOP/s",
                     "peak": round(peak_tf, 4), "peak_kind": "derived: SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
                     "frac": round(ach_tf / peak_tf, 4), "fma_per_launch": fma}
     kernels = {}
@@ -988,7 +990,8 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "headline": head,
                    "n_rows": n, "nnz": nnz, "draws_cycled": draws, "l2": "inputs larger than L2, no flush",
                    "layout": ({"kind": "sliced", "slices": sliced[0], "padded_entries": sliced[1],
-                               "index_words": sliced[2], "table_words": sliced[3]} if sliced else {"kind": "csr"}),
+                               "index_words": sliced[2], "table_words": sliced[3], "uniform4": uniform4}
+                              if sliced else {"kind": "csr"}),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "fp64_ms_per_step": round(results["fp64"]["ms_per_step"], 3) if "fp64" in results else None,
         "mixed_ms_per_step": round(results["mixed"]["ms_per_step"], 3) if "mixed" in results else None,

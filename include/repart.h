@@ -286,6 +286,11 @@ typedef struct rp_sliced_view {
    * it; then refilled by every value update. */
   const float* vals32s;
   const double* scale;
+  /* 1 if every slice has 4-bit indices and rows of at most 8 entries: the
+   * iteration then multiplies with a kernel instance that skips the checks of
+   * the general case (k_it_spmv_sl<T, true>; one part only, and not in the
+   * bounds-checked build, which checks every slice). */
+  int32_t uniform4;
 } rp_sliced_view;
 rp_status rp_get_sliced_view(const rp_handle* h, rp_sliced_view* out);
 

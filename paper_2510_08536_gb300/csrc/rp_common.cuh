@@ -200,6 +200,7 @@ struct Sliced {
   // one part, slice s holds rows 32 s ..
   const int2* srow = nullptr;
   int64_t n_entries = 0, ibuf_len = 0, tabs_len = 0;  // array lengths (bounds-checked build)
+  int u4 = 0;  // every slice has 4-bit indices and rows of at most 8 entries (every chunk is staged)
 };
 constexpr int kSliceDescPad = 8;  // bulk copies of descriptor runs may read past the end
 // Probe bound of the wait for a block's own bulk copies after another wait
@@ -345,6 +346,7 @@ struct rp_handle {
   int64_t sl_entries = 0;    // padded entries (32 per slice and width unit)
   int64_t sl_ibuf_len = 0;   // index words
   int64_t sl_tabs_len = 0;   // int32 words of the distinct tables
+  int sl_u4 = 0;             // every slice 4-bit with rows of at most 8 entries
   int64_t* sl_part_soff = nullptr;  // [n_parts + 1] first slice of each part (device)
   int2* sl_srow = nullptr;           // [sl_slices] first row, part << 6 | rows (n_parts > 1)
   uint2* sl_desc = nullptr;  // [sl_slices + 1]

@@ -263,6 +263,7 @@ void free_sliced(rp_handle* h) {
   h->sl_vals32 = nullptr;
   h->sl_valsT = nullptr;
   h->sl_slices = h->sl_entries = h->sl_ibuf_len = h->sl_tabs_len = 0;
+  h->sl_u4 = 0;
 }
 
 rp_status build_sliced(rp_handle* h, cudaStream_t st) {
@@ -315,6 +316,7 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
   std::unordered_map<std::string, uint32_t> seen;
   std::vector<uint2> desc(S + 1 + kSliceDescPad, make_uint2(0u, 0u));
   uint64_t x = 0, y = 0;
+  bool u4 = true;
   for (int64_t s = 0; s < S; ++s) {
     const int D = ht[s];
     std::string key(reinterpret_cast<const char*>(htab.data() + toff[s]), 4 * (size_t)D);
@@ -329,6 +331,7 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
       t = it->second;
     }
     const bool w4 = D <= 16;
+    u4 = u4 && w4 && hw[s] <= 8;
     tinfo[s] = t | (w4 ? kSliceW4 : 0u);
     desc[s] = make_uint2((uint32_t)x, (uint32_t)y);
     const int per = w4 ? 8 : 4;
@@ -391,6 +394,7 @@ rp_status build_sliced(rp_handle* h, cudaStream_t st) {
   RP_TRY(cu(cudaStreamSynchronize(st), "sliced layout build"));
   if (herr) return undo(fail(RP_ECUDA, "sliced layout: slice sizes differ between passes"));
   h->sl_slices = S;
+  h->sl_u4 = u4 ? 1 : 0;
   h->sl_entries = (int64_t)x;
   h->sl_ibuf_len = (int64_t)y;
   h->sl_tabs_len = (int64_t)tabs.size();
@@ -517,5 +521,6 @@ extern "C" rp_status rp_get_sliced_view(const rp_handle* h, rp_sliced_view* out)
   out->vals32s = h->sl_vals32s;
   out->scale = h->s64;
   out->srow = reinterpret_cast<const int32_t*>(h->sl_srow);
+  out->uniform4 = h->sl_u4 && !h->sl_srow ? 1 : 0;
   return RP_OK;
 }

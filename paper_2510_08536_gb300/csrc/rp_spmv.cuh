@@ -115,12 +115,12 @@ inline Sliced<double> sliced64(const rp_handle* h, const double* vals) {
   const double* v = vals == h->vals ? h->sl_vals : vals == h->valsT ? h->sl_valsT : nullptr;
   if (h->sl_slices == 0 || !v) return Sliced<double>{};
   return Sliced<double>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, v, h->opts.spin_limit,
-                        h->sl_srow, h->sl_entries, h->sl_ibuf_len, h->sl_tabs_len};
+                        h->sl_srow, h->sl_entries, h->sl_ibuf_len, h->sl_tabs_len, h->sl_u4};
 }
 inline Sliced<float> sliced32(const rp_handle* h) {
   if (h->sl_slices == 0 || !h->sl_vals32) return Sliced<float>{};
   return Sliced<float>{h->sl_slices, h->sl_desc, h->sl_tinfo, h->sl_tabs, h->sl_ibuf, h->sl_vals32,
-                       h->opts.spin_limit, h->sl_srow, h->sl_entries, h->sl_ibuf_len, h->sl_tabs_len};
+                       h->opts.spin_limit, h->sl_srow, h->sl_entries, h->sl_ibuf_len, h->sl_tabs_len, h->sl_u4};
 }
 
 // Rows of slice s: the first (global) row, how many of its 32 lanes hold a

@@ -58,7 +58,7 @@ class SolveInfo(ctypes.Structure):
 class SlicedView(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("n_slices", "n_entries", "ibuf_len", "tabs_len")] + \
                [(k, ctypes.c_void_p) for k in ("desc", "tinfo", "tabs", "ibuf", "pos", "vals", "vals32", "srow",
-                                               "vals32s", "scale")]
+                                               "vals32s", "scale")] + [("uniform4", ctypes.c_int32)]
 
 
 class MapView(ctypes.Structure):
@@ -291,6 +291,14 @@ def sliced_sizes(h: Handle):
     return (v.n_slices, v.n_entries, v.ibuf_len, v.tabs_len) if v.n_slices else None
 
 
+def sliced_uniform4(h: Handle) -> bool:
+    """Whether every slice has 4-bit indices and rows of at most 8 entries (the
+    iteration then runs the uniform-slice instance of its SpMV kernel)."""
+    v = SlicedView()
+    _check(load().rp_get_sliced_view(h.ptr, ctypes.byref(v)), "rp_get_sliced_view")
+    return bool(v.n_slices and v.uniform4)
+
+
 def inner_scaled(h: Handle) -> bool:
     """Whether the mixed solves' FP32 iteration runs on the scaled system S A S
     (made by the first mixed solve on a handle that takes it)."""
@@ -318,7 +326,7 @@ def get_sliced_view(h: Handle) -> dict:
                 vals32=_view(v.vals32, v.n_entries, "<f4").clone() if v.vals32 else None,
                 srow=_view(v.srow, 2 * v.n_slices, "<i4").clone() if v.srow else None,
                 vals32s=_view(v.vals32s, v.n_entries, "<f4").clone() if v.vals32s else None,
-                scale=_view(v.scale, h.n, "<f8").clone() if v.scale else None)
+                scale=_view(v.scale, h.n, "<f8").clone() if v.scale else None, uniform4=bool(v.uniform4))
 
 
 def batch_build(systems, want_fp32: bool = True, **opts) -> Handle:

@@ -129,6 +129,17 @@ def test_layout_and_values_bit_exact(name):
     view = repart.get_sliced_view(h)
     assert view is not None, "layout not built"
     check_layout(view, S.map, S.n)
+    # the uniform-slice flag: every slice 4-bit (table reference bit 31) with rows
+    # of at most 8 entries -- the iteration then runs the kernel instance without
+    # the general case's checks (the parity tests below cover both instances)
+    d = view["desc"].cpu().numpy().view(np.uint32).reshape(-1, 2)[: view["n_slices"] + 1, 0].astype(np.int64)
+    w4 = (view["tinfo"].cpu().numpy().view(np.uint32) >> 31) == 1
+    expect = bool(w4.all() and (np.diff(d) // 32 <= 8).all())
+    assert view["uniform4"] == expect, (name, view["uniform4"], expect)
+    if name == "box32_k8":  # 7-point stencil, equal cubic ranks: few offsets a slice
+        assert view["uniform4"]
+    if name == "banded_wide":  # rows of up to 25 entries
+        assert not view["uniform4"]
     pos = view["pos"].cpu().numpy()
     want = np.where(pos >= 0, S.vals[np.maximum(pos, 0)], 0.0)
     np.testing.assert_array_equal(view["vals"].cpu().numpy(), want)
