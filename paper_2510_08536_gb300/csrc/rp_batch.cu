@@ -168,7 +168,10 @@ __device__ __forceinline__ bool stageable(uint2 d0, uint2 d1, const BatchArgs& a
 // slice's gathers, so its latency hides behind theirs. Values and x are written
 // inside the kernel (the values before a block barrier, read back through L2;
 // x and pre with plain loads); descriptors, tables and index words are read-only.
-template <typename T, typename F>
+// U4: every slice has 4-bit indices and rows of at most kStageL entries (the
+// layout's uniform flag): every slice is staged and summed by the 4-bit row
+// sum directly, without the per-slice tests of the general case.
+template <typename T, bool U4 = false, typename F>
 __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, int64_t s0, const T* x, const T* pre,
                                             int64_t i0, int64_t i1, int64_t n, unsigned char* stage, F&& f) {
   if (i0 >= i1) return;  // i0 = n need not be a multiple of 32
@@ -188,7 +191,7 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
     n1 = __ldg(desc + ls + nw + 1);
     ninfo = __ldg(tinfo + ls + nw);
   }
-  if (stageable(d0, d1, a)) stage_slice<T>(wbuf, vals, a.sl_ibuf, d0, d1, lane);
+  if (U4 || stageable(d0, d1, a)) stage_slice<T>(wbuf, vals, a.sl_ibuf, d0, d1, lane);
   cp_async_commit();
   constexpr bool kTabAhead = sizeof(T) == 4;
   int32_t tv = kTabAhead ? slice_tab_entry(info, a.sl_tabs, lane, a.sl_tabs_len) : 0;  // this slice's table entry
@@ -196,7 +199,7 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
   for (;;) {
     const bool more = ls + nw < end;
     // the next slice's copy goes out before this one is summed
-    if (more && stageable(n0, n1, a)) stage_slice<T>(wbuf + (b ^ 1) * kStageBuf, vals, a.sl_ibuf, n0, n1, lane);
+    if (more && (U4 || stageable(n0, n1, a))) stage_slice<T>(wbuf + (b ^ 1) * kStageBuf, vals, a.sl_ibuf, n0, n1, lane);
     cp_async_commit();
     const int64_t lm = ls + 2 * nw;
     uint2 m0 = n1, m1 = n1;
@@ -226,7 +229,14 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
       else return slice_sum<T, true>(d0, d1, info, sv, si, a.sl_tabs, x + row, valid, lane, ck);
     };
     T sum;
-    if (stageable(d0, d1, a)) {
+    if constexpr (U4) {
+      const unsigned char* cur = wbuf + b * kStageBuf;
+      const int32_t* tab = a.sl_tabs + (info & ~kSliceW4);
+      sum = slice_row<T, kIdx4, true>(reinterpret_cast<const T*>(cur) + lane,
+                                      reinterpret_cast<const uint32_t*>(cur + kStageValBytes) + lane,
+                                      kTabAhead ? tv : __ldg(tab + (lane & 15)), tab, x + row, valid,
+                                      (int)((d1.x - d0.x) >> 5), 0, ck);
+    } else if (stageable(d0, d1, a)) {
       const unsigned char* cur = wbuf + b * kStageBuf;
       sum = sum_of(reinterpret_cast<const T*>(cur) + lane, reinterpret_cast<const uint32_t*>(cur + kStageValBytes) + lane);
     } else {
@@ -323,7 +333,7 @@ __device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, con
 
 // MODE: 0 FP64 PCG, 1 mixed (restarted inner PCG), 2 mixed with continued inner PCG;
 // SL: the SpMV and residual passes run on the sliced layout
-template <int MODE, bool SL>
+template <int MODE, bool SL, bool U4 = false>
 __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
   constexpr bool MIXED = MODE != 0;
   cg::cluster_group cl = cg::this_cluster();
@@ -372,7 +382,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
     const int tid = threadIdx.x, nth = blockDim.x;
     // A x for rows [i0, i1) of this CTA, f(i, (A x)_i) for each
     auto spmv64 = [&](const double* xv, const double* pre, auto&& f) {
-      if (sl) spmv_slices<double>(a, a.sl_vals, s0, xv, pre, i0, i1, n, stage, f);
+      if (sl) spmv_slices<double, U4>(a, a.sl_vals, s0, xv, pre, i0, i1, n, stage, f);
       else
         for (int64_t i = i0 + tid; i < i1; i += nth) f(i, row_dot_coherent<double>(rp, col, vals, xv, i, n), pre[i]);
     };
@@ -479,7 +489,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
             q[i] = qi;
             v1[0] = fma(pi, qi, v1[0]);
           };
-          if (sl) spmv_slices<double>(a, a.sl_vals, s0, p, p, i0, i1, n, stage, qrow);
+          if (sl) spmv_slices<double, U4>(a, a.sl_vals, s0, p, p, i0, i1, n, stage, qrow);
           else spmv_rows<double>(rp, col, vals, p, p, i0, i1, n, qrow);
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
           if (!(t1[0] > 0.0) || !isfinite(t1[0])) { status = RP_BREAKDOWN; break; }
@@ -604,7 +614,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
             q[i] = qi;
             acc = fmaf(pi, qi, acc);
           };
-          if (sl) spmv_slices<float>(a, a.sl_vals32, s0, p, p, i0, i1, n, stage, qrow);
+          if (sl) spmv_slices<float, U4>(a, a.sl_vals32, s0, p, p, i0, i1, n, stage, qrow);
           else spmv_rows<float>(rp, col, vals32, p, p, i0, i1, n, qrow);
           double v1[1] = {(double)acc}, t1[1];
           team_sum<1>(v1, t1, cl, spart, swarp, parity);
@@ -724,7 +734,16 @@ rp_status balloc(T** p, int64_t count) {
   return RP_OK;
 }
 
-void* batch_kernel(int mode, bool sl) {
+// the uniform-slice instances (never in the bounds-checked build, which checks every slice)
+#ifdef RP_CHECK
+constexpr bool kBatchU4 = false;
+#else
+constexpr bool kBatchU4 = true;
+#endif
+void* batch_kernel(int mode, bool sl, bool u4) {
+  if (sl && u4 && kBatchU4)
+    return mode == 2 ? (void*)k_batch<2, true, true> : mode == 1 ? (void*)k_batch<1, true, true>
+                                                                 : (void*)k_batch<0, true, true>;
   if (sl) return mode == 2 ? (void*)k_batch<2, true> : mode == 1 ? (void*)k_batch<1, true> : (void*)k_batch<0, true>;
   return mode == 2 ? (void*)k_batch<2, false> : mode == 1 ? (void*)k_batch<1, false> : (void*)k_batch<0, false>;
 }
@@ -732,7 +751,7 @@ void* batch_kernel(int mode, bool sl) {
 rp_status launch_config(rp_handle* h, int mode, int cluster, int threads, cudaLaunchConfig_t* cfg,
                         cudaLaunchAttribute* attr, int* n_clusters) {
   const bool sl = h->batch_args.sl_desc != nullptr;
-  void* fn = batch_kernel(mode, sl);
+  void* fn = batch_kernel(mode, sl, h->sl_u4 != 0);
   if (cluster > 8) RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   const int smem = sl ? (threads / 32) * kWarpStage : 0;
   RP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -768,7 +787,7 @@ rp_status build_batch_graph(rp_handle* h, int mode, int cluster, int threads, cu
   if (e == cudaSuccess) {
     cudaMemsetAsync(h->batch_queue, 0, sizeof(unsigned int), cs);
     void* args[] = {&ba};
-    cudaLaunchKernelExC(&cfg, batch_kernel(mode, ba.sl_desc != nullptr), args);
+    cudaLaunchKernelExC(&cfg, batch_kernel(mode, ba.sl_desc != nullptr, h->sl_u4 != 0), args);
     e = cudaStreamEndCapture(cs, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
