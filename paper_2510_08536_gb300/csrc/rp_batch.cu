@@ -132,14 +132,25 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // The warp copies slice (d0, d1) into buf: values (a multiple of 32 entries,
 // 128-byte aligned) at buf, index words (a multiple of 32) at buf + kStageValBytes.
+// The slices of a team's matrix are read once an iteration and are too many to
+// stay in L2 across the teams; copying them with an evict-first hint leaves L2 to
+// the vectors, which every pass reads again (4.6% of the continued-refinement
+// batch, 2.3% of FP64; the same hint in the single-system SpMV, whose vectors
+// fit in L2 anyway, made it slower).
+__device__ __forceinline__ void cp_async16_ef(void* dst, const void* src, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "l"(pol)
+               : "memory");
+}
 template <typename T>
 __device__ __forceinline__ void stage_slice(unsigned char* buf, const T* vals, const uint32_t* ibuf, uint2 d0,
                                             uint2 d1, int lane) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
   const uint32_t vb = (d1.x - d0.x) * (uint32_t)sizeof(T), ib = (d1.y - d0.y) * 4u;
   const unsigned char* vs = reinterpret_cast<const unsigned char*>(vals + d0.x);
   const unsigned char* is = reinterpret_cast<const unsigned char*>(ibuf + d0.y);
-  for (uint32_t o = 16u * lane; o < vb; o += 512u) cp_async16(buf + o, vs + o);
-  for (uint32_t o = 16u * lane; o < ib; o += 512u) cp_async16(buf + kStageValBytes + o, is + o);
+  for (uint32_t o = 16u * lane; o < vb; o += 512u) cp_async16_ef(buf + o, vs + o, pol);
+  for (uint32_t o = 16u * lane; o < ib; o += 512u) cp_async16_ef(buf + kStageValBytes + o, is + o, pol);
 }
 
 // Slices of up to kStageL entries a row are staged; in the bounds-checked
