@@ -308,9 +308,11 @@ __device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, con
     // D vectors in flight a lane: three where the slots fit, else two
     constexpr int D = 3 * NOP * 32 * 16 <= kWarpStage ? 3 : 2;
     uint4* slot = reinterpret_cast<uint4*>(stage + (tid >> 5) * kWarpStage) + (tid & 31);  // [buffer][operand][lane]
+    uint64_t pol;  // the vectors are read again by the next passes: keep them in L2
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     auto issue = [&](int64_t v, int b) {
 #pragma unroll
-      for (int j = 0; j < NOP; ++j) cp_async16(slot + (b * NOP + j) * 32, ops.p[j] + v);
+      for (int j = 0; j < NOP; ++j) cp_async16_ef(slot + (b * NOP + j) * 32, ops.p[j] + v, pol);
     };
     int64_t v = v0 + tid;
 #pragma unroll
