@@ -375,6 +375,28 @@ void launch_k1(const IterArgs<T>& a, int grid, cudaStream_t s) {
 
 // K2: r -= alpha q; z = D^-1 r (LINE: z = M^-1 r, stored; SCALED: the system
 // is scaled to a unit diagonal and z = r); (r, z), (r, r); stop test; beta.
+// FP32 vector loads / stores with an L2 evict-first policy, for vectors whose next
+// use is far: q after the residual kernel has read it, the correction d (read and
+// written once an iteration). With the matrix copies of K1 also evict-first, the
+// vectors the next kernels read (p, r) stay in L2: the scaled FP32 iteration's K2
+// 0.0391 -> 0.0363 ms, K3 0.0552 -> 0.0535 ms, the headline step 2% faster.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float4 ld_ef(const float4* p, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_ef(float4* p, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(pol)
+               : "memory");
+}
+
 template <typename T, bool LINE, bool SCALED = false>
 __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
   Ctl* c = a.ctl;
@@ -432,7 +454,15 @@ __global__ void __launch_bounds__(kThreads) k_it_resid(IterArgs<T> a) {
       });
     };
     for (; k + stride < nv; k += 2 * stride) {
-      V q0 = reinterpret_cast<const V*>(a.q)[k], q1 = reinterpret_cast<const V*>(a.q)[k + stride];
+      V q0, q1;
+      if constexpr (sizeof(T) == 4) {
+        const uint64_t pol = l2_evict_first();  // q is not read again
+        q0 = ld_ef(reinterpret_cast<const float4*>(a.q) + k, pol);
+        q1 = ld_ef(reinterpret_cast<const float4*>(a.q) + k + stride, pol);
+      } else {
+        q0 = reinterpret_cast<const V*>(a.q)[k];
+        q1 = reinterpret_cast<const V*>(a.q)[k + stride];
+      }
       V r0 = reinterpret_cast<const V*>(a.r)[k], r1 = reinterpret_cast<const V*>(a.r)[k + stride];
       sstep(r0, q0);
       sstep(r1, q1);
@@ -516,12 +546,15 @@ __global__ void __launch_bounds__(kThreads) k_it_xp(IterArgs<T> a) {
   const int64_t nv = (reinterpret_cast<uintptr_t>(x) & 15) ? 0 : a.n / W;
   for (int64_t k = tid; k < nv; k += stride) {
     V pv = reinterpret_cast<const V*>(a.p)[k];
-    V xv = reinterpret_cast<const V*>(x)[k];
+    V xv;
+    if constexpr (sizeof(T) == 4 && SCALED) xv = ld_ef(reinterpret_cast<const float4*>(x) + k, l2_evict_first());
+    else xv = reinterpret_cast<const V*>(x)[k];
     for_each_comp<W>([&](auto e) {
       constexpr int E = decltype(e)::value;
       comp<E>(xv) = fma(alpha, comp<E>(pv), comp<E>(xv));
     });
-    reinterpret_cast<V*>(x)[k] = xv;
+    if constexpr (sizeof(T) == 4 && SCALED) st_ef(reinterpret_cast<float4*>(x) + k, xv, l2_evict_first());
+    else reinterpret_cast<V*>(x)[k] = xv;
     if (upd_p) {
       if constexpr (LINE) {
         V zv = reinterpret_cast<const V*>(a.line.z)[k];
