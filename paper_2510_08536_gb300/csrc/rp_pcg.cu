@@ -377,9 +377,10 @@ void launch_k1(const IterArgs<T>& a, int grid, cudaStream_t s) {
 // is scaled to a unit diagonal and z = r); (r, z), (r, r); stop test; beta.
 // FP32 vector loads / stores with an L2 evict-first policy, for vectors whose next
 // use is far: q after the residual kernel has read it, the correction d (read and
-// written once an iteration). With the matrix copies of K1 also evict-first, the
-// vectors the next kernels read (p, r) stay in L2: the scaled FP32 iteration's K2
-// 0.0391 -> 0.0363 ms, K3 0.0552 -> 0.0535 ms, the headline step 2% faster.
+// written once an iteration), r when K3 has read it (K2 reads it next, after a whole
+// SpMV). With the matrix copies of K1 also evict-first, the vector the SpMV gathers
+// seven times (p) stays in L2: the headline step 257.4 -> 252.3 ms with the first two,
+// -> 245.0 ms with r (K1 0.1289 -> 0.1256 ms, K3 0.0551 -> 0.0501 ms).
 __device__ __forceinline__ uint64_t l2_evict_first() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -563,7 +564,9 @@ __global__ void __launch_bounds__(kThreads) k_it_xp(IterArgs<T> a) {
           comp<E>(pv) = fma(beta, comp<E>(pv), comp<E>(zv));
         });
       } else if constexpr (SCALED) {
-        V rv = reinterpret_cast<const V*>(a.r)[k];
+        V rv;
+        if constexpr (sizeof(T) == 4) rv = ld_ef(reinterpret_cast<const float4*>(a.r) + k, l2_evict_first());
+        else rv = reinterpret_cast<const V*>(a.r)[k];
         for_each_comp<W>([&](auto e) {
           constexpr int E = decltype(e)::value;
           comp<E>(pv) = fma(beta, comp<E>(pv), comp<E>(rv));
