@@ -273,6 +273,7 @@ __device__ __forceinline__ void spmv_slices(const BatchArgs& a, const T* vals, i
 template <int NOP>
 struct VecOps {
   const uint4* p[NOP];
+  unsigned first = 0;  // bit j: operand j is not read again soon (L2 evict-first), else evict-last
 };
 __device__ __forceinline__ const uint4* vec16(const void* p) { return reinterpret_cast<const uint4*>(p); }
 __device__ __forceinline__ float4 as_f4(uint4 u) {
@@ -308,11 +309,13 @@ __device__ __forceinline__ void rows_vec(int64_t ro, int64_t i0, int64_t i1, con
     // D vectors in flight a lane: three where the slots fit, else two
     constexpr int D = 3 * NOP * 32 * 16 <= kWarpStage ? 3 : 2;
     uint4* slot = reinterpret_cast<uint4*>(stage + (tid >> 5) * kWarpStage) + (tid & 31);  // [buffer][operand][lane]
-    uint64_t pol;  // the vectors are read again by the next passes: keep them in L2
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    uint64_t pol_last, pol_first;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_last));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol_first));
     auto issue = [&](int64_t v, int b) {
 #pragma unroll
-      for (int j = 0; j < NOP; ++j) cp_async16_ef(slot + (b * NOP + j) * 32, ops.p[j] + v, pol);
+      for (int j = 0; j < NOP; ++j)
+        cp_async16_ef(slot + (b * NOP + j) * 32, ops.p[j] + v, (ops.first >> j) & 1u ? pol_first : pol_last);
     };
     int64_t v = v0 + tid;
 #pragma unroll
@@ -642,6 +645,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           VecOps<SCALED ? 2 : 3> rops;
           rops.p[0] = vec16(a.q32);
           rops.p[1] = vec16(a.r32);
+          rops.first = 1u;  // q
           if constexpr (!SCALED) rops.p[2] = vec16(a.dinv32);
           rows_vec<4, SCALED ? 2 : 3, SL>(
               ro, i0, i1, rops, stage,
@@ -674,6 +678,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch(BatchArgs a) {
           xops.p[0] = vec16(a.p32);
           xops.p[1] = vec16(a.d32);
           xops.p[2] = vec16(a.r32);
+          xops.first = 2u | 4u;  // d, r
           if constexpr (!SCALED) xops.p[3] = vec16(a.dinv32);
           rows_vec<4, SCALED ? 3 : 4, SL>(
               ro, i0, i1, xops, stage,
