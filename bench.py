@@ -40,11 +40,11 @@ sys.path.insert(0, ROOT)
 METRIC = "update+PCG ms/time-step at 256^3 cells, FP64 vs mixed; SpMV HBM GB/s vs peak"
 # DRAM bytes per launch from ncu captures of the same kernels on the 192^3 case, scaled to
 # a 256^3 launch by the ratio of algorithmic bytes (one pass per array): sliced FP32 SpMV
-# (uniform-slice instance, evict-first copies) 261.9 MB of 285.2 MB algorithmic -- the
-# q writes now stay in L2 --, sliced FP64 506.9 MB of 539.4 MB, CSR FP32 477.4 MB of
+# (uniform-slice instance, evict-first copies) 261.5 MB of 285.2 MB algorithmic -- the
+# q writes now stay in L2 --, sliced FP64 507.1 MB of 539.4 MB, CSR FP32 477.4 MB of
 # 479.5 MB. Remove an entry when its kernel changes, until it is captured again.
-PROFILED_TRAFFIC = {("mixed_256", "k_it_spmv_sl<float, true>"): 621.1e6,
-                    ("mixed_256", "k_it_spmv_sl<double, true>"): 1202.0e6,
+PROFILED_TRAFFIC = {("mixed_256", "k_it_spmv_sl<float, true>"): 620.1e6,
+                    ("mixed_256", "k_it_spmv_sl<double, true>"): 1202.6e6,
                     ("mixed_256", "k_it_spmv<float>"): 1132.7e6}
 # FP64 FMA issue rate of a GB300 SM (2 per clock; 152 SMs x 2 x 2 flop x 2.07 GHz =
 # 1.26 TFLOP/s, the nominal 1.25): the FP64 path is bound by it, not by HBM.
