@@ -123,9 +123,6 @@ constexpr int kStageIdxBytes = 2 * 32 * 4;            // 8-bit indices: 2 words 
 constexpr int kStageBuf = kStageValBytes + kStageIdxBytes;
 constexpr int kWarpStage = 2 * kStageBuf;
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }

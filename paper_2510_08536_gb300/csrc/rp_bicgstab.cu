@@ -686,7 +686,7 @@ rp_status build_bs_graph(rp_handle* h, bool mixed, cudaGraphExec_t* exec) {
   cudaGraphConditionalHandle hout, hin;
   RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hout, top, 1, cudaGraphCondAssignDefault));
   cudaGraphNode_t wout, nres, win, nk[5];
-  cudaGraph_t obody, ibody;
+  cudaGraph_t obody = nullptr, ibody = nullptr;
   RP_TRY(while_node(top, &wout, nullptr, hout, &obody));
   RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hin, obody, 0, 0));
   BsArgs a = bs_args(h, hin, hout, 1);

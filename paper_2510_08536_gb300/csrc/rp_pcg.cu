@@ -978,7 +978,7 @@ rp_status build_solve_graph(rp_handle* h, int mode, const double* vals, const do
   cudaGraphConditionalHandle hout, hin;
   RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hout, top.g, 1, cudaGraphCondAssignDefault));
   cudaGraphNode_t wout, nres, win, n1, n2, n3, ncor;
-  cudaGraph_t obody, ibody;
+  cudaGraph_t obody = nullptr, ibody = nullptr;
   RP_TRY(add_while(top.g, &wout, nullptr, hout, &obody));
   RP_TRY_CUDA(cudaGraphConditionalHandleCreate(&hin, obody, 0, 0));
 
